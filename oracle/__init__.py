@@ -1,0 +1,264 @@
+"""CPU oracle for the WETSAND alignment hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  It shares
+no code with the CUDA library (``paper_2404_12134_gb300``) and never imports
+it; the only common module is the seeded input generator, which holds none of
+the method's arithmetic.
+
+What it computes (paper sections; the C body cites the equations):
+
+* ``dtw``          - DTW cost, optimal path, per-row column ranges, |pi|
+                     (Eq. 1, Eq. 5 at gamma = 0, Definitions "Alignment path"
+                     and "Alignment matrix", Sec. 3.2);
+* ``score``        - d_score = DTW / |pi| (Eq. 8, Sec. 3.4);
+* ``dba_iterate``  - one DTW Barycenter Averaging step (cited in Sec. 2 and
+                     used as a comparison in Table II; no formula printed);
+* ``softdtw``      - Soft-DTW value, R, E and gradient (Eqs. 3-6);
+* ``softdtw_batch``- barycenter objective Eq. 7 and its gradient;
+* ``medoid``, ``resample``, ``euclid_mean`` - initial barycenters (Table I:
+                     Euclidean-mean init; medoid for DBA).
+
+``prec='f64'`` is the reference precision.  ``prec='f32'`` mirrors the CUDA
+kernels' operation order in float so that the warping path, an integer
+decision taken from float comparisons, is decided in the same precision on
+both sides.
+
+Parity status: every function is pinned by tests/test_oracle_pins.py against
+brute-force enumeration, closed forms and invariants; the real-data
+experiments of the paper (Tables II-VI) are not reproducible here (parity
+unpinned for those, by absence of the data).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wetsand_oracle.c")
+_HDR = os.path.join(_HERE, "oracle_body.h")
+_BUILD = os.path.join(_HERE, "_build")
+_lock = threading.Lock()
+_libs: dict = {}
+
+f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+VP = ctypes.c_void_p
+
+
+def build(defines: tuple = (), force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, plain C, OpenMP across pairs)."""
+    tag = "_".join(d.lower() for d in defines) or "plain"
+    out = os.path.join(_BUILD, f"liboracle_{tag}.so")
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-std=c11", "-o", tmp, _SRC, "-lm"] + [f"-D{d}" for d in defines]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _lib(defines: tuple = ()):
+    key = tuple(defines)
+    with _lock:
+        if key in _libs:
+            return _libs[key]
+        lib = ctypes.CDLL(build(key))
+        for p, R, Rp in (("f64", ctypes.c_double, f64p), ("f32", ctypes.c_float, f32p)):
+            fn = getattr(lib, f"orc_dtw_{p}")
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int,
+                           VP, VP, VP, VP, VP, VP]
+            fn.restype = ctypes.c_int
+            fn = getattr(lib, f"orc_score_{p}")
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP]
+            fn.restype = ctypes.c_int
+            fn = getattr(lib, f"orc_dba_{p}")
+            fn.argtypes = [Rp, Rp, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP]
+            fn.restype = ctypes.c_int
+            fn = getattr(lib, f"orc_softdtw_{p}")
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, R, VP, VP, VP, VP]
+            fn.restype = ctypes.c_int
+            fn = getattr(lib, f"orc_softdtw_batch_{p}")
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, R, VP, VP, VP, VP]
+            fn.restype = ctypes.c_int
+        _libs[key] = lib
+        return lib
+
+
+def _dt(prec: str):
+    if prec not in ("f64", "f32"):
+        raise ValueError(prec)
+    return np.float64 if prec == "f64" else np.float32
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _as2d(x: np.ndarray) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float32)
+    if x.ndim == 1:
+        x = x[:, None]
+    return np.ascontiguousarray(x)
+
+
+def dtw(B, Y, prec: str = "f64", path: bool = True, _defines: tuple = ()):
+    """DTW(B, Y) with its optimal path under the tie order diag > up > left.
+
+    Returns dict(cost, plen, jlo, jhi, path_i, path_j); rows index B."""
+    B = _as2d(B); Y = _as2d(Y)
+    M, d = B.shape; N = Y.shape[0]
+    assert Y.shape[1] == d and M >= 1 and N >= 1
+    dt = _dt(prec)
+    cost = np.zeros(1, dtype=dt)
+    plen = np.zeros(1, dtype=np.int32)
+    jlo = np.zeros(M, dtype=np.int32); jhi = np.zeros(M, dtype=np.int32)
+    pi = np.zeros(M + N - 1, dtype=np.int32) if path else None
+    pj = np.zeros(M + N - 1, dtype=np.int32) if path else None
+    rc = getattr(_lib(_defines), f"orc_dtw_{prec}")(B, M, Y, N, d, _ptr(cost), _ptr(plen), _ptr(jlo), _ptr(jhi),
+                                                  _ptr(pi), _ptr(pj))
+    if rc:
+        raise RuntimeError(f"oracle dtw failed (rc={rc}: -1 allocation, -2 invalid choice matrix)")
+    L = int(plen[0])
+    out = dict(cost=cost[0], plen=L, jlo=jlo, jhi=jhi)
+    if path:
+        out["path_i"] = pi[:L].copy(); out["path_j"] = pj[:L].copy()
+    return out
+
+
+def score(B, data, offsets, prec: str = "f64", _defines: tuple = ()):
+    """Similarity score Eq. 8 for each cycle of a packed batch: (score, cost, plen)."""
+    B = _as2d(B); data = _as2d(data)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    T = offsets.shape[0] - 1
+    dt = _dt(prec)
+    s = np.zeros(T, dtype=dt); c = np.zeros(T, dtype=dt); L = np.zeros(T, dtype=np.int32)
+    rc = getattr(_lib(_defines), f"orc_score_{prec}")(B, B.shape[0], data, offsets, T, B.shape[1],
+                                                    _ptr(s), _ptr(c), _ptr(L))
+    if rc:
+        raise MemoryError("oracle score allocation failed")
+    return s, c, L
+
+
+def dba_iterate(B, data, offsets, prec: str = "f64", _defines: tuple = ()):
+    """One DBA iteration: (B_new, counts, cost_before, per-cycle costs)."""
+    dt = _dt(prec)
+    B = np.ascontiguousarray(np.asarray(B, dtype=dt).reshape(len(B), -1))
+    data = _as2d(data)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    T = offsets.shape[0] - 1
+    M, d = B.shape
+    Bo = np.zeros_like(B)
+    cnt = np.zeros(M, dtype=np.int32)
+    cb = np.zeros(1, dtype=np.float64)
+    ck = np.zeros(T, dtype=dt)
+    rc = getattr(_lib(_defines), f"orc_dba_{prec}")(B, Bo, M, data, offsets, T, d, _ptr(cnt), _ptr(cb), _ptr(ck))
+    if rc:
+        raise MemoryError("oracle dba allocation failed")
+    return Bo, cnt, float(cb[0]), ck
+
+
+def softdtw(B, Y, gamma: float, prec: str = "f64", want_R=False, want_E=False, want_grad=True,
+            _defines: tuple = ()):
+    """Soft-DTW^gamma(B, Y), optionally R, E ((M+2) x (N+2), 1-based) and grad [M, d]."""
+    B = _as2d(B); Y = _as2d(Y)
+    M, d = B.shape; N = Y.shape[0]
+    dt = _dt(prec)
+    v = np.zeros(1, dtype=dt)
+    R = np.zeros((M + 2, N + 2), dtype=dt) if want_R else None
+    E = np.zeros((M + 2, N + 2), dtype=dt) if want_E else None
+    g = np.zeros((M, d), dtype=dt) if want_grad else None
+    rc = getattr(_lib(_defines), f"orc_softdtw_{prec}")(B, M, Y, N, d, gamma, _ptr(v), _ptr(R), _ptr(E), _ptr(g))
+    if rc:
+        raise ValueError("oracle softdtw failed (allocation, or gamma <= 0 with a gradient requested)")
+    return dict(value=v[0], R=R, E=E, grad=g)
+
+
+def softdtw_batch(B, data, offsets, gamma: float, weights=None, prec: str = "f64", want_grad=True,
+                  _defines: tuple = ()):
+    """Eq. 7 objective over a packed batch: (values[T], loss, grad[M, d] or None)."""
+    B = _as2d(B); data = _as2d(data)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    T = offsets.shape[0] - 1
+    M, d = B.shape
+    dt = _dt(prec)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=dt)
+    vals = np.zeros(T, dtype=dt)
+    loss = np.zeros(1, dtype=dt)
+    g = np.zeros((M, d), dtype=dt) if want_grad else None
+    rc = getattr(_lib(_defines), f"orc_softdtw_batch_{prec}")(B, M, data, offsets, T, d, gamma, _ptr(w),
+                                                            _ptr(vals), _ptr(loss), _ptr(g))
+    if rc:
+        raise ValueError("oracle softdtw_batch failed")
+    return vals, loss[0], g
+
+
+# --- initial barycenters (Table I: Euclidean-mean init; DBA: medoid) ---------
+
+def medoid(data, offsets, subset=None):
+    """argmin_k sum_l DTW(Y_k, Y_l) over ``subset`` (default all); ties -> lowest k.
+
+    Pairwise costs use the FP32 mirror (the same precision the GPU uses), the
+    row sums are taken in double in ascending l.  Returns (index, cost matrix)."""
+    data = _as2d(data)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    idx = np.arange(offsets.shape[0] - 1) if subset is None else np.asarray(subset)
+    n = len(idx)
+    C = np.zeros((n, n), dtype=np.float32)
+    for a in range(n):
+        for b in range(a + 1, n):
+            ka, kb = int(idx[a]), int(idx[b])
+            c = dtw(data[offsets[ka]:offsets[ka + 1]], data[offsets[kb]:offsets[kb + 1]], "f32", path=False)["cost"]
+            C[a, b] = C[b, a] = c
+    sums = np.zeros(n, dtype=np.float64)
+    for a in range(n):
+        s = 0.0
+        for b in range(n):
+            s += float(C[a, b])
+        sums[a] = s
+    best = 0
+    for a in range(1, n):
+        if sums[a] < sums[best]:
+            best = a
+    return int(idx[best]), C
+
+
+def resample(x, M: int) -> np.ndarray:
+    """Linear resampling of a [N, d] series to M points spanning the same range.
+
+    Position m maps to p = m (N - 1) / (M - 1) in double; the value is
+    x[i] + (p - i)(x[i + 1] - x[i]) with i = floor(p), in double, rounded to float."""
+    x = _as2d(x).astype(np.float64)
+    N = x.shape[0]
+    out = np.zeros((M, x.shape[1]), dtype=np.float64)
+    for m in range(M):
+        p = (m * (N - 1)) / (M - 1) if M > 1 else 0.0
+        i = min(int(np.floor(p)), N - 1)
+        f = p - i
+        if i + 1 < N:
+            out[m] = x[i] + f * (x[i + 1] - x[i])
+        else:
+            out[m] = x[i]
+    return out.astype(np.float32)
+
+
+def euclid_mean(data, offsets, M: int) -> np.ndarray:
+    """Euclidean mean of the cycles, each resampled to M (Table I default init).
+    Summed in double, k ascending, divided by T, rounded to float."""
+    data = _as2d(data)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    T = offsets.shape[0] - 1
+    acc = np.zeros((M, data.shape[1]), dtype=np.float64)
+    for k in range(T):
+        acc += resample(data[offsets[k]:offsets[k + 1]], M).astype(np.float64)
+    return (acc / T).astype(np.float32)

@@ -1,0 +1,322 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each check ties the oracle to brute-force enumeration over all alignment paths
+(Definition "Alignment path", Eq. 1, Eq. 4), to a closed form, or to an
+invariant of the mathematics; none re-derives the oracle's recursion.  The
+last test plants plausible mistakes in the oracle (compile-time mutation
+hooks) and checks that each one trips at least one pin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from paper_2404_12134_gb300 import synth
+
+
+def _real_pair(rng, M, N, d):
+    return (rng.normal(size=(M, d)).astype(np.float32), rng.normal(size=(N, d)).astype(np.float32))
+
+
+# --- DTW: brute force -------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dtw_matches_brute_force_integer_ties(prec):
+    """Integer samples in {-3..3}: every cost exact, ties frequent.  Cost equal,
+    and the path equal to the lexicographically greatest optimal path under
+    the tie order diag > up > left."""
+    rng = np.random.default_rng(11)
+    for M in range(1, 7):
+        for N in range(1, 7):
+            for d in (1, 2, 3):
+                B, Y = synth.integer_pair(rng, M, N, d, -3, 3)
+                best, chosen, opt = brute.dtw(B, Y)
+                r = oracle.dtw(B, Y, prec)
+                assert float(r["cost"]) == best, (M, N, d)
+                assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen, (M, N, d)
+                assert r["plen"] == len(chosen)
+
+
+def test_dtw_matches_brute_force_real():
+    rng = np.random.default_rng(12)
+    for M in range(1, 7):
+        for N in range(1, 7):
+            B, Y = _real_pair(rng, M, N, 2)
+            best, chosen, opt = brute.dtw(B, Y)
+            r = oracle.dtw(B, Y, "f64")
+            assert abs(r["cost"] - best) <= 1e-12 * max(1.0, best)
+            assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen
+
+
+def test_path_counts_are_delannoy():
+    # the enumerator itself: number of complete paths = Delannoy D(M-1, N-1)
+    for M in range(1, 7):
+        for N in range(1, 7):
+            assert len(brute.paths(M, N)) == brute.delannoy(M - 1, N - 1)
+    assert brute.delannoy(5, 5) == 1683
+
+
+# --- DTW: closed forms and invariants ----------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dtw_self_is_zero_on_diagonal(prec):
+    rng = np.random.default_rng(13)
+    x = rng.normal(size=(257, 3)).astype(np.float32)
+    r = oracle.dtw(x, x, prec)
+    assert r["cost"] == 0
+    assert r["plen"] == 257
+    assert (r["path_i"] == np.arange(257)).all() and (r["path_j"] == np.arange(257)).all()
+    assert (r["jlo"] == np.arange(257)).all() and (r["jhi"] == np.arange(257)).all()
+
+
+def test_dtw_symmetric_cost():
+    rng = np.random.default_rng(14)
+    for M, N in ((40, 55), (1, 9), (9, 1), (63, 64)):
+        B, Y = _real_pair(rng, M, N, 3)
+        a = oracle.dtw(B, Y, "f64")["cost"]
+        b = oracle.dtw(Y, B, "f64")["cost"]
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(a))
+        Bi, Yi = synth.integer_pair(rng, M, N, 2)
+        assert oracle.dtw(Bi, Yi, "f32")["cost"] == oracle.dtw(Yi, Bi, "f32")["cost"]
+
+
+def test_dtw_bounded_by_euclidean_for_equal_lengths():
+    rng = np.random.default_rng(15)
+    for M in (1, 5, 100):
+        B, Y = _real_pair(rng, M, M, 2)
+        euc = float(((B.astype(np.float64) - Y) ** 2).sum())
+        assert oracle.dtw(B, Y, "f64")["cost"] <= euc * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_single_row_and_single_column_closed_form(prec):
+    rng = np.random.default_rng(16)
+    x = rng.integers(-5, 6, size=(1, 2)).astype(np.float32)
+    Y = rng.integers(-5, 6, size=(37, 2)).astype(np.float32)
+    exact = float(((Y.astype(np.float64) - x) ** 2).sum())
+    r = oracle.dtw(x, Y, prec)
+    assert float(r["cost"]) == exact and r["plen"] == 37
+    assert r["jlo"][0] == 0 and r["jhi"][0] == 36
+    r = oracle.dtw(Y, x, prec)
+    assert float(r["cost"]) == exact and r["plen"] == 37
+    assert (r["jlo"] == 0).all() and (r["jhi"] == 0).all()
+
+
+def test_integer_inputs_f32_equals_f64():
+    """Integer samples keep every partial sum exact in float and double, so the
+    two precisions must agree bit for bit, ties included."""
+    rng = np.random.default_rng(17)
+    for M, N, d in ((200, 180, 3), (64, 300, 1), (129, 130, 6)):
+        B, Y = synth.integer_pair(rng, M, N, d)
+        a = oracle.dtw(B, Y, "f64"); b = oracle.dtw(B, Y, "f32")
+        assert float(a["cost"]) == float(b["cost"])
+        assert (a["path_i"] == b["path_i"]).all() and (a["path_j"] == b["path_j"]).all()
+
+
+def test_ranges_describe_the_path():
+    rng = np.random.default_rng(18)
+    B, Y = _real_pair(rng, 90, 140, 2)
+    r = oracle.dtw(B, Y, "f64")
+    jlo, jhi = r["jlo"], r["jhi"]
+    assert jlo[0] == 0 and jhi[-1] == 139
+    assert (jlo <= jhi).all()
+    assert ((jlo[1:] == jhi[:-1]) | (jlo[1:] == jhi[:-1] + 1)).all()
+    assert int((jhi - jlo + 1).sum()) == r["plen"]
+    # |pi| = M + N - 1 - number of diagonal steps
+    di = np.diff(r["path_i"]); dj = np.diff(r["path_j"])
+    assert r["plen"] == 90 + 140 - 1 - int(((di == 1) & (dj == 1)).sum())
+
+
+# --- score (Eq. 8) ------------------------------------------------------------
+
+def test_score_closed_forms():
+    rng = np.random.default_rng(19)
+    x = rng.normal(size=(50, 2)).astype(np.float32)
+    Y = rng.normal(size=(70, 2)).astype(np.float32)
+    data = np.concatenate([x, Y]); offs = np.array([0, 50, 120])
+    s, c, L = oracle.score(x, data, offs, "f64")
+    assert s[0] == 0 and L[0] == 50
+    # single-sample prototype: score = mean local cost
+    s, c, L = oracle.score(x[:1], data, offs, "f64")
+    mean = ((Y.astype(np.float64) - x[0]) ** 2).sum(-1).mean()
+    assert abs(s[1] - mean) <= 1e-12 * mean and L[1] == 70
+
+
+# --- DBA ----------------------------------------------------------------------
+
+def test_dba_cost_non_increasing():
+    b = synth.config_batch(0, scale=0.08)
+    k0, _ = oracle.medoid(b.data, b.offsets)
+    B = b.cycle(k0).astype(np.float64)
+    prev = math.inf
+    for _ in range(8):
+        B, cnt, cost, _ = oracle.dba_iterate(B, b.data, b.offsets, "f64")
+        assert cost <= prev * (1 + 1e-12)
+        prev = cost
+
+
+def test_dba_counts_and_average_against_brute_force_paths():
+    rng = np.random.default_rng(20)
+    T, M, d = 3, 5, 2
+    B = rng.normal(size=(M, d)).astype(np.float32)
+    cyc = [rng.normal(size=(n, d)).astype(np.float32) for n in (4, 6, 5)]
+    data = np.concatenate(cyc); offs = np.array([0, 4, 10, 15])
+    Bn, cnt, cost, ck = oracle.dba_iterate(B, data, offs, "f64")
+    sums = np.zeros((M, d)); n = np.zeros(M)
+    tot = 0.0
+    for y in cyc:
+        best, path, _ = brute.dtw(B, y)
+        tot += best
+        for i, j in path:
+            sums[i] += y[j]; n[i] += 1
+    assert (cnt == n).all() and (cnt >= T).all()
+    assert np.allclose(Bn, sums / n[:, None], rtol=0, atol=1e-12)
+    assert abs(cost - tot) <= 1e-12 * tot
+
+
+def test_dba_fixed_points():
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(40, 3)).astype(np.float32)
+    data = np.concatenate([x, x, x]); offs = np.array([0, 40, 80, 120])
+    Bn, cnt, cost, _ = oracle.dba_iterate(x, data, offs, "f32")
+    assert (Bn == x).all() and cost == 0 and (cnt == 3).all()
+    const = np.full((33, 3), 0.375, dtype=np.float32)
+    data = np.concatenate([const, const[:20], const[:27]]); offs = np.array([0, 33, 53, 80])
+    Bn, cnt, cost, _ = oracle.dba_iterate(rng.normal(size=(25, 3)), data, offs, "f64")
+    assert (Bn == 0.375).all()
+
+
+# --- Soft-DTW ------------------------------------------------------------------
+
+def test_softdtw_matches_brute_force():
+    rng = np.random.default_rng(22)
+    for M in range(1, 6):
+        for N in range(1, 6):
+            B, Y = _real_pair(rng, M, N, 2)
+            for g in (0.1, 1.0, 10.0):
+                v, E = brute.softdtw(B, Y, g)
+                r = oracle.softdtw(B, Y, g, "f64", want_E=True)
+                assert abs(r["value"] - v) <= 1e-10 * max(1.0, abs(v)), (M, N, g)
+                assert np.allclose(r["E"][1:M + 1, 1:N + 1], E, rtol=1e-9, atol=1e-12), (M, N, g)
+
+
+def test_softdtw_sandwich_and_limit():
+    """DTW - gamma ln D(M-1,N-1) <= Soft-DTW <= DTW, so Soft-DTW -> DTW as gamma -> 0."""
+    rng = np.random.default_rng(23)
+    B, Y = _real_pair(rng, 6, 6, 1)
+    dtw = oracle.dtw(B, Y, "f64")["cost"]
+    nA = brute.delannoy(5, 5)
+    for g in (1.0, 0.1, 0.01, 0.001):
+        v = oracle.softdtw(B, Y, g, "f64", want_grad=False)["value"]
+        assert dtw - g * math.log(nA) - 1e-12 <= v <= dtw + 1e-12
+    B, Y = _real_pair(rng, 60, 70, 2)
+    dtw = oracle.dtw(B, Y, "f64")["cost"]
+    assert oracle.softdtw(B, Y, 0.0, "f64", want_grad=False)["value"] == dtw
+
+
+def test_softdtw_E_properties():
+    rng = np.random.default_rng(24)
+    B, Y = _real_pair(rng, 30, 41, 2)
+    E = oracle.softdtw(B, Y, 0.5, "f64", want_E=True)["E"][1:31, 1:42]
+    assert (E >= 0).all() and (E <= 1 + 1e-12).all()
+    assert abs(E[0, 0] - 1) < 1e-12 and abs(E[-1, -1] - 1) < 1e-12
+    assert (E.sum(1) >= 1 - 1e-9).all() and (E.sum(0) >= 1 - 1e-9).all()
+
+
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_softdtw_gradient_finite_differences(gamma):
+    """Central differences, h = 1e-3, lengths <= 64, in double."""
+    rng = np.random.default_rng(25)
+    B, Y = _real_pair(rng, 24, 64, 2)
+    g = oracle.softdtw(B, Y, gamma, "f64")["grad"]
+    h = 1e-3
+    for (i, c) in ((0, 0), (5, 1), (23, 0), (12, 1)):
+        Bp = B.astype(np.float64).copy(); Bm = Bp.copy()
+        # the oracle takes float32 samples: perturb by a float-representable step
+        Bp[i, c] += h; Bm[i, c] -= h
+        vp = oracle.softdtw(Bp.astype(np.float32), Y, gamma, "f64", want_grad=False)["value"]
+        vm = oracle.softdtw(Bm.astype(np.float32), Y, gamma, "f64", want_grad=False)["value"]
+        hp = float(np.float32(Bp[i, c])) - float(np.float32(Bm[i, c]))
+        fd = (vp - vm) / hp
+        assert abs(fd - g[i, c]) <= 1e-4 * max(1.0, abs(g[i, c])), (i, c, fd, g[i, c])
+
+
+def test_softdtw_batch_objective():
+    rng = np.random.default_rng(26)
+    B = rng.normal(size=(12, 1)).astype(np.float32)
+    cyc = [rng.normal(size=(n, 1)).astype(np.float32) for n in (10, 14, 9)]
+    data = np.concatenate(cyc); offs = np.array([0, 10, 24, 33])
+    vals, loss, grad = oracle.softdtw_batch(B, data, offs, 0.3)
+    exp_loss = 0.0; exp_grad = np.zeros_like(grad)
+    for y in cyc:
+        r = oracle.softdtw(B, y, 0.3)
+        exp_loss += r["value"] / len(y); exp_grad += r["grad"] / len(y)
+    assert abs(loss - exp_loss) < 1e-12 and np.allclose(grad, exp_grad, atol=1e-12)
+    # gradient of the objective by central differences
+    h = 1e-3
+    Bp = B.copy(); Bp[4, 0] += np.float32(h)
+    Bm = B.copy(); Bm[4, 0] -= np.float32(h)
+    fd = (oracle.softdtw_batch(Bp, data, offs, 0.3, want_grad=False)[1]
+          - oracle.softdtw_batch(Bm, data, offs, 0.3, want_grad=False)[1]) / (float(Bp[4, 0]) - float(Bm[4, 0]))
+    assert abs(fd - grad[4, 0]) < 1e-4 * max(1, abs(grad[4, 0]))
+
+
+# --- init helpers ---------------------------------------------------------------
+
+def test_resample_and_mean():
+    x = np.arange(10, dtype=np.float32)[:, None] * 2 + 1
+    assert (oracle.resample(x, 10) == x).all()
+    y = oracle.resample(x, 19)           # a line stays a line, endpoints kept
+    assert y[0, 0] == 1 and y[-1, 0] == 19 and np.allclose(np.diff(y[:, 0]), 1.0)
+    data = np.concatenate([x, x + 2]); offs = np.array([0, 10, 20])
+    assert np.allclose(oracle.euclid_mean(data, offs, 10), x + 1)
+
+
+def test_medoid_brute_force():
+    rng = np.random.default_rng(27)
+    cyc = [rng.normal(size=(n, 1)).astype(np.float32) for n in (5, 4, 6, 5)]
+    cyc.append(cyc[0] * 0 + cyc[3].mean())     # a flat cycle
+    data = np.concatenate(cyc); offs = np.concatenate([[0], np.cumsum([len(c) for c in cyc])])
+    k, C = oracle.medoid(data, offs)
+    S = [sum(brute.dtw(a, b)[0] for b in cyc) for a in cyc]
+    assert k == int(np.argmin(S))
+
+
+def test_generator_is_seeded():
+    a = synth.config_batch(1, scale=0.01); b = synth.config_batch(1, scale=0.01)
+    assert (a.data == b.data).all() and (a.offsets == b.offsets).all()
+    assert a.d == 6 and a.T == 200 and int(a.labels.astype(bool).sum()) == 20
+
+
+# --- mutation check: each planted mistake trips a pin ----------------------------
+
+def _pins_fail(defines) -> bool:
+    rng = np.random.default_rng(28)
+    try:
+        for M in range(2, 7):
+            for N in range(2, 7):
+                for d in (1, 3):
+                    B, Y = synth.integer_pair(rng, M, N, d, -2, 2)
+                    best, chosen, _ = brute.dtw(B, Y)
+                    r = oracle.dtw(B, Y, "f64", _defines=defines)
+                    if float(r["cost"]) != best or list(zip(r["path_i"].tolist(), r["path_j"].tolist())) != chosen:
+                        return True
+        for M, N in ((4, 5), (6, 3), (5, 5)):
+            B, Y = _real_pair(rng, M, N, 2)
+            v, E = brute.softdtw(B, Y, 0.5)
+            s = oracle.softdtw(B, Y, 0.5, "f64", want_E=True, _defines=defines)
+            if abs(s["value"] - v) > 1e-9 * max(1, abs(v)) or not np.allclose(s["E"][1:M + 1, 1:N + 1], E, atol=1e-9):
+                return True
+    except Exception:
+        return True
+    return False
+
+
+@pytest.mark.parametrize("plant", ["ORACLE_PLANT_DROP_CHANNEL", "ORACLE_PLANT_DIAG_INDEX",
+                                   "ORACLE_PLANT_TIE_ORDER", "ORACLE_PLANT_SOFTMIN_SIGN",
+                                   "ORACLE_PLANT_E_TRANSPOSE"])
+def test_planted_mistakes_are_caught(plant):
+    assert not _pins_fail(())
+    assert _pins_fail((plant,))
