@@ -1,0 +1,182 @@
+/*
+ * wetsand.h - C ABI of the GB300 (sm_103a) alignment hot path of WETSAND
+ * ("Warped Time Series Anomaly Detection", arXiv 2404.12134).
+ *
+ * The hot path is the alignment of many long, uneven cycles against one
+ * prototype by Dynamic Time Warping: it feeds DTW Barycenter Averaging (the
+ * prototype) and the per-cycle anomaly score, plus Soft-DTW with its gradient
+ * for gradient-based barycenters.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Rows index the prototype / barycenter B (length M), columns index a cycle
+ *    Y_k (length N_k): DTW(B, C_k) as in Eq. 8, Soft-DTW(B, Y_i) as in Eq. 7.
+ *  - Samples are d-channel FP32 vectors, row-major: B is [M][d]; a batch packs
+ *    T cycles back to back, cycle k = data[offsets[k]*d .. offsets[k+1]*d).
+ *    Time steps with missing values must already be removed (Sec. 3.1): every
+ *    sample must be finite; results for non-finite samples are unspecified
+ *    (no fault, no hang).
+ *  - Local cost delta(b_i, y_j) = sum_c (b_ic - y_jc)^2 (the Euclidean norm of
+ *    Sec. 3.2, squared).
+ *  - Equal predecessors resolve diag (i-1,j-1) first, then up (i-1,j), then
+ *    left (i,j-1): the path returned is, among all optimal complete alignment
+ *    paths, the one whose steps read backwards from (M-1,N-1) are
+ *    lexicographically greatest under diag > up > left.
+ *  - Every array argument is a DEVICE pointer owned by the caller unless
+ *    marked host.  The library never allocates device memory: scratch space is
+ *    one caller-owned workspace buffer whose size wts_workspace_size() gives.
+ *    A workspace must not be shared by calls in flight at the same time.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Outputs are valid once the stream has reached the call.
+ *    Inputs are validated on the host before any launch.
+ *  - Return value: WTS_OK or an error code; wts_last_error() gives the text
+ *    (thread-local).  A wait inside a kernel that gives up (it never does in
+ *    normal operation) leaves WTS_ETIMEOUT in the workspace's device status
+ *    word, read by wts_read_status().
+ */
+#ifndef WETSAND_H
+#define WETSAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    WTS_OK = 0,
+    WTS_EINVAL = 1,      /* bad argument: null pointer, shape, length, d, gamma */
+    WTS_ENOMEM = 2,      /* workspace smaller than wts_workspace_size() */
+    WTS_ECUDA = 3,       /* CUDA runtime error (launch or configuration) */
+    WTS_ETIMEOUT = 4,    /* a bounded in-kernel wait gave up (device status) */
+};
+
+/* Operation codes for wts_workspace_size(). */
+enum {
+    WTS_OP_ANOMALY_SCORE = 1,
+    WTS_OP_DTW_ALIGN = 2,
+    WTS_OP_DBA_ITERATE = 3,
+    WTS_OP_SOFTDTW = 4,        /* softdtw_forward + softdtw_backward (R kept in the workspace) */
+    WTS_OP_PAIRWISE = 5,
+};
+
+/* A packed batch of T cycles (Sec. 3.1: d-channel series of uneven lengths). */
+typedef struct wts_batch {
+    const float* data;             /* device, [sum_k N_k][d] */
+    const int64_t* offsets;        /* device, [T+1]: offsets[0] = 0, N_k = offsets[k+1]-offsets[k] >= 1 */
+    const int64_t* offsets_host;   /* host copy of offsets (plans the work, validates lengths) */
+    int32_t T;                     /* >= 1 */
+    int32_t d;                     /* 1..16 */
+} wts_batch;
+
+/* Launch options; a zeroed struct (or NULL) selects the defaults. */
+typedef struct wts_options {
+    int32_t rows_per_thread;       /* prototype rows held per lane: 0 = default (32 if d <= 2, else 16); 16 or 32 (32 needs d <= 3) */
+    int32_t warps_per_block;       /* 0 = 4; 1..8 */
+    int32_t max_blocks;            /* 0 = as many as are resident at once (persistent grid); else a cap */
+    int32_t keep_batch_order;      /* 0 = schedule the longest pairs first; 1 = batch order */
+    int32_t reserved[12];
+} wts_options;
+
+/* Library version (major * 100 + minor). */
+int wts_version(void);
+
+/* Text of the last error returned on this thread ("" if none). */
+const char* wts_last_error(void);
+
+/* Bytes of workspace that operation `op` needs for prototype length M and
+ * batch Y (M is ignored for WTS_OP_PAIRWISE).  Host-only; no CUDA call. */
+int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes);
+
+/* Synchronise `stream` and read the device status word of `workspace`
+ * (0 = ok, WTS_ETIMEOUT = an in-kernel wait gave up) into *status (host). */
+int wts_read_status(const void* workspace, void* stream, int32_t* status);
+
+/*
+ * anomaly_score - similarity score of Eq. 8 (Sec. 3.4):
+ *     d_score(B, C_k) = DTW(B, C_k) / |pi_k|,
+ * DTW by Eq. 1 (the recursion Eq. 5 at gamma = 0), |pi_k| = number of index
+ * pairs on the tie-rule optimal path (Definition "Alignment path"), counted on
+ * the fly without storing the path.  The division is one FP32 division.
+ *   B     [M][d]   prototype
+ *   score [T]      out: d_score per cycle
+ *   cost  [T]      out (may be NULL): DTW(B, C_k)
+ *   plen  [T]      out (may be NULL): |pi_k|
+ * Workspace: wts_workspace_size(WTS_OP_ANOMALY_SCORE, ...).
+ */
+int anomaly_score(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
+                  void* workspace, size_t workspace_bytes, void* stream,
+                  float* score, float* cost, int32_t* plen);
+
+/*
+ * dtw_align - DTW (Eq. 1) and its optimal complete alignment path
+ * (Definitions "Alignment path" / "Alignment matrix", Sec. 3.2) for every
+ * cycle.  The path of cycle k is returned as per-row column ranges: row i of
+ * B is aligned to columns jlo[k][i] .. jhi[k][i] of Y_k (a monotone path
+ * visits each row on one contiguous run of columns), and |pi_k| = sum_i
+ * (jhi - jlo + 1).
+ *   cost [T], plen [T]           out (either may be NULL)
+ *   jlo  [T][M], jhi [T][M]      out (int32)
+ * A 2-bit predecessor code per cell is kept in the workspace (M*N_k/4 bytes
+ * per cycle, plus a skew margin); wts_workspace_size(WTS_OP_DTW_ALIGN, ...).
+ */
+int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
+              void* workspace, size_t workspace_bytes, void* stream,
+              float* cost, int32_t* plen, int32_t* jlo, int32_t* jhi);
+
+/*
+ * dba_iterate - one iteration of DTW Barycenter Averaging (Petitjean et al.
+ * 2011; the paper cites it in Sec. 2 and compares with it in Table II and
+ * Fig. 6 without printing a formula):
+ *   1. align every cycle Y_k to B_in (dtw_align);
+ *   2. B_out[i] = (sum over k, over (i, j) on pi_k, of y_k[j]) / counts[i],
+ *      counts[i] = number of samples aligned to row i over all cycles;
+ *   3. cost_before = sum_k DTW(B_in, Y_k) (the intraclass inertia of Sec. 4.2
+ *      under the squared cost).
+ * Sums are accumulated in FP64 in a fixed order (cycle k ascending, sample j
+ * ascending), divided in FP64 and rounded once to FP32: the result does not
+ * depend on scheduling.
+ *   B_in [M][d], B_out [M][d] (must not alias B_in)
+ *   counts [M] out (may be NULL), cost_before: one double, out (may be NULL),
+ *   cost [T] out (may be NULL): DTW(B_in, Y_k)
+ * Workspace: wts_workspace_size(WTS_OP_DBA_ITERATE, ...).
+ */
+int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, const wts_options* opt,
+                void* workspace, size_t workspace_bytes, void* stream,
+                int32_t* counts, double* cost_before, float* cost);
+
+/*
+ * wts_pairwise_dtw - DTW between every two cycles of the batch (rows = the
+ * lower-index cycle), for the medoid that initialises DBA.
+ *   C [T][T] out: symmetric, C[a][a] = 0.
+ * Workspace: wts_workspace_size(WTS_OP_PAIRWISE, 0, Y, ...).  T >= 2.
+ */
+int wts_pairwise_dtw(const wts_batch* Y, const wts_options* opt, void* workspace, size_t workspace_bytes,
+                     void* stream, float* C);
+
+/*
+ * wts_medoid - argmin_a sum_b C[a][b] (row sums in FP64, b ascending; ties go
+ * to the lowest a).  C [n][n] from wts_pairwise_dtw; sums [n] out (double);
+ * index: one int32, out.
+ */
+int wts_medoid(const float* C, int32_t n, void* stream, double* sums, int32_t* index);
+
+/*
+ * wts_resample - linear resampling of x [N][d] to out [M][d] over the same
+ * span (position m -> m (N-1)/(M-1)), in FP64, rounded to FP32; used to bring
+ * an initial barycenter to the barycenter length m_b (Sec. 3.3).
+ */
+int wts_resample(const float* x, int64_t N, int32_t d, float* out, int64_t M, void* stream);
+
+/*
+ * wts_euclid_mean - Euclidean mean of the batch's cycles, each resampled to M
+ * (the default barycenter initialisation of Table I): out [M][d].
+ */
+int wts_euclid_mean(const wts_batch* Y, int64_t M, float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WETSAND_H */

@@ -1,0 +1,212 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Every function takes CUDA tensors, builds the C structs, hands raw device
+pointers and the current torch stream to ``libwetsand.so`` and returns the
+output tensors.  No step of the method runs here; PyTorch supplies device
+memory (outputs and the workspace, from its caching allocator) and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, wts_batch, wts_options
+
+
+class Batch:
+    """A packed batch of T cycles resident on the GPU (Sec. 3.1 layout).
+
+    data [sum N_k, d] float32 (CUDA), offsets [T+1] int64 (CUDA) plus the host
+    copy of the offsets, which the library uses to plan the work."""
+
+    def __init__(self, data: torch.Tensor, offsets: torch.Tensor, offsets_host: np.ndarray | None = None):
+        if data.dim() == 1:
+            data = data[:, None]
+        if not (data.is_cuda and data.dtype == torch.float32 and data.is_contiguous()):
+            raise ValueError("data must be a contiguous float32 CUDA tensor")
+        if not (offsets.is_cuda and offsets.dtype == torch.int64 and offsets.is_contiguous()):
+            raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+        self.data = data
+        self.offsets = offsets
+        if offsets_host is None:
+            offsets_host = offsets.cpu().numpy()
+        self.offsets_host = np.ascontiguousarray(offsets_host, dtype=np.int64)
+        self.T = int(self.offsets_host.shape[0] - 1)
+        self.d = int(data.shape[1])
+
+    @classmethod
+    def from_numpy(cls, data: np.ndarray, offsets: np.ndarray, device="cuda") -> "Batch":
+        d = torch.from_numpy(np.ascontiguousarray(data, dtype=np.float32)).to(device)
+        o = torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.int64)).to(device)
+        return cls(d, o, offsets)
+
+    @property
+    def lengths(self) -> np.ndarray:
+        return np.diff(self.offsets_host)
+
+    def c(self) -> wts_batch:
+        b = wts_batch()
+        b.data = self.data.data_ptr()
+        b.offsets = self.offsets.data_ptr()
+        b.offsets_host = self.offsets_host.ctypes.data
+        b.T = self.T
+        b.d = self.d
+        return b
+
+
+def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0) -> wts_options:
+    o = wts_options()
+    o.rows_per_thread = rows_per_thread
+    o.warps_per_block = warps_per_block
+    o.max_blocks = max_blocks
+    o.keep_batch_order = keep_batch_order
+    return o
+
+
+def _opt(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _p(t: torch.Tensor | None):
+    return None if t is None else t.data_ptr()
+
+
+class Workspace:
+    """A reusable device buffer from torch's allocator, grown on demand."""
+
+    def __init__(self, device=None):
+        self.device = torch.device("cuda" if device is None else device)
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = None
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    def status(self) -> int:
+        return read_status(self.buf)
+
+
+_default_ws: dict = {}
+
+
+def _ws(ws: Workspace | None, nbytes: int) -> torch.Tensor:
+    if ws is None:
+        dev = torch.cuda.current_device()
+        ws = _default_ws.setdefault(dev, Workspace(dev))
+    return ws.get(nbytes)
+
+
+def workspace_size(op: int, M: int, batch: Batch, opts=None) -> int:
+    n = ctypes.c_size_t(0)
+    check(_abi.load().wts_workspace_size(op, M, ctypes.byref(batch.c()), _opt(opts), ctypes.byref(n)))
+    return n.value
+
+
+def read_status(buf: torch.Tensor) -> int:
+    s = ctypes.c_int32(0)
+    check(_abi.load().wts_read_status(buf.data_ptr(), _stream(), ctypes.byref(s)))
+    return s.value
+
+
+def _check_B(B: torch.Tensor, d: int) -> torch.Tensor:
+    if B.dim() == 1:
+        B = B[:, None]
+    if not (B.is_cuda and B.dtype == torch.float32 and B.is_contiguous()) or B.shape[1] != d:
+        raise ValueError(f"prototype must be a contiguous float32 CUDA tensor [M, {d}]")
+    return B
+
+
+def anomaly_score(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None):
+    """Eq. 8 per cycle: (score [T], cost [T], plen [T])."""
+    B = _check_B(B, batch.d)
+    M = B.shape[0]
+    lib = _abi.load()
+    nb = workspace_size(_abi.OP_ANOMALY_SCORE, M, batch, opts)
+    buf = _ws(ws, nb)
+    dev = B.device
+    score = torch.empty(batch.T, dtype=torch.float32, device=dev)
+    cost = torch.empty(batch.T, dtype=torch.float32, device=dev)
+    plen = torch.empty(batch.T, dtype=torch.int32, device=dev)
+    check(lib.anomaly_score(B.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts), buf.data_ptr(), buf.numel(),
+                            _stream(), score.data_ptr(), cost.data_ptr(), plen.data_ptr()))
+    return score, cost, plen
+
+
+def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None):
+    """DTW and tie-rule path per cycle: (cost [T], plen [T], jlo [T, M], jhi [T, M])."""
+    B = _check_B(B, batch.d)
+    M = B.shape[0]
+    lib = _abi.load()
+    nb = workspace_size(_abi.OP_DTW_ALIGN, M, batch, opts)
+    buf = _ws(ws, nb)
+    dev = B.device
+    cost = torch.empty(batch.T, dtype=torch.float32, device=dev)
+    plen = torch.empty(batch.T, dtype=torch.int32, device=dev)
+    jlo = torch.empty((batch.T, M), dtype=torch.int32, device=dev)
+    jhi = torch.empty((batch.T, M), dtype=torch.int32, device=dev)
+    check(lib.dtw_align(B.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts), buf.data_ptr(), buf.numel(),
+                        _stream(), cost.data_ptr(), plen.data_ptr(), jlo.data_ptr(), jhi.data_ptr()))
+    return cost, plen, jlo, jhi
+
+
+def dba_iterate(B_in: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None, B_out=None,
+                counts=None, cost_before=None, cost=None):
+    """One DBA iteration: (B_out [M, d], counts [M], cost_before (0-d float64), cost [T])."""
+    B_in = _check_B(B_in, batch.d)
+    M = B_in.shape[0]
+    lib = _abi.load()
+    nb = workspace_size(_abi.OP_DBA_ITERATE, M, batch, opts)
+    buf = _ws(ws, nb)
+    dev = B_in.device
+    B_out = torch.empty_like(B_in) if B_out is None else B_out
+    counts = torch.empty(M, dtype=torch.int32, device=dev) if counts is None else counts
+    cost_before = torch.empty((), dtype=torch.float64, device=dev) if cost_before is None else cost_before
+    cost = torch.empty(batch.T, dtype=torch.float32, device=dev) if cost is None else cost
+    check(lib.dba_iterate(B_in.data_ptr(), B_out.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts),
+                          buf.data_ptr(), buf.numel(), _stream(), counts.data_ptr(), cost_before.data_ptr(),
+                          cost.data_ptr()))
+    return B_out, counts, cost_before, cost
+
+
+def pairwise_dtw(batch: Batch, opts=None, ws: Workspace | None = None) -> torch.Tensor:
+    """[T, T] symmetric matrix of DTW costs between cycles."""
+    lib = _abi.load()
+    nb = workspace_size(_abi.OP_PAIRWISE, 0, batch, opts)
+    buf = _ws(ws, nb)
+    C = torch.empty((batch.T, batch.T), dtype=torch.float32, device=batch.data.device)
+    check(lib.wts_pairwise_dtw(ctypes.byref(batch.c()), _opt(opts), buf.data_ptr(), buf.numel(), _stream(),
+                               C.data_ptr()))
+    return C
+
+
+def medoid(C: torch.Tensor):
+    """(index (0-d int32 tensor), row sums [n] float64) of a pairwise cost matrix."""
+    n = C.shape[0]
+    sums = torch.empty(n, dtype=torch.float64, device=C.device)
+    idx = torch.empty((), dtype=torch.int32, device=C.device)
+    check(_abi.load().wts_medoid(C.contiguous().data_ptr(), n, _stream(), sums.data_ptr(), idx.data_ptr()))
+    return idx, sums
+
+
+def resample(x: torch.Tensor, M: int) -> torch.Tensor:
+    if x.dim() == 1:
+        x = x[:, None]
+    x = x.contiguous()
+    out = torch.empty((M, x.shape[1]), dtype=torch.float32, device=x.device)
+    check(_abi.load().wts_resample(x.data_ptr(), x.shape[0], x.shape[1], out.data_ptr(), M, _stream()))
+    return out
+
+
+def euclid_mean(batch: Batch, M: int) -> torch.Tensor:
+    out = torch.empty((M, batch.d), dtype=torch.float32, device=batch.data.device)
+    check(_abi.load().wts_euclid_mean(ctypes.byref(batch.c()), M, out.data_ptr(), _stream()))
+    return out

@@ -1,0 +1,419 @@
+// C ABI entry points: validation, workspace layout, launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/wetsand.h"
+#include "dba.cuh"
+#include "dtw_wavefront.cuh"
+#include "plan.cuh"
+
+namespace wts {
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int ok()
+{
+    g_err.clear();
+    return WTS_OK;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(WTS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int pick_D(int d)
+{
+    static const int Ds[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    for (int D : Ds)
+        if (D >= d) return D;
+    return 0;
+}
+
+int pick_R(int D, const wts_options* opt)
+{
+    if (opt && opt->rows_per_thread) return opt->rows_per_thread;
+    return D <= 2 ? 32 : 16;
+}
+
+int check_batch(const wts_batch* Y, bool need_device)
+{
+    if (!Y) return fail(WTS_EINVAL, "batch is NULL");
+    if (Y->T < 1) return fail(WTS_EINVAL, "batch has T=%d cycles (need >= 1)", Y->T);
+    if (Y->d < 1 || Y->d > kMaxD) return fail(WTS_EINVAL, "d=%d outside 1..%d", Y->d, kMaxD);
+    if (!Y->offsets_host) return fail(WTS_EINVAL, "batch offsets_host is NULL");
+    if (need_device && (!Y->data || !Y->offsets)) return fail(WTS_EINVAL, "batch data/offsets is NULL");
+    if (Y->offsets_host[0] != 0) return fail(WTS_EINVAL, "offsets[0] must be 0");
+    for (int k = 0; k < Y->T; ++k) {
+        const int64_t n = Y->offsets_host[k + 1] - Y->offsets_host[k];
+        if (n < 1) return fail(WTS_EINVAL, "cycle %d has length %lld (need >= 1)", k, (long long)n);
+        if (n > (int64_t)1 << 30) return fail(WTS_EINVAL, "cycle %d too long (%lld)", k, (long long)n);
+    }
+    return WTS_OK;
+}
+
+int check_opt(const wts_options* opt, int D)
+{
+    if (!opt) return WTS_OK;
+    if (opt->rows_per_thread && opt->rows_per_thread != 16 && opt->rows_per_thread != 32)
+        return fail(WTS_EINVAL, "rows_per_thread must be 0, 16 or 32");
+    if (opt->rows_per_thread == 32 && D > 3) return fail(WTS_EINVAL, "rows_per_thread=32 needs d <= 3");
+    if (opt->warps_per_block < 0 || opt->warps_per_block > 8) return fail(WTS_EINVAL, "warps_per_block must be 0..8");
+    if (opt->max_blocks < 0) return fail(WTS_EINVAL, "max_blocks must be >= 0");
+    return WTS_OK;
+}
+
+// Layout of the workspace for one call (host side; mirrors the setup kernel).
+int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt, Layout* L)
+{
+    int rc = check_batch(Y, false);
+    if (rc) return rc;
+    const int D = pick_D(Y->d);
+    rc = check_opt(opt, D);
+    if (rc) return rc;
+    if (op != kOpPairwise && (M < 1 || M > (int64_t)1 << 30)) return fail(WTS_EINVAL, "M=%lld out of range", (long long)M);
+    if (op == kOpPairwise && Y->T < 2) return fail(WTS_EINVAL, "pairwise DTW needs T >= 2");
+    if (op == kOpPairwise && Y->T > 4096) return fail(WTS_EINVAL, "pairwise DTW limited to T <= 4096");
+    *L = Layout{};
+    L->op = op;
+    L->T = Y->T;
+    L->P = op == kOpPairwise ? Y->T * (Y->T - 1) / 2 : Y->T;
+    L->d = Y->d;
+    L->D = D;
+    L->R = pick_R(D, opt);
+    L->BR = 32 * L->R;
+    L->M = M;
+    const int64_t* o = Y->offsets_host;
+    int64_t items = 0, h = 0, dw = 0, rs = 0;
+    for (int p = 0; p < L->P; ++p) {
+        int64_t Mp, Np;
+        if (op == kOpPairwise) {
+            int a = 0, rem = p;
+            while (rem >= L->T - 1 - a) { rem -= L->T - 1 - a; ++a; }
+            const int b = a + 1 + rem;
+            Mp = o[a + 1] - o[a];
+            Np = o[b + 1] - o[b];
+        } else {
+            Mp = M;
+            Np = o[p + 1] - o[p];
+        }
+        const int64_t nb = cdiv(Mp, L->BR);
+        items += nb;
+        h += pair_hbuf_floats(nb, Np);
+        if (op == kOpAlign || op == kOpDba) dw += pair_dir_words(nb, Np, L->R);
+        if (op == kOpSoft) rs += pair_rstore_floats(nb, Np, L->R);
+    }
+    if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
+    L->n_items = items;
+    L->n_flags = items;
+    L->hbuf_floats = h;
+    L->dir_words = dw;
+    L->rstore_floats = rs;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
+    L->off_hdr = take(sizeof(WsHeader));
+    L->off_flags = take((size_t)items * sizeof(int));            // zeroed with the header
+    if (op == kOpSoft) L->off_flags2 = take((size_t)items * sizeof(int));
+    L->off_pairs = take((size_t)L->P * sizeof(PairDesc));
+    L->off_order = take((size_t)L->P * sizeof(int32_t));
+    L->off_prefix = take((size_t)(L->P + 1) * sizeof(int32_t));
+    L->off_hbuf = take((size_t)h * sizeof(float));
+    if (op == kOpScore) L->off_hcnt = take((size_t)h * sizeof(int));
+    if (op == kOpAlign || op == kOpDba) L->off_dirs = take((size_t)dw * sizeof(uint32_t));
+    if (op == kOpDba) {
+        L->off_jlo = take((size_t)L->T * M * sizeof(int32_t));
+        L->off_jhi = take((size_t)L->T * M * sizeof(int32_t));
+        L->off_costs = take((size_t)L->T * sizeof(float));
+    }
+    if (op == kOpSoft) {
+        L->off_rstore = take((size_t)rs * sizeof(float));
+        L->off_gpart = take((size_t)L->T * M * D * sizeof(float));
+        L->off_ebuf = take((size_t)h * 2 * sizeof(float));
+        L->off_pcost = take((size_t)L->T * sizeof(float));
+    }
+    L->total = off;
+    return WTS_OK;
+}
+
+int check_ws(const Layout& L, const void* ws, size_t bytes)
+{
+    if (!ws) return fail(WTS_EINVAL, "workspace is NULL");
+    if (((uintptr_t)ws & 255) != 0) return fail(WTS_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < L.total) return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, L.total);
+    return WTS_OK;
+}
+
+struct DevInfo {
+    int sms = 0;
+};
+
+int device_info(DevInfo* di)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&di->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    return WTS_OK;
+}
+
+// Reset header + progress counters, build the work list.
+int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const wts_options* opt,
+            cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.off_flags + (size_t)L.n_flags * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace header)");
+    if (L.off_flags2) {
+        e = cudaMemsetAsync(ws + L.off_flags2, 0, (size_t)L.n_flags * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace flags)");
+    }
+    SetupParams sp{};
+    sp.op = L.op;
+    sp.T = L.T;
+    sp.P = L.P;
+    sp.d = L.d;
+    sp.R = L.R;
+    sp.BR = L.BR;
+    sp.M = L.M;
+    sp.B = B;
+    sp.data = Y->data;
+    sp.offsets = Y->offsets;
+    sp.pairs = reinterpret_cast<PairDesc*>(ws + L.off_pairs);
+    sp.order = reinterpret_cast<int32_t*>(ws + L.off_order);
+    sp.prefix = reinterpret_cast<int32_t*>(ws + L.off_prefix);
+    sp.sort = (opt && opt->keep_batch_order) ? 0 : 1;
+    launch_setup(sp, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "setup kernel launch");
+    return WTS_OK;
+}
+
+int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* block)
+{
+    DevInfo di;
+    int rc = device_info(&di);
+    if (rc) return rc;
+    const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
+    *block = 32 * wpb;
+    int occ = dtw_wavefront_max_blocks_per_sm(mode, L.D, L.R, *block);
+    if (occ < 1) return fail(WTS_ECUDA, "no resident block for D=%d R=%d block=%d", L.D, L.R, *block);
+    int64_t g = (int64_t)occ * di.sms;
+    const int64_t need = (L.n_items + wpb - 1) / wpb;
+    if (g > need) g = need;
+    if (opt && opt->max_blocks && g > opt->max_blocks) g = opt->max_blocks;
+    *grid = (int)(g < 1 ? 1 : g);
+    return WTS_OK;
+}
+
+DPParams base_params(const Layout& L, char* ws)
+{
+    DPParams p{};
+    p.pairs = reinterpret_cast<const PairDesc*>(ws + L.off_pairs);
+    p.order = reinterpret_cast<const int32_t*>(ws + L.off_order);
+    p.prefix = reinterpret_cast<const int32_t*>(ws + L.off_prefix);
+    p.P = L.P;
+    p.n_items = (int)L.n_items;
+    p.d = L.d;
+    p.hdr = reinterpret_cast<WsHeader*>(ws + L.off_hdr);
+    p.flags = reinterpret_cast<int*>(ws + L.off_flags);
+    p.hbuf = reinterpret_cast<float*>(ws + L.off_hbuf);
+    p.hcnt = L.off_hcnt ? reinterpret_cast<int*>(ws + L.off_hcnt) : nullptr;
+    p.dirs = L.off_dirs ? reinterpret_cast<uint32_t*>(ws + L.off_dirs) : nullptr;
+    p.T = L.T;
+    return p;
+}
+
+int launch_dp(int mode, const Layout& L, const DPParams& p, const wts_options* opt, cudaStream_t st)
+{
+    int grid = 0, block = 0;
+    int rc = grid_for(mode, L, opt, &grid, &block);
+    if (rc) return rc;
+    cudaError_t e = launch_dtw_wavefront(mode, L.D, L.R, p, grid, block, st);
+    if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
+    return WTS_OK;
+}
+
+// Shared body of dtw_align and dba_iterate: directions + backtrack.
+int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, const wts_options* opt,
+               cudaStream_t st, float* cost, int32_t* plen, int32_t* jlo, int32_t* jhi)
+{
+    int rc = prepare(L, ws, B, Y, opt, st);
+    if (rc) return rc;
+    DPParams p = base_params(L, ws);
+    p.cost_out = cost;
+    rc = launch_dp(kModeDirs, L, p, opt, st);
+    if (rc) return rc;
+    BTParams bt{};
+    bt.pairs = p.pairs;
+    bt.P = L.P;
+    bt.R = L.R;
+    bt.dirs = p.dirs;
+    bt.jlo = jlo;
+    bt.jhi = jhi;
+    bt.plen = plen;
+    bt.M = L.M;
+    cudaError_t e = launch_backtrack(bt, st);
+    if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+    return WTS_OK;
+}
+
+}  // namespace
+}  // namespace wts
+
+using namespace wts;
+
+extern "C" {
+
+int wts_version(void) { return 100; }
+
+const char* wts_last_error(void) { return g_err.c_str(); }
+
+int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes)
+{
+    if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
+    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise};
+    if (op < 1 || op > 5) return fail(WTS_EINVAL, "unknown op %d", op);
+    Layout L;
+    int rc = compute_layout(map[op], M, Y, opt, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return ok();
+}
+
+int wts_read_status(const void* workspace, void* stream, int32_t* status)
+{
+    if (!workspace || !status) return fail(WTS_EINVAL, "NULL argument");
+    WsHeader h;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading workspace status");
+    *status = h.status == kDevTimeout ? WTS_ETIMEOUT : WTS_OK;
+    return ok();
+}
+
+int anomaly_score(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
+                  void* workspace, size_t workspace_bytes, void* stream,
+                  float* score, float* cost, int32_t* plen)
+{
+    Layout L;
+    int rc = compute_layout(kOpScore, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!B || !score) return fail(WTS_EINVAL, "B and score must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
+    DPParams p = base_params(L, ws);
+    p.cost_out = cost;
+    p.plen_out = plen;
+    p.score_out = score;
+    if ((rc = launch_dp(kModePlen, L, p, opt, st))) return rc;
+    return ok();
+}
+
+int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
+              void* workspace, size_t workspace_bytes, void* stream,
+              float* cost, int32_t* plen, int32_t* jlo, int32_t* jhi)
+{
+    Layout L;
+    int rc = compute_layout(kOpAlign, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!B || !jlo || !jhi) return fail(WTS_EINVAL, "B, jlo and jhi must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    if ((rc = align_into(L, (char*)workspace, B, Y, opt, (cudaStream_t)stream, cost, plen, jlo, jhi))) return rc;
+    return ok();
+}
+
+int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, const wts_options* opt,
+                void* workspace, size_t workspace_bytes, void* stream,
+                int32_t* counts, double* cost_before, float* cost)
+{
+    Layout L;
+    int rc = compute_layout(kOpDba, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!B_in || !B_out) return fail(WTS_EINVAL, "B_in and B_out must not be NULL");
+    if (B_in == B_out) return fail(WTS_EINVAL, "B_out must not alias B_in");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t* jlo = reinterpret_cast<int32_t*>(ws + L.off_jlo);
+    int32_t* jhi = reinterpret_cast<int32_t*>(ws + L.off_jhi);
+    float* costs = reinterpret_cast<float*>(ws + L.off_costs);
+    if ((rc = align_into(L, ws, B_in, Y, opt, st, costs, nullptr, jlo, jhi))) return rc;
+    cudaError_t e = launch_dba_average(Y->data, Y->offsets, L.T, L.d, M, jlo, jhi, costs, B_out, counts,
+                                       cost_before, st);
+    if (e != cudaSuccess) return cuda_fail(e, "averaging launch");
+    if (cost) {
+        e = cudaMemcpyAsync(cost, costs, (size_t)L.T * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cost copy");
+    }
+    return ok();
+}
+
+int wts_pairwise_dtw(const wts_batch* Y, const wts_options* opt, void* workspace, size_t workspace_bytes,
+                     void* stream, float* C)
+{
+    Layout L;
+    int rc = compute_layout(kOpPairwise, 0, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!C) return fail(WTS_EINVAL, "C must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    cudaError_t e = cudaMemsetAsync(C, 0, (size_t)L.T * L.T * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(C)");
+    if ((rc = prepare(L, ws, nullptr, Y, opt, st))) return rc;
+    DPParams p = base_params(L, ws);
+    p.cost_matrix = C;
+    if ((rc = launch_dp(kModeCost, L, p, opt, st))) return rc;
+    return ok();
+}
+
+int wts_medoid(const float* C, int32_t n, void* stream, double* sums, int32_t* index)
+{
+    if (!C || !sums || !index) return fail(WTS_EINVAL, "NULL argument");
+    if (n < 1) return fail(WTS_EINVAL, "n must be >= 1");
+    cudaError_t e = launch_medoid(C, n, index, sums, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "medoid launch");
+    return ok();
+}
+
+int wts_resample(const float* x, int64_t N, int32_t d, float* out, int64_t M, void* stream)
+{
+    if (!x || !out) return fail(WTS_EINVAL, "NULL argument");
+    if (N < 1 || M < 1 || d < 1 || d > kMaxD) return fail(WTS_EINVAL, "bad shape");
+    cudaError_t e = launch_resample(x, N, d, out, M, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resample launch");
+    return ok();
+}
+
+int wts_euclid_mean(const wts_batch* Y, int64_t M, float* out, void* stream)
+{
+    int rc = check_batch(Y, true);
+    if (rc) return rc;
+    if (!out || M < 1) return fail(WTS_EINVAL, "bad output");
+    cudaError_t e = launch_euclid_mean(Y->data, Y->offsets, Y->T, Y->d, M, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mean launch");
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// Backtrack of the tie-rule path, DBA averaging, and initial barycenters.
+#include "dba.cuh"
+
+namespace wts {
+
+namespace {
+
+constexpr int kBtWarps = 2;      // warps per backtrack CTA
+constexpr int kBtWords = 4096;   // 16 KB of direction words cached per warp
+
+// Walk the stored predecessor codes back from (M-1, N-1) to (0, 0).
+// Directions of band b live at dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]
+// for the word w of lane t at step s, and a cell (i, j) of the band sits in
+// lane t = (i mod BR) / R at step s = j + t, bits 2*(i mod 16) of word
+// (i mod R) / 16.  Along the walk s only decreases inside a band, so a window
+// of kBtWords / (32 W) steps is loaded into shared memory (coalesced) and the walk reads
+// it; every lane walks the same path (broadcast reads), lane 0 writes.
+// Row i's range is [jlo(i), jhi(i)]: jhi when the walk enters the row, jlo
+// when it leaves it (Definition "Alignment path": monotone, so each row's
+// columns are contiguous).
+template <int W>
+__global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
+{
+    constexpr int kBtWin = kBtWords / (32 * W);     // steps of one band in the window
+    __shared__ uint32_t win_all[kBtWarps][kBtWords];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    uint32_t* win = win_all[wid];
+    const int R = p.R, BR = 32 * p.R;
+    for (int q = blockIdx.x * kBtWarps + wid; q < p.P; q += gridDim.x * kBtWarps) {
+        const PairDesc pd = p.pairs[q];
+        const int N = pd.N;
+        int32_t* jlo = p.jlo + (int64_t)pd.out * p.M;
+        int32_t* jhi = p.jhi + (int64_t)pd.out * p.M;
+        int i = pd.M - 1, j = N - 1, len = 0;
+        int band = -1, wlo = 0, whi = -1;
+        if (lane == 0) jhi[i] = j;
+        for (;;) {
+            ++len;
+            if (i == 0 && j == 0) break;
+            const int b = i / BR;
+            const int t = (i - b * BR) / R;
+            const int k = i % R;
+            const int s = j + t;
+            if (b != band || s < wlo || s > whi) {
+                band = b;
+                whi = s;
+                wlo = max(0, s - kBtWin + 1);
+                const uint32_t* src = p.dirs + pd.dir_off + (int64_t)b * (N + 31) * 32 * W + (int64_t)wlo * 32 * W;
+                const int n = (whi - wlo + 1) * 32 * W;
+                __syncwarp();
+                for (int x = lane; x < n; x += 32) win[x] = __ldcs(src + x);
+                __syncwarp();
+            }
+            const uint32_t w = win[((s - wlo) * 32 + t) * W + (k >> 4)];
+            const int code = (w >> (2 * (k & 15))) & 3;
+            // a valid code matrix only moves left on row 0 and only up on
+            // column 0; anything else is reported as |pi| = -1
+            if ((i == 0 && code != 2) || (j == 0 && code != 1) || code == 3) { len = -1; break; }
+            if (code == 0) {
+                if (lane == 0) jlo[i] = j;
+                --i; --j;
+                if (lane == 0) jhi[i] = j;
+            } else if (code == 1) {
+                if (lane == 0) jlo[i] = j;
+                --i;
+                if (lane == 0) jhi[i] = j;
+            } else {
+                --j;
+            }
+        }
+        if (lane == 0) {
+            if (i == 0 && j == 0) jlo[0] = 0;
+            if (p.plen) p.plen[pd.out] = len;
+        }
+    }
+}
+
+// One thread per prototype row i; sums in double, cycles in ascending order,
+// samples in ascending order, then one division and one rounding to float.
+template <int D>
+__global__ void dba_average_kernel(const float* __restrict__ data, const int64_t* __restrict__ offsets, int T, int d,
+                                   int64_t M, const int32_t* __restrict__ jlo, const int32_t* __restrict__ jhi,
+                                   const float* __restrict__ costs, float* __restrict__ B_out,
+                                   int32_t* __restrict__ counts, double* cost_before)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) {
+        double acc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = 0.0;
+        int64_t cnt = 0;
+        for (int k = 0; k < T; ++k) {
+            const int64_t o0 = __ldg(offsets + k);
+            const int n = (int)(__ldg(offsets + k + 1) - o0);
+            // ranges come from the backtrack; clamping keeps every read inside
+            // the cycle even if a range were never written
+            const int a = max(__ldg(jlo + (int64_t)k * M + i), 0);
+            const int b = min(__ldg(jhi + (int64_t)k * M + i), n - 1);
+            const float* y = data + o0 * d;
+            for (int j = a; j <= b; ++j)
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    if (c < d) acc[c] = __dadd_rn(acc[c], (double)__ldg(y + (int64_t)j * d + c));
+            cnt += b >= a ? b - a + 1 : 0;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (c < d) B_out[i * d + c] = __double2float_rn(__ddiv_rn(acc[c], (double)(cnt > 0 ? cnt : 1)));
+        if (counts) counts[i] = (int32_t)cnt;
+    }
+    if (i == 0 && cost_before) {
+        double s = 0.0;
+        for (int k = 0; k < T; ++k) s = __dadd_rn(s, (double)costs[k]);
+        *cost_before = s;
+    }
+}
+
+// Linear resampling: p = m (N-1)/(M-1), i = floor(p), x_i + (p - i)(x_{i+1} - x_i),
+// in double with every operation rounded separately, then rounded to float.
+__device__ __forceinline__ float resample_at(const float* x, int64_t N, int d, int c, int64_t m, int64_t M)
+{
+    const double pos = M > 1 ? __ddiv_rn((double)(m * (N - 1)), (double)(M - 1)) : 0.0;
+    int64_t i = (int64_t)floor(pos);
+    if (i > N - 1) i = N - 1;
+    const double f = __dsub_rn(pos, (double)i);
+    const double xi = (double)x[i * d + c];
+    double v = xi;
+    if (i + 1 < N) v = __dadd_rn(xi, __dmul_rn(f, __dsub_rn((double)x[(i + 1) * d + c], xi)));
+    return __double2float_rn(v);
+}
+
+__global__ void resample_kernel(const float* x, int64_t N, int d, float* out, int64_t M)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < M * d) out[q] = resample_at(x, N, d, (int)(q % d), q / d, M);
+}
+
+__global__ void euclid_mean_kernel(const float* data, const int64_t* offsets, int T, int d, int64_t M, float* out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= M * d) return;
+    const int c = (int)(q % d);
+    const int64_t m = q / d;
+    double acc = 0.0;
+    for (int k = 0; k < T; ++k) {
+        const int64_t o = offsets[k];
+        acc = __dadd_rn(acc, (double)resample_at(data + o * d, offsets[k + 1] - o, d, c, m, M));
+    }
+    out[q] = __double2float_rn(__ddiv_rn(acc, (double)T));
+}
+
+// Row sums of the symmetric pairwise cost matrix in double (ascending column),
+// then the first index of the smallest sum.
+__global__ void medoid_kernel(const float* C, int T, int32_t* index_out, double* sums)
+{
+    for (int a = threadIdx.x; a < T; a += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < T; ++b) s = __dadd_rn(s, (double)C[(int64_t)a * T + b]);
+        sums[a] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int best = 0;
+        for (int a = 1; a < T; ++a)
+            if (sums[a] < sums[best]) best = a;
+        *index_out = best;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int need = (p.P + kBtWarps - 1) / kBtWarps;
+    const int grid = need < 4 * sms ? need : 4 * sms;
+    if (p.R == 16) backtrack_kernel<1><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    else if (p.R == 32) backtrack_kernel<2><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dba_average(const float* data, const int64_t* offsets, int T, int d, int64_t M,
+                               const int32_t* jlo, const int32_t* jhi, const float* costs,
+                               float* B_out, int32_t* counts, double* cost_before, cudaStream_t st)
+{
+    const int block = 128;
+    const int grid = (int)((M + block - 1) / block);
+    if (d <= 1) dba_average_kernel<1><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
+    else if (d <= 3) dba_average_kernel<3><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
+    else if (d <= 6) dba_average_kernel<6><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
+    else dba_average_kernel<16><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const float* x, int64_t N, int d, float* out, int64_t M, cudaStream_t st)
+{
+    const int64_t n = M * d;
+    resample_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, N, d, out, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euclid_mean(const float* data, const int64_t* offsets, int T, int d, int64_t M,
+                               float* out, cudaStream_t st)
+{
+    const int64_t n = M * d;
+    euclid_mean_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(data, offsets, T, d, M, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_medoid(const float* C, int T, int32_t* index_out, double* sums, cudaStream_t st)
+{
+    medoid_kernel<<<1, 256, 0, st>>>(C, T, index_out, sums);
+    return cudaGetLastError();
+}
+
+}  // namespace wts

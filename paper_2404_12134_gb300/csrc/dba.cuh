@@ -1,0 +1,33 @@
+// Backtrack, DBA averaging and barycenter initialisation kernels.
+#pragma once
+
+#include "plan.cuh"
+#include "wts_common.cuh"
+
+namespace wts {
+
+struct BTParams {
+    const PairDesc* pairs;
+    int P;
+    int R;
+    const uint32_t* dirs;
+    int32_t* jlo;        // [P][M] indexed by PairDesc::out
+    int32_t* jhi;
+    int32_t* plen;       // [P] (may be null)
+    int64_t M;           // row stride of jlo/jhi
+};
+
+cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st);
+
+// B_out[i] = mean of the cycle samples aligned to row i over all cycles;
+// counts[i] = number of aligned samples; cost_before = sum_k costs[k].
+cudaError_t launch_dba_average(const float* data, const int64_t* offsets, int T, int d, int64_t M,
+                               const int32_t* jlo, const int32_t* jhi, const float* costs,
+                               float* B_out, int32_t* counts, double* cost_before, cudaStream_t st);
+
+cudaError_t launch_resample(const float* x, int64_t N, int d, float* out, int64_t M, cudaStream_t st);
+cudaError_t launch_euclid_mean(const float* data, const int64_t* offsets, int T, int d, int64_t M,
+                               float* out, cudaStream_t st);
+cudaError_t launch_medoid(const float* C, int T, int32_t* index_out, double* sums_out, cudaStream_t st);
+
+}  // namespace wts

@@ -1,0 +1,39 @@
+// Hard-min band wavefront (DTW, Eq. 1 via Eq. 5 with gamma = 0).
+#pragma once
+
+#include "plan.cuh"
+#include "wts_common.cuh"
+
+namespace wts {
+
+enum DPMode : int {
+    kModeCost = 0,    // r(M,N) only
+    kModePlen = 1,    // r(M,N) and |pi| (cells on the tie-rule path), score = r / |pi|
+    kModeDirs = 2,    // r(M,N) and a 2-bit predecessor code per cell
+};
+
+struct DPParams {
+    const PairDesc* pairs;
+    const int32_t* order;
+    const int32_t* prefix;
+    int P;
+    int n_items;
+    int d;
+    WsHeader* hdr;
+    int* flags;          // progress counters (columns of the band's bottom row published)
+    float* hbuf;         // hand-off rows
+    int* hcnt;           // hand-off path-cell counts (kModePlen)
+    uint32_t* dirs;      // direction words (kModeDirs)
+    float* cost_out;     // [*] indexed by PairDesc::out (may be null)
+    int32_t* plen_out;   // [*] (kModePlen, may be null)
+    float* score_out;    // [*] (kModePlen, may be null)
+    float* cost_matrix;  // pairwise mode: [T][T] symmetric, written at (a,b) and (b,a) (may be null)
+    int T;               // cycles (pairwise index decode)
+    const int32_t* subset;  // pairwise subset (may be null)
+};
+
+// Launch the persistent wavefront for D (padded channels) and R (rows/lane).
+cudaError_t launch_dtw_wavefront(int mode, int D, int R, const DPParams& p, int grid, int block, cudaStream_t st);
+int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block);
+
+}  // namespace wts

@@ -1,0 +1,129 @@
+// Setup kernel: per-pair descriptors, longest-first order and item prefix.
+#include "plan.cuh"
+
+namespace wts {
+
+namespace {
+
+constexpr int kSetupThreads = 1024;
+
+// Exclusive block scan of one int64 per thread; returns the block total.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* out_excl)
+{
+    __shared__ int64_t warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;            // inclusive over warps
+    }
+    __syncthreads();
+    int64_t base = wid ? warp_tot[wid - 1] : 0;
+    *out_excl = base + x - v;
+    int64_t total = warp_tot[31];
+    __syncthreads();
+    return total;
+}
+
+__device__ void decode_pair(int p, int T, int* a, int* b)
+{
+    // pairs (a, b), a < b, enumerated a-major
+    int aa = 0, rem = p;
+    while (rem >= T - 1 - aa) { rem -= T - 1 - aa; ++aa; }
+    *a = aa;
+    *b = aa + 1 + rem;
+}
+
+__global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
+{
+    const int P = sp.P;
+    // pass 1: descriptors and storage offsets in pair order
+    int64_t run_h = 0, run_d = 0, run_r = 0, run_f = 0;
+    for (int base = 0; base < P; base += kSetupThreads) {
+        const int p = base + threadIdx.x;
+        PairDesc pd{};
+        int64_t nb = 0, h = 0, dw = 0, rs = 0;
+        if (p < P) {
+            int64_t M, N;
+            if (sp.op == kOpPairwise) {
+                int a, b;
+                decode_pair(p, sp.T, &a, &b);
+                pd.X = sp.data + sp.offsets[a] * sp.d;
+                M = sp.offsets[a + 1] - sp.offsets[a];
+                pd.Y = sp.data + sp.offsets[b] * sp.d;
+                N = sp.offsets[b + 1] - sp.offsets[b];
+            } else {
+                pd.X = sp.B;
+                M = sp.M;
+                pd.Y = sp.data + sp.offsets[p] * sp.d;
+                N = sp.offsets[p + 1] - sp.offsets[p];
+            }
+            nb = cdiv(M, sp.BR);
+            pd.M = (int32_t)M;
+            pd.N = (int32_t)N;
+            pd.nbands = (int32_t)nb;
+            pd.out = p;
+            h = pair_hbuf_floats(nb, N);
+            if (sp.op == kOpAlign || sp.op == kOpDba) dw = pair_dir_words(nb, N, sp.R);
+            if (sp.op == kOpSoft) rs = pair_rstore_floats(nb, N, sp.R);
+        }
+        int64_t eh, ed, er, ef;
+        int64_t th = block_exclusive_scan(h, &eh);
+        int64_t td = block_exclusive_scan(dw, &ed);
+        int64_t tr = block_exclusive_scan(rs, &er);
+        int64_t tf = block_exclusive_scan(nb, &ef);
+        if (p < P) {
+            pd.hbuf_off = run_h + eh;
+            pd.dir_off = run_d + ed;
+            pd.aux_off = run_r + er;
+            pd.flag_off = (int32_t)(run_f + ef);
+            sp.pairs[p] = pd;
+        }
+        run_h += th; run_d += td; run_r += tr; run_f += tf;
+    }
+    __syncthreads();
+    // pass 2: order (longest first by cells, ties by index) via rank counting
+    for (int p = threadIdx.x; p < P; p += kSetupThreads) {
+        if (!sp.sort) { sp.order[p] = p; continue; }
+        const int64_t cp = (int64_t)sp.pairs[p].M * sp.pairs[p].N;
+        int rank = 0;
+        for (int q = 0; q < P; ++q) {
+            const int64_t cq = (int64_t)sp.pairs[q].M * sp.pairs[q].N;
+            rank += (cq > cp) || (cq == cp && q < p);
+        }
+        sp.order[rank] = p;
+    }
+    __syncthreads();
+    // pass 3: item prefix in that order
+    int64_t run = 0;
+    for (int base = 0; base < P; base += kSetupThreads) {
+        const int q = base + threadIdx.x;
+        int64_t nb = q < P ? sp.pairs[sp.order[q]].nbands : 0;
+        int64_t ex;
+        int64_t tot = block_exclusive_scan(nb, &ex);
+        if (q < P) sp.prefix[q] = (int32_t)(run + ex);
+        run += tot;
+    }
+    if (threadIdx.x == 0) sp.prefix[P] = (int32_t)run;
+}
+
+}  // namespace
+
+void launch_setup(const SetupParams& sp, cudaStream_t st)
+{
+    setup_kernel<<<1, kSetupThreads, 0, st>>>(sp);
+}
+
+}  // namespace wts

@@ -1,0 +1,64 @@
+// Workspace layout and work list of one library call.
+//
+// The caller owns all device memory (inputs, outputs and one workspace
+// buffer).  The host computes the layout below from the host copy of the
+// cycle offsets; a one-CTA setup kernel rebuilds the same per-pair offsets on
+// the device, so no host-to-device copy is issued inside a call (calls can be
+// captured in a CUDA graph).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "wts_common.cuh"
+
+namespace wts {
+
+enum Op : int {
+    kOpScore = 1,      // cost + |pi| fused (anomaly_score)
+    kOpAlign = 2,      // cost + 2-bit directions + backtrack (dtw_align)
+    kOpDba = 3,        // kOpAlign + averaging (dba_iterate)
+    kOpSoft = 4,       // soft-DTW forward (R stored) + backward
+    kOpPairwise = 5,   // cost-only DTW between all cycle pairs (medoid init)
+    kOpCost = 6,       // cost only
+};
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-pair storage, shared by host sizing and the device setup kernel.
+__host__ __device__ inline int64_t pair_hbuf_floats(int64_t nb, int64_t N) { return (nb - 1) * N; }
+__host__ __device__ inline int64_t pair_dir_words(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * (R / 16); }
+__host__ __device__ inline int64_t pair_rstore_floats(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * R; }
+
+struct Layout {
+    int op = 0;
+    int T = 0;            // cycles in the batch
+    int P = 0;            // alignment problems (T, or T(T-1)/2 for pairwise)
+    int d = 0, D = 0, R = 0, BR = 0;
+    int64_t M = 0;        // prototype length (shared-prototype ops)
+    int64_t n_items = 0;  // total (pair, band) items
+    int64_t hbuf_floats = 0, dir_words = 0, rstore_floats = 0, n_flags = 0;
+    size_t off_hdr = 0, off_pairs = 0, off_order = 0, off_prefix = 0, off_flags = 0, off_flags2 = 0;
+    size_t off_hbuf = 0, off_hcnt = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0;
+    size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
+    size_t total = 0;
+};
+
+// Device-side parameters of the setup kernel.
+struct SetupParams {
+    int op;
+    int T, P, d, R, BR;
+    int64_t M;
+    const float* B;            // shared prototype (or null for pairwise)
+    const float* data;         // packed cycles
+    const int64_t* offsets;    // [T+1]
+    PairDesc* pairs;           // [P]
+    int32_t* order;            // [P] longest first
+    int32_t* prefix;           // [P+1] first item of the q-th pair in order
+    int sort;                  // 1: order longest-first, 0: identity
+};
+
+void launch_setup(const SetupParams& sp, cudaStream_t st);
+
+}  // namespace wts

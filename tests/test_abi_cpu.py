@@ -1,0 +1,94 @@
+"""The C-ABI library loads and exports every symbol include/wetsand.h declares.
+
+No compute call is made (no GPU here); only host-side sizing and argument
+validation, which the library does before touching CUDA.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2404_12134_gb300 import _abi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _abi.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "wetsand.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"anomaly_score", "dtw_align", "dba_iterate"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(_abi.EXPORTS) == names
+
+
+def test_version(lib):
+    assert lib.wts_version() >= 100
+
+
+def _batch(lengths, d=1):
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    b = _abi.wts_batch()
+    b.data = 16          # never dereferenced by host-only calls
+    b.offsets = 16
+    b.offsets_host = offs.ctypes.data
+    b.T = len(lengths)
+    b.d = d
+    return b, offs
+
+
+def _size(lib, op, M, b, opts=None):
+    n = ctypes.c_size_t(0)
+    rc = lib.wts_workspace_size(op, M, ctypes.byref(b), ctypes.byref(opts) if opts else None, ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_sizes(lib):
+    b, offs = _batch([1000, 1200, 37], d=6)
+    rc, score = _size(lib, _abi.OP_ANOMALY_SCORE, 1100, b)
+    assert rc == 0 and score > 0
+    rc, align = _size(lib, _abi.OP_DTW_ALIGN, 1100, b)
+    assert rc == 0
+    # 2-bit codes: about M*N/4 bytes per cycle plus the skew margin
+    cells = 1100 * (1000 + 1200 + 37)
+    assert cells / 4 <= align - score <= cells / 4 * 2.5
+    rc, dba = _size(lib, _abi.OP_DBA_ITERATE, 1100, b)
+    assert rc == 0 and dba > align
+
+
+def test_validation_errors(lib):
+    b, offs = _batch([10, 0, 5])
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 8, b)[0] == _abi.WTS_EINVAL
+    assert b"length" in lib.wts_last_error()
+    b, offs = _batch([10, 5], d=17)
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 8, b)[0] == _abi.WTS_EINVAL
+    b, offs = _batch([10, 5])
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 0, b)[0] == _abi.WTS_EINVAL
+    assert _size(lib, 99, 8, b)[0] == _abi.WTS_EINVAL
+    o = _abi.wts_options()
+    o.rows_per_thread = 24
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 8, b, o)[0] == _abi.WTS_EINVAL
+    b6, _ = _batch([10, 5], d=6)
+    o.rows_per_thread = 32
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 8, b6, o)[0] == _abi.WTS_EINVAL
+    bp, _ = _batch([10])
+    assert _size(lib, _abi.OP_PAIRWISE, 0, bp)[0] == _abi.WTS_EINVAL
+    # a too-small workspace is rejected before any launch
+    b, offs = _batch([10, 5])
+    rc = lib.anomaly_score(256, 8, ctypes.byref(b), None, 256, 16, None, 256, None, None)
+    assert rc == _abi.WTS_ENOMEM
+    rc = lib.dba_iterate(256, 256, 8, ctypes.byref(b), None, 256, 1 << 30, None, None, None, None)
+    assert rc == _abi.WTS_EINVAL and b"alias" in lib.wts_last_error()

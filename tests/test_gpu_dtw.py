@@ -1,0 +1,171 @@
+"""GPU parity of the hard-min path (DTW, |pi|, score, alignment ranges, DBA)
+against the CPU oracle, through the C ABI.
+
+Bar: costs, |pi|, scores, paths, counts and DBA prototypes bit-exact against
+the oracle's FP32 mirror (same tie rule, same float operation order); against
+the FP64 oracle the relative error of costs / scores is stated and held to
+1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_12134_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wts():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12134_gb300 import api, build
+    build.build()
+    return api
+
+
+def _gb(wts, data, offs):
+    return wts.Batch.from_numpy(data, offs)
+
+
+def _pack(cycles):
+    b = synth.pack(cycles)
+    return b.data, b.offsets
+
+
+def _cases():
+    rng = np.random.default_rng(101)
+    out = []
+    # ragged lengths around the 32-column chunk and the 512-row band edges
+    lens = [1, 2, 31, 32, 33, 97, 500, 1100]
+    for d in (1, 3, 6):
+        for M in (1, 5, 511, 512, 513, 1100):
+            cyc = [rng.normal(size=(n, d)).astype(np.float32) for n in lens]
+            B = rng.normal(size=(M, d)).astype(np.float32)
+            out.append((f"real-d{d}-M{M}", B, cyc))
+    # integer samples: frequent exact ties exercise the tie rule
+    for d in (1, 2):
+        cyc = [rng.integers(-2, 3, size=(n, d)).astype(np.float32) for n in (40, 77, 129, 300)]
+        B = rng.integers(-2, 3, size=(150, d)).astype(np.float32)
+        out.append((f"int-d{d}", B, cyc))
+    # odd channel counts that run zero-padded (d=5 in D=6, d=9 in D=12)
+    for d in (5, 9):
+        cyc = [rng.normal(size=(n, d)).astype(np.float32) for n in (64, 600)]
+        out.append((f"pad-d{d}", rng.normal(size=(700, d)).astype(np.float32), cyc))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_anomaly_score_bit_exact(wts, case):
+    _, B, cyc = case
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    score, cost, plen = wts.anomaly_score(torch.from_numpy(B).cuda(), gb)
+    s32, c32, L32 = oracle.score(B, data, offs, "f32")
+    assert (cost.cpu().numpy() == c32).all()
+    assert (plen.cpu().numpy() == L32).all()
+    assert (score.cpu().numpy() == s32).all()
+    s64, c64, L64 = oracle.score(B, data, offs, "f64")
+    rel = np.abs(cost.cpu().numpy() - c64) / np.maximum(np.abs(c64), 1e-30)
+    assert rel.max() <= 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("case", CASES[::2], ids=[c[0] for c in CASES[::2]])
+def test_dtw_align_paths_bit_exact(wts, case):
+    _, B, cyc = case
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    cost, plen, jlo, jhi = wts.dtw_align(torch.from_numpy(B).cuda(), gb)
+    cost, plen, jlo, jhi = (t.cpu().numpy() for t in (cost, plen, jlo, jhi))
+    for k, y in enumerate(cyc):
+        r = oracle.dtw(B, y, "f32")
+        assert cost[k] == r["cost"], k
+        assert plen[k] == r["plen"], k
+        assert (jlo[k] == r["jlo"]).all() and (jhi[k] == r["jhi"]).all(), k
+
+
+@pytest.mark.parametrize("rows,warps,order", [(16, 1, 0), (16, 8, 1), (32, 4, 0), (32, 2, 1)])
+def test_launch_variants_agree(wts, rows, warps, order):
+    rng = np.random.default_rng(102)
+    cyc = [rng.normal(size=(n, 2)).astype(np.float32) for n in (3, 700, 1500, 1031)]
+    B = rng.normal(size=(1300, 2)).astype(np.float32)
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    opts = wts.options(rows_per_thread=rows, warps_per_block=warps, keep_batch_order=order)
+    Bt = torch.from_numpy(B).cuda()
+    score, cost, plen = wts.anomaly_score(Bt, gb, opts)
+    c2, p2, jlo, jhi = wts.dtw_align(Bt, gb, opts)
+    s32, c32, L32 = oracle.score(B, data, offs, "f32")
+    assert (cost.cpu().numpy() == c32).all() and (plen.cpu().numpy() == L32).all()
+    assert (c2.cpu().numpy() == c32).all() and (p2.cpu().numpy() == L32).all()
+    r = oracle.dtw(B, cyc[2], "f32")
+    assert (jlo[2].cpu().numpy() == r["jlo"]).all() and (jhi[2].cpu().numpy() == r["jhi"]).all()
+
+
+def test_dba_iterations_bit_exact(wts):
+    """Ten DBA iterations from the medoid on workload-0-shaped cycles (scaled
+    to 0.3): every iteration's prototype, counts and cost equal the FP32
+    mirror's; the FP64 oracle's cost stays within 1e-5."""
+    b = synth.config_batch(0, scale=0.3)
+    gb = _gb(wts, b.data, b.offsets)
+    C = wts.pairwise_dtw(gb)
+    idx, sums = wts.medoid(C)
+    k0, C_or = oracle.medoid(b.data, b.offsets)
+    assert (C.cpu().numpy() == C_or).all()
+    assert int(idx) == k0
+    B = b.cycle(k0).copy()
+    Bg = torch.from_numpy(B).cuda()
+    for it in range(10):
+        Bn, cnt, cb, ck = wts.dba_iterate(Bg, gb)
+        Bo, cnt_o, cb_o, ck_o = oracle.dba_iterate(B, b.data, b.offsets, "f32")
+        assert (Bn.cpu().numpy() == Bo).all(), it
+        assert (cnt.cpu().numpy() == cnt_o).all(), it
+        assert float(cb) == cb_o, it
+        assert (ck.cpu().numpy() == ck_o).all(), it
+        B, Bg = Bo, Bn
+    assert wts.read_status(wts._default_ws[torch.cuda.current_device()].buf) == 0
+
+
+def test_dba_fixed_point(wts):
+    rng = np.random.default_rng(103)
+    x = rng.normal(size=(777, 3)).astype(np.float32)
+    data, offs = _pack([x, x, x, x])
+    Bn, cnt, cb, ck = wts.dba_iterate(torch.from_numpy(x).cuda(), _gb(wts, data, offs))
+    assert (Bn.cpu().numpy() == x).all() and float(cb) == 0.0 and (cnt.cpu().numpy() == 4).all()
+
+
+def test_init_helpers_bit_exact(wts):
+    b = synth.config_batch(2, scale=0.05)
+    gb = _gb(wts, b.data, b.offsets)
+    for M in (1, 7, 500, 1001):
+        got = wts.euclid_mean(gb, M).cpu().numpy()
+        assert (got == oracle.euclid_mean(b.data, b.offsets, M)).all(), M
+        x = b.cycle(3)
+        got = wts.resample(torch.from_numpy(x).cuda(), M).cpu().numpy()
+        assert (got == oracle.resample(x, M)).all(), M
+
+
+def test_full_size_sampled_pair(wts):
+    """Full workload-1 shape (d = 6, M = 25,000, cycles 20k-30k) in the same
+    launch configuration as the benchmark: one pair checked cell-for-cell on
+    its path against the oracle, the others by path properties."""
+    b = synth.config_batch(1, T=3)
+    gb = _gb(wts, b.data, b.offsets)
+    B = synth.clean_prototype(b, synth.PROTO_LEN[1])
+    cost, plen, jlo, jhi = wts.dtw_align(torch.from_numpy(B).cuda(), gb)
+    cost, plen, jlo, jhi = (t.cpu().numpy() for t in (cost, plen, jlo, jhi))
+    r = oracle.dtw(B, b.cycle(1), "f32", path=False)
+    assert cost[1] == r["cost"] and plen[1] == r["plen"]
+    assert (jlo[1] == r["jlo"]).all() and (jhi[1] == r["jhi"]).all()
+    for k in range(3):
+        N = b.lengths[k]
+        assert jlo[k, 0] == 0 and jhi[k, -1] == N - 1
+        assert ((jlo[k, 1:] == jhi[k, :-1]) | (jlo[k, 1:] == jhi[k, :-1] + 1)).all()
+        assert int((jhi[k] - jlo[k] + 1).sum()) == plen[k]
+    s, c, L = wts.anomaly_score(torch.from_numpy(B).cuda(), gb)
+    assert (c.cpu().numpy() == cost).all() and (L.cpu().numpy() == plen).all()
