@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the WETSAND alignment hot path on one GB300 (or N replicas).
+
+Workload (the batched-DBA configuration): 200 synthetic cycles, 6 channels,
+FP32, pre-gap lengths U(20k, 30k) with 2 % gaps removed, 10 % anomalous,
+prototype length M = 25,000 (initialised, untimed, from the medoid of a seeded
+16-cycle subset resampled to M).  One step = one DBA iteration: the DTW
+wavefront with 2-bit predecessor codes over all 200 pairs, the backtrack and
+the averaging.  The metric is DTW cells per second (GCUPS, M * sum N_k cells
+per step) and seconds per DBA iteration; soft-DTW forward + backward GCUPS
+and anomaly-score GCUPS are reported beside it.
+
+--impl reference times the CPU oracle (the plain C implementation the tests
+check against) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2404_12134_gb300 import synth  # noqa: E402
+
+M_PROTO = synth.PROTO_LEN[1]
+WORKLOAD = ("batched DBA: 200 cycles x 6 ch FP32, pre-gap N ~ U(20k,30k), 2% gaps, "
+            "10% anomalous, M=25000, one DBA iteration per step")
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wetsand", choices=["wetsand", "reference"])
+    ap.add_argument("--T", type=int, default=200, help="cycles (default: the full workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_workload(T: int):
+    b = synth.config_batch(1, T=T)
+    rng = np.random.default_rng(synth.SEED_BASE + 77)
+    subset = np.sort(rng.choice(b.T, size=min(16, b.T), replace=False))
+    return b, subset
+
+
+# --- clocks ---------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --- CPU oracle timing (baseline and reference arm) ---------------------------
+
+def oracle_dba_sample(b, B, n_cycles: int, prec: str = "f64"):
+    """Time one oracle DBA iteration on the first n_cycles cycles; returns (GCUPS, seconds, cells)."""
+    import oracle
+    sub = b.subset(np.arange(n_cycles))
+    cells = int(B.shape[0]) * int(sub.lengths.sum())
+    t0 = time.perf_counter()
+    oracle.dba_iterate(B.astype(np.float64) if prec == "f64" else B, sub.data, sub.offsets, prec)
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, dt, cells
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    import oracle
+    oracle.build()
+    b, subset = make_workload(args.T)
+    B = synth.clean_prototype(b, M_PROTO)      # the oracle's step cost does not depend on B's values
+    n = min(ncores, b.T)
+    for _ in range(args.warmup):
+        oracle_dba_sample(b, B, n)
+    tot_t, tot_c = 0.0, 0
+    for _ in range(args.steps):
+        g, dt, cells = oracle_dba_sample(b, B, n)
+        tot_t += dt; tot_c += cells
+    val = tot_c / tot_t / 1e9
+    sample = f"{n} of {b.T} cycles per step (one oracle DBA iteration, FP64, M={M_PROTO}), {ncores} OpenMP threads"
+    print(json.dumps({
+        "impl": "reference", "metric": "dtw_gcups_dba_iteration", "value": val, "unit": "GCUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": b.T, "d": b.d, "M": M_PROTO},
+        "cpu_baseline": {"value": val, "unit": "GCUPS", "cores": ncores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+# --- GPU arm ----------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2404_12134_gb300 import api, build
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    b, subset = make_workload(args.T)
+    cells = M_PROTO * int(b.lengths.sum())
+    gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
+
+    # initial prototype (untimed): medoid of a seeded 16-cycle subset, resampled to M
+    sub = b.subset(subset)
+    gsub = api.Batch.from_numpy(sub.data, sub.offsets, device=dev)
+    C = api.pairwise_dtw(gsub)
+    idx, _ = api.medoid(C)
+    k = int(idx)
+    B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M_PROTO)
+    del C, gsub
+
+    ws = api.Workspace(dev)
+    B = B0.clone()
+    Bn = torch.empty_like(B)
+    counts = torch.empty(M_PROTO, dtype=torch.int32, device=dev)
+    cb = torch.empty((), dtype=torch.float64, device=dev)
+    cost = torch.empty(b.T, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        nonlocal B, Bn
+        api.dba_iterate(B, gb, ws=ws, B_out=Bn, counts=counts, cost_before=cb, cost=cost)
+        B, Bn = Bn, B
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else None
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id)
+    time.sleep(0.5)
+    api.profile_read("")                  # drop earlier records
+    api.profile_enable(True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    barrier()
+    api.profile_enable(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    wf_ms, wf_n = api.profile_read("wavefront")
+    bt_ms, bt_n = api.profile_read("backtrack")
+    av_ms, av_n = api.profile_read("dba_average")
+    rest_ms, rest_n = api.profile_read("")
+    launches = wf_n + bt_n + av_n + rest_n
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = api.read_status(ws.buf)
+    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+    dba_cost = float(cb.item())
+
+    out = {
+        "metric": "dtw_gcups_dba_iteration", "value": value, "unit": "GCUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": b.T, "d": b.d, "M": M_PROTO, "cells_per_step": cells,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "no flush: each step writes ~31 GB of predecessor codes (>> 129 MB L2)"},
+        "s_per_dba_iter": ms / args.steps * 1e-3,
+        "dba_cost_after_warmup_and_steps": dba_cost,
+        "device_status": status,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # roofline of the dominant kernel: the wavefront (2-bit code mode).  Work per
+    # cell = 2d + 3 FP32 ops (d subtractions, d fused multiply-adds, two mins,
+    # one add); peak = SMs x 128 FP32 lanes x max SM clock.
+    d = b.d
+    wf_avg_s = wf_ms / max(wf_n, 1) * 1e-3
+    ops = cells * (2 * d + 3)
+    peak = sms * FP32_LANES_PER_SM * 2.070e9 / 1e12
+    achieved = ops / wf_avg_s / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s (FP32 lane ops)",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "dtw_wavefront_kernel<D=6,R=16,dirs>",
+                       "peak_note": f"{sms} SMs x 128 FP32 lanes x 2070 MHz (max SM clock)"}
+    out["kernel_ms_per_step"] = {"wavefront": wf_ms / args.steps, "backtrack": bt_ms / args.steps,
+                                 "dba_average": av_ms / args.steps, "other": rest_ms / args.steps}
+    out["dp_only_gcups"] = cells / wf_avg_s / 1e9
+
+    # end to end through the C ABI with host buffers: pinned host -> device
+    # copy of the cycles and prototype, the iteration, device -> host of the
+    # new prototype and the cost, every step inside the timed region
+    h_data = torch.from_numpy(b.data).pin_memory()
+    h_B = B.cpu().pin_memory()
+    h_out = torch.empty_like(h_B).pin_memory()
+    h_cost = torch.empty((), dtype=torch.float64).pin_memory()
+    d_data = torch.empty_like(gb.data)
+    gb_e2e = api.Batch(d_data, gb.offsets, gb.offsets_host)
+    d_B = torch.empty_like(B)
+    n_e2e = max(2, min(args.steps, 3))
+
+    def e2e_step():
+        d_data.copy_(h_data, non_blocking=True)
+        d_B.copy_(h_B, non_blocking=True)
+        api.dba_iterate(d_B, gb_e2e, ws=ws, B_out=Bn, counts=counts, cost_before=cb, cost=cost)
+        h_out.copy_(Bn, non_blocking=True)
+        h_cost.copy_(cb, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    out["e2e"] = {"value": world * cells * n_e2e / e2e_s / 1e9, "unit": "GCUPS",
+                  "h2d_bytes_per_step": int(h_data.numel() * 4 + h_B.numel() * 4),
+                  "d2h_bytes_per_step": int(h_out.numel() * 4 + 8), "steps": n_e2e}
+    del d_data, gb_e2e
+
+    if not args.no_extras:
+        # anomaly score on the same batch against the current prototype (|pi| fused)
+        api.anomaly_score(B, gb, ws=ws)
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(st)
+        api.anomaly_score(B, gb, ws=ws)
+        s1.record(st)
+        barrier()
+        out["anomaly_score_gcups"] = cells / (s0.elapsed_time(s1) * 1e-3) / 1e9
+
+    if rank == 0 and not args.no_cpu_baseline:
+        ncores = os.cpu_count() or 1
+        os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+        n = min(ncores, b.T)
+        g, dt, c = oracle_dba_sample(b, B.cpu().numpy(), n)
+        out["cpu_baseline"] = {"value": g, "unit": "GCUPS", "cores": ncores, "kind": "oracle",
+                               "sample": f"{n} of {b.T} cycles, one oracle DBA iteration (FP64), "
+                                         f"{dt:.1f} s wall on {ncores} threads"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -93,6 +93,17 @@ int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options*
  * (0 = ok, WTS_ETIMEOUT = an in-kernel wait gave up) into *status (host). */
 int wts_read_status(const void* workspace, void* stream, int32_t* status);
 
+/* Kernel timing for measurement: while enabled, every kernel the library
+ * launches is bracketed by a pair of CUDA events recorded on the launching
+ * stream (library-owned events, created per launch).  Host-only switch. */
+int wts_profile_enable(int enable);
+
+/* Sum of the recorded durations (ms) and launch count of one kernel
+ * ("setup", "wavefront", "backtrack", "dba_average", "softdtw_fwd",
+ * "softdtw_bwd", "softdtw_grad"; "" = all), then forget those records.
+ * Waits for the recorded events to complete. */
+int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches);
+
 /*
  * anomaly_score - similarity score of Eq. 8 (Sec. 3.4):
  *     d_score(B, C_k) = DTW(B, C_k) / |pi_k|,

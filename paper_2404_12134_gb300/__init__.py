@@ -10,7 +10,7 @@ from __future__ import annotations
 
 _API_NAMES = {
     "Batch", "Workspace", "options", "workspace_size", "read_status", "anomaly_score", "dtw_align",
-    "dba_iterate", "pairwise_dtw", "medoid", "resample", "euclid_mean",
+    "dba_iterate", "pairwise_dtw", "medoid", "resample", "euclid_mean", "profile_enable", "profile_read",
 }
 
 

@@ -117,6 +117,19 @@ def read_status(buf: torch.Tensor) -> int:
     return s.value
 
 
+def profile_enable(enable: bool = True):
+    """Record CUDA events around every library kernel launch (measurement)."""
+    check(_abi.load().wts_profile_enable(1 if enable else 0))
+
+
+def profile_read(kernel: str = ""):
+    """(total ms, launches) of the recorded launches of one kernel ("" = all)."""
+    ms = ctypes.c_double(0)
+    n = ctypes.c_int32(0)
+    check(_abi.load().wts_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
 def _check_B(B: torch.Tensor, d: int) -> torch.Tensor:
     if B.dim() == 1:
         B = B[:, None]

@@ -2,7 +2,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/wetsand.h"
 #include "dba.cuh"
@@ -35,6 +37,36 @@ int cuda_fail(cudaError_t e, const char* what)
 {
     return fail(WTS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+// Opt-in kernel timing: a CUDA event pair recorded on the launching stream
+// around every kernel launch while enabled; read (and cleared) per kernel.
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof = false;
+std::vector<ProfRec> g_recs;
+
+struct Prof {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t st;
+    const char* name;
+    Prof(const char* n, cudaStream_t s) : st(s), name(n)
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        if (!g_prof) return;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { a = b = nullptr; return; }
+        cudaEventRecord(a, st);
+    }
+    ~Prof()
+    {
+        if (!a) return;
+        cudaEventRecord(b, st);
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        g_recs.push_back({name, a, b});
+    }
+};
 
 int pick_D(int d)
 {
@@ -196,7 +228,10 @@ int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const
     sp.order = reinterpret_cast<int32_t*>(ws + L.off_order);
     sp.prefix = reinterpret_cast<int32_t*>(ws + L.off_prefix);
     sp.sort = (opt && opt->keep_batch_order) ? 0 : 1;
-    launch_setup(sp, st);
+    {
+        Prof pr("setup", st);
+        launch_setup(sp, st);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "setup kernel launch");
     return WTS_OK;
@@ -242,7 +277,11 @@ int launch_dp(int mode, const Layout& L, const DPParams& p, const wts_options* o
     int grid = 0, block = 0;
     int rc = grid_for(mode, L, opt, &grid, &block);
     if (rc) return rc;
-    cudaError_t e = launch_dtw_wavefront(mode, L.D, L.R, p, grid, block, st);
+    cudaError_t e;
+    {
+        Prof pr("wavefront", st);
+        e = launch_dtw_wavefront(mode, L.D, L.R, p, grid, block, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
     return WTS_OK;
 }
@@ -266,7 +305,11 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
     bt.jhi = jhi;
     bt.plen = plen;
     bt.M = L.M;
-    cudaError_t e = launch_backtrack(bt, st);
+    cudaError_t e;
+    {
+        Prof pr("backtrack", st);
+        e = launch_backtrack(bt, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
     return WTS_OK;
 }
@@ -281,6 +324,39 @@ extern "C" {
 int wts_version(void) { return 100; }
 
 const char* wts_last_error(void) { return g_err.c_str(); }
+
+int wts_profile_enable(int enable)
+{
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof = enable != 0;
+    return ok();
+}
+
+int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches)
+{
+    if (!kernel || !total_ms || !launches) return fail(WTS_EINVAL, "NULL argument");
+    std::vector<ProfRec> mine;
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        std::vector<ProfRec> keep;
+        for (auto& r : g_recs) (r.name == kernel || kernel[0] == 0 ? mine : keep).push_back(r);
+        g_recs.swap(keep);
+    }
+    double tot = 0;
+    int err = WTS_OK;
+    for (auto& r : mine) {
+        float ms = 0;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess && err == WTS_OK) err = cuda_fail(e, "reading kernel events");
+        tot += ms;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    *total_ms = tot;
+    *launches = (int32_t)mine.size();
+    return err ? err : ok();
+}
 
 int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes)
 {
@@ -358,8 +434,11 @@ int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, 
     int32_t* jhi = reinterpret_cast<int32_t*>(ws + L.off_jhi);
     float* costs = reinterpret_cast<float*>(ws + L.off_costs);
     if ((rc = align_into(L, ws, B_in, Y, opt, st, costs, nullptr, jlo, jhi))) return rc;
-    cudaError_t e = launch_dba_average(Y->data, Y->offsets, L.T, L.d, M, jlo, jhi, costs, B_out, counts,
-                                       cost_before, st);
+    cudaError_t e;
+    {
+        Prof pr("dba_average", st);
+        e = launch_dba_average(Y->data, Y->offsets, L.T, L.d, M, jlo, jhi, costs, B_out, counts, cost_before, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "averaging launch");
     if (cost) {
         e = cudaMemcpyAsync(cost, costs, (size_t)L.T * sizeof(float), cudaMemcpyDeviceToDevice, st);
