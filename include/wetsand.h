@@ -186,6 +186,32 @@ int wts_resample(const float* x, int64_t N, int32_t d, float* out, int64_t M, vo
  */
 int wts_euclid_mean(const wts_batch* Y, int64_t M, float* out, void* stream);
 
+/*
+ * anomaly_score_noalloc - anomaly_score without a caller workspace.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory - code that runs inside a host whose device
+ * memory is owned and budgeted by another allocator, or a scoring loop that
+ * must not stall (cudaMalloc and cudaFree can synchronise the device and take
+ * unbounded time).  It computes exactly what anomaly_score computes, with the
+ * same inputs and outputs (all caller-owned device pointers), but its scratch
+ * is a fixed 32 MiB array inside the library: every GPU that loads the library
+ * holds those 32 MiB until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *  - A batch whose scratch need (the WTS_OP_ANOMALY_SCORE workspace size)
+ *    exceeds 32 MiB is rejected with WTS_ENOMEM before anything is launched;
+ *    for M = 25,000 and d > 2 that is about two 30,000-sample cycles per call.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents; each
+ *    call clears what must start at zero.  Calls whose work overlaps on the
+ *    GPU (other streams, other host threads, without ordering between them)
+ *    race on the array: serialise them.
+ *  - The device status word of this scratch is not readable by the caller.
+ */
+int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
+                          void* stream, float* score, float* cost, int32_t* plen);
+
 #ifdef __cplusplus
 }
 #endif

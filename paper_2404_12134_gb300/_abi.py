@@ -20,7 +20,7 @@ EXPORTS = (
     "wts_version", "wts_last_error", "wts_workspace_size", "wts_read_status",
     "wts_profile_enable", "wts_profile_read",
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
-    "wts_resample", "wts_euclid_mean",
+    "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
 )
 
 
@@ -71,6 +71,7 @@ _SIGS = {
     "wts_medoid": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),
+    "anomaly_score_noalloc": ([VP, I64, PB, PO, VP, VP, VP, VP], ctypes.c_int),
 }
 
 

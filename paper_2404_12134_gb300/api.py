@@ -154,6 +154,22 @@ def anomaly_score(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None
     return score, cost, plen
 
 
+def anomaly_score_noalloc(B: torch.Tensor, batch: Batch, opts=None):
+    """anomaly_score for callers that cannot allocate device memory: the
+    library's fixed 32 MiB scratch replaces the workspace (small batches only;
+    calls must not overlap on the GPU).  Outputs are allocated here by torch
+    only for convenience; a C caller passes its own."""
+    B = _check_B(B, batch.d)
+    M = B.shape[0]
+    dev = B.device
+    score = torch.empty(batch.T, dtype=torch.float32, device=dev)
+    cost = torch.empty(batch.T, dtype=torch.float32, device=dev)
+    plen = torch.empty(batch.T, dtype=torch.int32, device=dev)
+    check(_abi.load().anomaly_score_noalloc(B.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts), _stream(),
+                                            score.data_ptr(), cost.data_ptr(), plen.data_ptr()))
+    return score, cost, plen
+
+
 def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None):
     """DTW and tie-rule path per cycle: (cost [T], plen [T], jlo [T, M], jhi [T, M])."""
     B = _check_B(B, batch.d)

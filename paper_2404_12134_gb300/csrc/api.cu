@@ -496,3 +496,72 @@ int wts_euclid_mean(const wts_batch* Y, int64_t M, float* out, void* stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// anomaly_score_noalloc: the same score with a fixed, library-owned scratch
+// area instead of a caller workspace, for callers that cannot allocate device
+// memory (see include/wetsand.h).  The scratch is a file-scope __device__
+// array, so it exists on every GPU that loads this library, until exit.
+// ---------------------------------------------------------------------------
+namespace wts {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char wts_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(WTS_EINVAL, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, wts_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return WTS_OK;
+}
+
+}  // namespace
+}  // namespace wts
+
+extern "C" int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
+                                     void* stream, float* score, float* cost, int32_t* plen)
+{
+    using namespace wts;
+    Layout L;
+    int rc = compute_layout(kOpScore, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!B || !score) return fail(WTS_EINVAL, "B and score must not be NULL");
+    if (L.total > kNoAllocScratchBytes)
+        return fail(WTS_ENOMEM,
+                    "anomaly_score_noalloc: this batch needs %zu bytes of scratch but the fixed scratch holds %zu; "
+                    "score fewer or shorter cycles per call, or use anomaly_score with a workspace",
+                    L.total, kNoAllocScratchBytes);
+    void* scratch = nullptr;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)scratch;
+    // prepare() zeroes the header and progress counters left by the previous call
+    if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
+    DPParams p = base_params(L, ws);
+    p.cost_out = cost;
+    p.plen_out = plen;
+    p.score_out = score;
+    if ((rc = launch_dp(kModePlen, L, p, opt, st))) return rc;
+    return ok();
+}
