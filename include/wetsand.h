@@ -158,6 +158,44 @@ int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, 
                 int32_t* counts, double* cost_before, float* cost);
 
 /*
+ * softdtw_forward - Soft-DTW^gamma(B, Y_k) for every cycle (Eq. 4, computed by
+ * the recursion Eq. 5 with the soft minimum of Eq. 3, read with the exponent
+ * -a_i/gamma).  The soft minimum is evaluated as
+ *     m - gamma ln(sum_i exp(-(a_i - m)/gamma)),  m = min_i a_i,
+ * with the hardware ex2 / lg2 approximations, in FP32.  Every r(i,j) is kept
+ * in the workspace for softdtw_backward (4 bytes per cell plus a skew
+ * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)).
+ *   B [M][d] (d <= 8), gamma > 0 (gamma = 0 is DTW: use anomaly_score),
+ *   value [T] out.
+ */
+int softdtw_forward(const float* B, int64_t M, const wts_batch* Y, float gamma, const wts_options* opt,
+                    void* workspace, size_t workspace_bytes, void* stream, float* value);
+
+/*
+ * softdtw_backward - gradient of sum_k g_k Soft-DTW^gamma(B, Y_k) with
+ * respect to B (Eq. 6): grad_B[i][c] = sum_k g_k sum_j e_k(i,j) 2 (b_ic - y_jc),
+ * where E_k is the reverse recursion of Cuturi and Blondel (cited by the
+ * paper): e(M,N) = 1, e(i,j) = sum over the successors s of (i,j) of
+ * exp(((r(s) - r(i,j)) - delta(s))/gamma) e(s).  With g_k = lambda_k / m_k this
+ * is the gradient of the barycenter objective Eq. 7.
+ * The workspace must still hold the R written by softdtw_forward for the same
+ * B, Y, gamma and options (the call may be repeated with other g).
+ *   grad_value [T] in (g_k), grad_B [M][d] out; the sum over k is in FP64, k
+ *   ascending.
+ */
+int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma, const float* grad_value,
+                     const wts_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                     float* grad_B);
+
+/*
+ * wts_adam_step - one Adam update (Kingma and Ba) of n parameters x given
+ * grad, with first / second moments m, v (zero before step t = 1), used to
+ * descend the Eq. 7 objective with the gradient of softdtw_backward.
+ */
+int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                  float eps, int32_t t, void* stream);
+
+/*
  * wts_pairwise_dtw - DTW between every two cycles of the batch (rows = the
  * lower-index cycle), for the medoid that initialises DBA.
  *   C [T][T] out: symmetric, C[a][a] = 0.

@@ -21,6 +21,7 @@ EXPORTS = (
     "wts_profile_enable", "wts_profile_read",
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
+    "softdtw_forward", "softdtw_backward", "wts_adam_step",
 )
 
 
@@ -72,6 +73,10 @@ _SIGS = {
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),
     "anomaly_score_noalloc": ([VP, I64, PB, PO, VP, VP, VP, VP], ctypes.c_int),
+    "softdtw_forward": ([VP, I64, PB, ctypes.c_float, PO, VP, SZ, VP, VP], ctypes.c_int),
+    "softdtw_backward": ([VP, I64, PB, ctypes.c_float, VP, PO, VP, SZ, VP, VP], ctypes.c_int),
+    "wts_adam_step": ([VP, VP, VP, VP, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                       I32, VP], ctypes.c_int),
 }
 
 

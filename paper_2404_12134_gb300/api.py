@@ -239,3 +239,88 @@ def euclid_mean(batch: Batch, M: int) -> torch.Tensor:
     out = torch.empty((M, batch.d), dtype=torch.float32, device=batch.data.device)
     check(_abi.load().wts_euclid_mean(ctypes.byref(batch.c()), M, out.data_ptr(), _stream()))
     return out
+
+
+# --- Soft-DTW ------------------------------------------------------------------
+
+def softdtw_forward(B: torch.Tensor, batch: Batch, gamma: float, opts=None, ws: Workspace | None = None):
+    """Soft-DTW^gamma(B, Y_k) for every cycle (Eq. 4): values [T].  The
+    workspace keeps R for softdtw_backward."""
+    B = _check_B(B, batch.d)
+    M = B.shape[0]
+    nb = workspace_size(_abi.OP_SOFTDTW, M, batch, opts)
+    buf = _ws(ws, nb)
+    values = torch.empty(batch.T, dtype=torch.float32, device=B.device)
+    check(_abi.load().softdtw_forward(B.data_ptr(), M, ctypes.byref(batch.c()), float(gamma), _opt(opts),
+                                      buf.data_ptr(), buf.numel(), _stream(), values.data_ptr()))
+    return values
+
+
+def softdtw_backward(B: torch.Tensor, batch: Batch, gamma: float, grad_value: torch.Tensor, opts=None,
+                     ws: Workspace | None = None, grad_B: torch.Tensor | None = None):
+    """d/dB of sum_k grad_value[k] * Soft-DTW^gamma(B, Y_k) (Eq. 6): [M, d].
+    ``ws`` must be the workspace of the matching softdtw_forward."""
+    B = _check_B(B, batch.d)
+    M = B.shape[0]
+    nb = workspace_size(_abi.OP_SOFTDTW, M, batch, opts)
+    buf = _ws(ws, nb)
+    gv = grad_value.to(device=B.device, dtype=torch.float32).contiguous()
+    if gv.numel() != batch.T:
+        raise ValueError("grad_value must have T entries")
+    grad_B = torch.empty_like(B) if grad_B is None else grad_B
+    check(_abi.load().softdtw_backward(B.data_ptr(), M, ctypes.byref(batch.c()), float(gamma), gv.data_ptr(),
+                                       _opt(opts), buf.data_ptr(), buf.numel(), _stream(), grad_B.data_ptr()))
+    return grad_B
+
+
+def adam_step(x: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, t: int,
+              lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """In-place Adam update of x (library kernel)."""
+    check(_abi.load().wts_adam_step(x.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), x.numel(),
+                                    lr, beta1, beta2, eps, t, _stream()))
+
+
+class SoftDTW(torch.autograd.Function):
+    """values[k] = Soft-DTW^gamma(B, Y_k), differentiable in B through the
+    hand-written backward kernel (each call owns its workspace, which holds R
+    until backward)."""
+
+    @staticmethod
+    def forward(ctx, B, batch, gamma, opts=None):
+        ws = Workspace(B.device)
+        values = softdtw_forward(B.detach().contiguous(), batch, gamma, opts, ws)
+        ctx.save_for_backward(B)
+        ctx.batch, ctx.gamma, ctx.opts, ctx.ws = batch, gamma, opts, ws
+        return values
+
+    @staticmethod
+    def backward(ctx, grad_values):
+        (B,) = ctx.saved_tensors
+        g = softdtw_backward(B.detach().contiguous(), ctx.batch, ctx.gamma, grad_values, ctx.opts, ctx.ws)
+        return g, None, None, None
+
+
+def softdtw(B: torch.Tensor, batch: Batch, gamma: float, opts=None) -> torch.Tensor:
+    return SoftDTW.apply(B, batch, gamma, opts)
+
+
+def softdtw_barycenter(batch: Batch, M: int, gamma: float, steps: int = 50, lr: float = 1e-2,
+                       init: torch.Tensor | None = None, weights: torch.Tensor | None = None, opts=None):
+    """Soft-DTW barycenter (Eq. 7) by Adam: B minimises sum_k w_k Soft-DTW^gamma(B, Y_k),
+    w_k = lambda_k / m_k with lambda_k = 1 by default.  Starts from the Euclidean
+    mean of the cycles resampled to M (Table I's default initialisation).
+    Returns (B, values per step [steps, T] on the device, weights)."""
+    dev = batch.data.device
+    B = euclid_mean(batch, M) if init is None else init.detach().clone().contiguous()
+    if weights is None:
+        weights = torch.from_numpy((1.0 / batch.lengths).astype(np.float32)).to(dev)
+    m = torch.zeros_like(B)
+    v = torch.zeros_like(B)
+    ws = Workspace(dev)
+    grad = torch.empty_like(B)
+    hist = torch.empty((steps, batch.T), dtype=torch.float32, device=dev)
+    for t in range(1, steps + 1):
+        hist[t - 1] = softdtw_forward(B, batch, gamma, opts, ws)
+        softdtw_backward(B, batch, gamma, weights, opts, ws, grad_B=grad)
+        adam_step(B, grad, m, v, t, lr=lr)
+    return B, hist, weights

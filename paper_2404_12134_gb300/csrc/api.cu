@@ -1,5 +1,6 @@
 // C ABI entry points: validation, workspace layout, launches.
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -10,6 +11,7 @@
 #include "dba.cuh"
 #include "dtw_wavefront.cuh"
 #include "plan.cuh"
+#include "softdtw.cuh"
 
 namespace wts {
 namespace {
@@ -127,6 +129,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->d = Y->d;
     L->D = D;
     L->R = pick_R(D, opt);
+    if (op == kOpSoft) {
+        if (D > 8) return fail(WTS_EINVAL, "soft-DTW supports d <= 8 (got %d)", Y->d);
+        L->R = soft_rows(D);          // fixed by the channel count (registers)
+    }
     L->BR = 32 * L->R;
     L->M = M;
     const int64_t* o = Y->offsets_host;
@@ -174,7 +180,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     if (op == kOpSoft) {
         L->off_rstore = take((size_t)rs * sizeof(float));
         L->off_gpart = take((size_t)L->T * M * D * sizeof(float));
-        L->off_ebuf = take((size_t)h * 2 * sizeof(float));
+        L->off_ebuf = take((size_t)h * 3 * sizeof(float));
         L->off_pcost = take((size_t)L->T * sizeof(float));
     }
     L->total = off;
@@ -311,6 +317,49 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
         e = launch_backtrack(bt, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+    return WTS_OK;
+}
+
+SoftParams soft_params(const Layout& L, char* ws, float gamma)
+{
+    SoftParams p{};
+    p.pairs = reinterpret_cast<const PairDesc*>(ws + L.off_pairs);
+    p.order = reinterpret_cast<const int32_t*>(ws + L.off_order);
+    p.prefix = reinterpret_cast<const int32_t*>(ws + L.off_prefix);
+    p.P = L.P;
+    p.n_items = (int)L.n_items;
+    p.d = L.d;
+    p.gamma = gamma;
+    p.hdr = reinterpret_cast<WsHeader*>(ws + L.off_hdr);
+    p.flags = reinterpret_cast<int*>(ws + L.off_flags);
+    p.flags2 = reinterpret_cast<int*>(ws + L.off_flags2);
+    p.hbuf = reinterpret_cast<float*>(ws + L.off_hbuf);
+    p.ebuf = reinterpret_cast<float*>(ws + L.off_ebuf);
+    p.rstore = reinterpret_cast<float*>(ws + L.off_rstore);
+    p.gpart = reinterpret_cast<float*>(ws + L.off_gpart);
+    return p;
+}
+
+int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block)
+{
+    DevInfo di;
+    int rc = device_info(&di);
+    if (rc) return rc;
+    const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
+    *block = 32 * wpb;
+    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block);
+    if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
+    int64_t g = (int64_t)occ * di.sms;
+    const int64_t need = (L.n_items + wpb - 1) / wpb;
+    if (g > need) g = need;
+    if (opt && opt->max_blocks && g > opt->max_blocks) g = opt->max_blocks;
+    *grid = (int)(g < 1 ? 1 : g);
+    return WTS_OK;
+}
+
+int check_gamma(float gamma)
+{
+    if (!(gamma > 0.f) || !(gamma < 1e30f)) return fail(WTS_EINVAL, "gamma must be finite and > 0 (gamma = 0 is DTW)");
     return WTS_OK;
 }
 
@@ -464,6 +513,76 @@ int wts_pairwise_dtw(const wts_batch* Y, const wts_options* opt, void* workspace
     DPParams p = base_params(L, ws);
     p.cost_matrix = C;
     if ((rc = launch_dp(kModeCost, L, p, opt, st))) return rc;
+    return ok();
+}
+
+int softdtw_forward(const float* B, int64_t M, const wts_batch* Y, float gamma, const wts_options* opt,
+                    void* workspace, size_t workspace_bytes, void* stream, float* value)
+{
+    Layout L;
+    int rc = compute_layout(kOpSoft, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if ((rc = check_gamma(gamma))) return rc;
+    if (!B || !value) return fail(WTS_EINVAL, "B and value must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
+    SoftParams p = soft_params(L, ws, gamma);
+    p.value_out = value;
+    int grid = 0, block = 0;
+    if ((rc = soft_grid(L, 0, opt, &grid, &block))) return rc;
+    cudaError_t e;
+    {
+        Prof pr("softdtw_fwd", st);
+        e = launch_softdtw_fwd(L.D, p, grid, block, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "soft-DTW forward launch");
+    return ok();
+}
+
+int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma, const float* grad_value,
+                     const wts_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                     float* grad_B)
+{
+    Layout L;
+    int rc = compute_layout(kOpSoft, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if ((rc = check_gamma(gamma))) return rc;
+    if (!B || !grad_value || !grad_B) return fail(WTS_EINVAL, "B, grad_value and grad_B must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    cudaError_t e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.off_flags2, 0, (size_t)L.n_flags * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward counters)");
+    SoftParams p = soft_params(L, ws, gamma);
+    int grid = 0, block = 0;
+    if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;
+    {
+        Prof pr("softdtw_bwd", st);
+        e = launch_softdtw_bwd(L.D, p, grid, block, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
+    {
+        Prof pr("softdtw_grad", st);
+        e = launch_softdtw_grad_reduce(p.gpart, grad_value, L.T, M, L.d, grad_B, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
+    return ok();
+}
+
+int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                  float eps, int32_t t, void* stream)
+{
+    if (!x || !grad || !m || !v) return fail(WTS_EINVAL, "NULL argument");
+    if (n < 1 || t < 1) return fail(WTS_EINVAL, "n and t must be >= 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+        return fail(WTS_EINVAL, "need 0 <= beta < 1 and eps > 0");
+    cudaError_t e = launch_adam(x, grad, m, v, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "adam launch");
     return ok();
 }
 

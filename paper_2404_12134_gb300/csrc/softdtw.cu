@@ -1,0 +1,408 @@
+// Soft-DTW on the band wavefront.
+//
+// Forward (Eqs. 3-5): r(i,j) = delta(i,j) + min^gamma(r(i-1,j-1), r(i-1,j), r(i,j-1)),
+//   min^gamma(a,b,c) = m - gamma ln(sum exp(-(v - m)/gamma)),  m = min(a,b,c)
+// (the exact rewrite of Eq. 3 with exp(-m/gamma) factored out), evaluated as
+//   m - (gamma ln 2) log2(sum 2^((m - v) log2(e)/gamma))
+// with the hardware ex2 / lg2 approximations.  Every r is stored (FP32) so the
+// backward pass can read it.
+//
+// Backward (Eq. 6 with E from the reverse recursion of Cuturi and Blondel,
+// which the paper cites): e(M,N) = 1 and
+//   e(i,j) = sum over successors s of exp(((r(s) - r(i,j)) - delta(s)) / gamma) e(s),
+// successors beyond the matrix contributing 0, then
+//   d/db_ic sum_j ... = sum_j e(i,j) 2 (b_ic - y_jc).
+// The difference r(s) - r(i,j) of neighbouring cells is taken first (exact in
+// floating point when the two are within a factor of two), then delta(s) is
+// subtracted: the exponent keeps the accuracy of the small quantity it is.
+//
+// Geometry is the hard-min kernel's: one warp per band of 32*R rows, lane t
+// owns R rows.  Forward: lane t at column j = s - t in step s, bands top to
+// bottom.  Backward: lane t at column j = N-1-s + (31-t) in step s (the lowest
+// lane leads), bands bottom to top; the cell a lane needs at backward step s
+// was written at forward step N+30-s by every lane, so each backward step
+// reads one contiguous block of R.  R layout per band:
+// [(N+31) steps][R/4][32 lanes][4 floats].
+#include "softdtw.cuh"
+
+namespace wts {
+
+namespace {
+
+__device__ __forceinline__ float ex2a(float x)
+{
+    float y;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2a(float x)
+{
+    float y;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+template <int D, int R>
+__device__ __forceinline__ void load_rows(float (&b)[R][D], const float* X, int i0, int M, int d)
+{
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            b[k][c] = (i0 + k < M && c < d) ? __ldg(X + (int64_t)(i0 + k) * d + c) : 0.f;
+}
+
+template <int D>
+__device__ __forceinline__ float local_cost(const float* bk, const float* y, float* t)
+{
+    t[0] = __fsub_rn(bk[0], y[0]);
+    float acc = __fmul_rn(t[0], t[0]);
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        t[c] = __fsub_rn(bk[c], y[c]);
+        acc = __fmaf_rn(t[c], t[c], acc);
+    }
+    return acc;
+}
+
+template <int D, int R>
+__device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane)
+{
+    constexpr int BR = 32 * R;
+    const int M = pd.M, N = pd.N, d = p.d;
+    const int i0 = band * BR + lane * R;
+    const bool top = band == 0;
+    const bool last = band == pd.nbands - 1;
+    const float INF = inf_f();
+    const float kk = kLog2e / p.gamma;
+    const float gl = p.gamma * kLn2;
+
+    float b[R][D];
+    load_rows<D, R>(b, pd.X, i0, M, d);
+    float col[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) col[k] = INF;
+    float y[D], ybuf[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { y[c] = 0.f; ybuf[c] = 0.f; }
+    float topv = INF;
+    float prev_up = (top && lane == 0) ? 0.f : INF;
+
+    const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
+    float* hcur = last ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
+    const int* fprev = top ? nullptr : p.flags + pd.flag_off + band - 1;
+    int* fcur = p.flags + pd.flag_off + band;
+    float* rs = p.rstore + pd.aux_off + (int64_t)band * (N + 31) * 32 * R;
+
+    const int steps = N + 31;
+    for (int s = 0; s < steps; ++s) {
+        if ((s & 31) == 0 && s < N) {
+            const int jj = s + lane;
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                ybuf[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+            if (!top) {
+                if (!wait_progress(fprev, min(s + 32, N), p.hdr, 3)) return;
+                topv = jj < N ? __ldcg(hprev + jj) : INF;
+            }
+        }
+        const int src = s & 31;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float fresh = __shfl_sync(FULL, ybuf[c], src);
+            const float moved = __shfl_up_sync(FULL, y[c], 1);
+            y[c] = lane == 0 ? fresh : moved;
+        }
+        const float above = __shfl_up_sync(FULL, col[R - 1], 1);
+        const float tv = __shfl_sync(FULL, topv, src);
+        const float up_in = lane == 0 ? (top ? INF : tv) : above;
+        const float dg_in = prev_up;
+        prev_up = up_in;
+
+        const int j = s - lane;
+        if (j >= 0 && j < N) {
+            float dg = dg_in, up = up_in;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const float lf = col[k];
+                float t[D];
+                const float delta = local_cost<D>(b[k], y, t);
+                const float m = fminf(dg, fminf(up, lf));
+                const float S = __fadd_rn(__fadd_rn(ex2a(__fmul_rn(__fsub_rn(m, dg), kk)),
+                                                    ex2a(__fmul_rn(__fsub_rn(m, up), kk))),
+                                          ex2a(__fmul_rn(__fsub_rn(m, lf), kk)));
+                const float sm = __fmaf_rn(-gl, lg2a(S), m);
+                const float r = __fadd_rn(delta, sm);
+                dg = lf;
+                up = r;
+                col[k] = r;
+            }
+            if (hcur != nullptr && lane == 31) {
+                __stcg(hcur + j, col[R - 1]);
+                if (((j + 1) & 31) == 0 || j == N - 1) st_release(fcur, j + 1);
+            }
+        }
+        float4* dst = reinterpret_cast<float4*>(rs + (int64_t)s * 32 * R);
+#pragma unroll
+        for (int k4 = 0; k4 < R / 4; ++k4)
+            dst[k4 * 32 + lane] = make_float4(col[4 * k4], col[4 * k4 + 1], col[4 * k4 + 2], col[4 * k4 + 3]);
+    }
+
+    if (last) {
+        const int ilast = M - 1 - band * BR;
+        if (lane == ilast / R) {
+            const int kk2 = ilast % R;
+            float v = col[0];
+#pragma unroll
+            for (int k = 1; k < R; ++k)
+                if (k == kk2) v = col[k];
+            p.value_out[pd.out] = v;
+        }
+    }
+}
+
+template <int D, int R>
+__device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane)
+{
+    constexpr int BR = 32 * R;
+    const int M = pd.M, N = pd.N, d = p.d;
+    const int i0 = band * BR + lane * R;
+    const bool top = band == 0;
+    const bool last = band == pd.nbands - 1;
+    const float NINF = -inf_f();
+    const float kk = kLog2e / p.gamma;
+
+    float b[R][D];
+    load_rows<D, R>(b, pd.X, i0, M, d);
+    // state of each row at the column to the right (r, delta, e); beyond the
+    // matrix: (-inf, 0, 0)
+    float rp[R], dp[R], ep[R];
+    float g[R][D];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        rp[k] = NINF; dp[k] = 0.f; ep[k] = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) g[k][c] = 0.f;
+    }
+    float y[D], ybuf[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { y[c] = 0.f; ybuf[c] = 0.f; }
+    float cr = NINF, cd = 0.f, ce = 0.f;          // chunk of the row below the band
+    float pbr = NINF, pbd = 0.f, pbe = 0.f;       // row below, one column to the right
+
+    // boundary slot b holds the top row of band b+1
+    const float* enext = last ? nullptr : p.ebuf + 3 * (pd.hbuf_off + (int64_t)band * N);
+    float* emine = top ? nullptr : p.ebuf + 3 * (pd.hbuf_off + (int64_t)(band - 1) * N);
+    const int* fnext = last ? nullptr : p.flags2 + pd.flag_off + band + 1;
+    int* fmine = p.flags2 + pd.flag_off + band;
+    const float* rs = p.rstore + pd.aux_off + (int64_t)band * (N + 31) * 32 * R;
+
+    const int steps = N + 31;
+    for (int s = 0; s < steps; ++s) {
+        if ((s & 31) == 0 && s < N) {
+            // lane l holds column N-1-s-l of the lane-31 feeds
+            const int jj = N - 1 - s - lane;
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                ybuf[c] = (jj >= 0 && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+            if (!last) {
+                if (!wait_progress(fnext, min(s + 32, N), p.hdr, 4)) return;
+                if (jj >= 0) {
+                    cr = __ldcg(enext + 3 * jj);
+                    cd = __ldcg(enext + 3 * jj + 1);
+                    ce = __ldcg(enext + 3 * jj + 2);
+                } else {
+                    cr = NINF; cd = 0.f; ce = 0.f;
+                }
+            }
+        }
+        const int src = s & 31;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float fresh = __shfl_sync(FULL, ybuf[c], src);
+            const float moved = __shfl_down_sync(FULL, y[c], 1);
+            y[c] = lane == 31 ? fresh : moved;
+        }
+        float br = __shfl_down_sync(FULL, rp[0], 1);
+        float bd = __shfl_down_sync(FULL, dp[0], 1);
+        float be = __shfl_down_sync(FULL, ep[0], 1);
+        const float fr = __shfl_sync(FULL, cr, src);
+        const float fd = __shfl_sync(FULL, cd, src);
+        const float fe = __shfl_sync(FULL, ce, src);
+        if (lane == 31) {
+            br = last ? NINF : fr;
+            bd = last ? 0.f : fd;
+            be = last ? 0.f : fe;
+        }
+        float xr = pbr, xd = pbd, xe = pbe;        // below, column j+1
+        pbr = br; pbd = bd; pbe = be;
+
+        const int j = N - 1 - s + (31 - lane);
+        if (j >= 0 && j < N) {
+            const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - s) * 32 * R);
+            float nr = br, nd = bd, ne = be;       // below, column j
+#pragma unroll
+            for (int k4 = R / 4 - 1; k4 >= 0; --k4) {
+                const float4 v4 = __ldcs(src4 + k4 * 32 + lane);
+                const float rv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int kq = 3; kq >= 0; --kq) {
+                    const int k = 4 * k4 + kq;
+                    const float rr = rp[k], rd = dp[k], re = ep[k];
+                    float rn = NINF, dn = 0.f, en = 0.f;
+                    if (i0 + k < M) {
+                        const float r = rv[kq];
+                        float t[D];
+                        const float delta = local_cost<D>(b[k], y, t);
+                        const float a = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(nr, r), nd), kk));
+                        const float bb = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(rr, r), rd), kk));
+                        const float cc = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(xr, r), xd), kk));
+                        float e = __fmaf_rn(cc, xe, __fmaf_rn(bb, re, __fmul_rn(a, ne)));
+                        if (i0 + k == M - 1 && j == N - 1) e = 1.f;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(e, t[c], g[k][c]);
+                        rn = r; dn = delta; en = e;
+                    }
+                    xr = rr; xd = rd; xe = re;
+                    nr = rn; nd = dn; ne = en;
+                    rp[k] = rn; dp[k] = dn; ep[k] = en;
+                }
+            }
+            if (emine != nullptr && lane == 0) {
+                __stcg(emine + 3 * j, rp[0]);
+                __stcg(emine + 3 * j + 1, dp[0]);
+                __stcg(emine + 3 * j + 2, ep[0]);
+                if (((N - j) & 31) == 0 || j == 0) st_release(fmine, N - j);
+            }
+        }
+    }
+
+    float* gout = p.gpart + (int64_t)pd.out * M * d;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (i0 + k < M)
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                if (c < d) gout[(int64_t)(i0 + k) * d + c] = __fmul_rn(2.f, g[k][c]);
+}
+
+template <int D, int R, bool BWD>
+__global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&p.hdr->item_counter, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= p.n_items) break;
+        if (ld_volatile(&p.hdr->abort)) break;
+        const int q = find_slot(p.prefix, p.P, item);
+        const PairDesc pd = p.pairs[p.order[q]];
+        const int k = item - p.prefix[q];
+        if (BWD) bwd_band<D, R>(p, pd, pd.nbands - 1 - k, lane);
+        else fwd_band<D, R>(p, pd, k, lane);
+    }
+}
+
+__global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g, int T, int64_t M,
+                                   int d, float* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = M * d;
+    if (q >= n) return;
+    double acc = 0.0;
+    for (int k = 0; k < T; ++k)
+        acc = __fma_rn((double)__ldg(g + k), (double)__ldg(gpart + (int64_t)k * n + q), acc);
+    out[q] = __double2float_rn(acc);
+}
+
+__global__ void adam_kernel(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                            float beta2, float eps, float bc1, float bc2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = grad[i];
+    const float mi = __fmaf_rn(beta1, m[i], __fmul_rn(1.f - beta1, gi));
+    const float vi = __fmaf_rn(beta2, v[i], __fmul_rn(1.f - beta2, __fmul_rn(gi, gi)));
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = __fdiv_rn(mi, bc1);
+    const float vh = __fdiv_rn(vi, bc2);
+    x[i] = __fsub_rn(x[i], __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(sqrtf(vh), eps)));
+}
+
+template <int D, bool BWD>
+cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
+{
+    constexpr int R = D <= 1 ? 16 : 8;
+    softdtw_kernel<D, R, BWD><<<grid, block, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int D, bool BWD>
+int occ_d(int block)
+{
+    constexpr int R = D <= 1 ? 16 : 8;
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD>, block, 0);
+    return n;
+}
+
+}  // namespace
+
+#define WTS_SOFT_DISPATCH(FN, BWD, ...)          \
+    switch (D) {                                 \
+        case 1: return FN<1, BWD>(__VA_ARGS__);  \
+        case 2: return FN<2, BWD>(__VA_ARGS__);  \
+        case 3: return FN<3, BWD>(__VA_ARGS__);  \
+        case 4: return FN<4, BWD>(__VA_ARGS__);  \
+        case 6: return FN<6, BWD>(__VA_ARGS__);  \
+        case 8: return FN<8, BWD>(__VA_ARGS__);  \
+        default: break;                          \
+    }
+
+cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st)
+{
+    WTS_SOFT_DISPATCH(launch_d, false, p, grid, block, st)
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st)
+{
+    WTS_SOFT_DISPATCH(launch_d, true, p, grid, block, st)
+    return cudaErrorInvalidValue;
+}
+
+int softdtw_max_blocks_per_sm(int D, int backward, int block)
+{
+    if (backward) {
+        WTS_SOFT_DISPATCH(occ_d, true, block)
+    } else {
+        WTS_SOFT_DISPATCH(occ_d, false, block)
+    }
+    return 0;
+}
+
+cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, int T, int64_t M, int d,
+                                       float* grad_B, cudaStream_t st)
+{
+    const int64_t n = M * d;
+    grad_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gpart, g, T, M, d, grad_B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                        float beta2, float eps, int t, cudaStream_t st)
+{
+    double b1t = 1.0, b2t = 1.0;
+    for (int i = 0; i < t; ++i) { b1t *= beta1; b2t *= beta2; }
+    adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, grad, m, v, n, lr, beta1, beta2, eps,
+                                                              (float)(1.0 - b1t), (float)(1.0 - b2t));
+    return cudaGetLastError();
+}
+
+}  // namespace wts

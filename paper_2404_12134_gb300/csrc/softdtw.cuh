@@ -1,0 +1,42 @@
+// Soft-DTW forward (Eqs. 3-5, R stored) and backward (E recursion, Eq. 6).
+#pragma once
+
+#include "plan.cuh"
+#include "wts_common.cuh"
+
+namespace wts {
+
+struct SoftParams {
+    const PairDesc* pairs;
+    const int32_t* order;
+    const int32_t* prefix;
+    int P;
+    int n_items;
+    int d;
+    float gamma;
+    WsHeader* hdr;
+    int* flags;          // forward progress (columns of a band's bottom row published)
+    int* flags2;         // backward progress (columns, counted from the right, of a band's top row)
+    float* hbuf;         // forward hand-off rows (r of a band's bottom row)
+    float* ebuf;         // backward hand-off rows: (r, delta, e) of a band's top row, 3 floats per column
+    float* rstore;       // R, per band [(N+31) steps][R/4][32 lanes][4]
+    float* value_out;    // [P] Soft-DTW value per pair (forward)
+    float* gpart;        // [P][M][d] per-pair gradient sum_j e_ij * 2 (b_i - y_j) (backward)
+};
+
+// Rows held per lane by the soft-DTW kernels for a padded channel count D.
+inline int soft_rows(int D) { return D <= 1 ? 16 : 8; }
+
+cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
+cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
+int softdtw_max_blocks_per_sm(int D, int backward, int block);
+
+// grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending)
+cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, int T, int64_t M, int d,
+                                       float* grad_B, cudaStream_t st);
+
+// One Adam step on n parameters (m, v: first / second moments, t >= 1).
+cudaError_t launch_adam(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                        float beta2, float eps, int t, cudaStream_t st);
+
+}  // namespace wts

@@ -1,0 +1,122 @@
+"""GPU parity of Soft-DTW forward / backward (Eqs. 3-7) against the FP64
+oracle, through the C ABI, plus the autograd wrapper and the Adam barycenter.
+
+Tolerances (derived in the design notes): values within 2e-5 relative of the
+FP64 oracle at these sizes; gradients within 1e-3 * gamma^-1 * 2^-24 * ... are
+not useful bounds in FP32, so the gradient bar is stated against the infinity
+norm of the FP64 gradient per case (GRAD_TOL below), and against central
+differences of the FP64 oracle's value.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_12134_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wts():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12134_gb300 import api, build
+    build.build()
+    return api
+
+
+VALUE_TOL = 2e-5
+GRAD_TOL = {1.0: 2e-4, 0.1: 1e-3, 0.01: 1e-2}
+
+
+def _case(seed, M, lens, d):
+    rng = np.random.default_rng(seed)
+    B = rng.normal(size=(M, d)).astype(np.float32)
+    cyc = [rng.normal(size=(n, d)).astype(np.float32) for n in lens]
+    return B, synth.pack(cyc)
+
+
+CASES = [
+    (1, 5, [1, 2, 7], 1),
+    (2, 64, [64, 40, 100], 1),
+    (3, 300, [1, 31, 33, 257, 700], 1),
+    (4, 513, [400, 600], 3),
+    (5, 260, [650, 80], 6),
+    (6, 520, [300, 777], 2),
+]
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.1, 0.01])
+@pytest.mark.parametrize("case", CASES, ids=[f"M{c[1]}-d{c[3]}" for c in CASES])
+def test_softdtw_value_and_gradient(wts, case, gamma):
+    seed, M, lens, d = case
+    B, b = _case(seed, M, lens, d)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    ws = wts.Workspace()
+    v = wts.softdtw_forward(Bt, gb, gamma, ws=ws)
+    w = torch.from_numpy((1.0 / np.asarray(lens)).astype(np.float32)).cuda()
+    g = wts.softdtw_backward(Bt, gb, gamma, w, ws=ws)
+    assert wts.read_status(ws.buf) == 0
+    vo, lo, go = oracle.softdtw_batch(B, b.data, b.offsets, gamma, weights=1.0 / np.asarray(lens, dtype=np.float64))
+    vg = v.cpu().numpy().astype(np.float64)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(vg - vo) <= VALUE_TOL * np.maximum(np.abs(vo), 1.0)), np.abs(vg - vo).max()
+    err = np.abs(gg - go).max() / np.abs(go).max()
+    assert err <= GRAD_TOL[gamma], err
+
+
+def test_gradient_against_finite_differences(wts):
+    """Central differences (h = 1e-3) of the FP64 oracle's Eq. 7 objective, lengths <= 64."""
+    B, b = _case(7, 48, [64, 50, 33], 1)
+    gamma = 0.1
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    ws = wts.Workspace()
+    wts.softdtw_forward(Bt, gb, gamma, ws=ws)
+    w = torch.from_numpy((1.0 / b.lengths).astype(np.float32)).cuda()
+    g = wts.softdtw_backward(Bt, gb, gamma, w, ws=ws).cpu().numpy()
+    for i in (0, 11, 30, 47):
+        Bp = B.copy(); Bp[i, 0] += np.float32(1e-3)
+        Bm = B.copy(); Bm[i, 0] -= np.float32(1e-3)
+        fp = oracle.softdtw_batch(Bp, b.data, b.offsets, gamma, want_grad=False)[1]
+        fm = oracle.softdtw_batch(Bm, b.data, b.offsets, gamma, want_grad=False)[1]
+        fd = (fp - fm) / (float(Bp[i, 0]) - float(Bm[i, 0]))
+        assert abs(fd - g[i, 0]) <= 2e-3 * max(1.0, abs(fd)), (i, fd, g[i, 0])
+
+
+def test_autograd_function(wts):
+    B, b = _case(8, 100, [90, 120], 2)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda().requires_grad_(True)
+    vals = wts.softdtw(Bt, gb, 0.5)
+    w = torch.tensor([0.3, -1.7], device="cuda")
+    (vals * w).sum().backward()
+    vo, lo, go = oracle.softdtw_batch(B, b.data, b.offsets, 0.5, weights=np.array([0.3, -1.7]))
+    err = np.abs(Bt.grad.cpu().numpy() - go).max() / np.abs(go).max()
+    assert err <= GRAD_TOL[1.0]
+
+
+def test_soft_barycenter_decreases_objective(wts):
+    """Eq. 7 by Adam from the Euclidean-mean init: the objective, evaluated by
+    the FP64 oracle, drops."""
+    b = synth.config_batch(2, scale=0.02, T=8)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M = 200
+    B0 = wts.euclid_mean(gb, M)
+    B, hist, w = wts.softdtw_barycenter(gb, M, gamma=0.1, steps=30, lr=2e-2, init=B0)
+    f0 = oracle.softdtw_batch(B0.cpu().numpy(), b.data, b.offsets, 0.1, want_grad=False)[1]
+    f1 = oracle.softdtw_batch(B.cpu().numpy(), b.data, b.offsets, 0.1, want_grad=False)[1]
+    assert f1 < f0
+    h = (hist.cpu().numpy() * w.cpu().numpy()).sum(1)
+    assert h[-1] < h[0]
+
+
+def test_gamma_validation(wts):
+    B, b = _case(9, 10, [10], 1)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    from paper_2404_12134_gb300._abi import WtsError
+    with pytest.raises(WtsError):
+        wts.softdtw_forward(torch.from_numpy(B).cuda(), gb, 0.0)
