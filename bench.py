@@ -156,6 +156,53 @@ def run_reference(args):
 
 # --- GPU arm ----------------------------------------------------------------------
 
+def hbm_peak_gbs() -> float:
+    """Measured HBM copy bandwidth (generated file), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0):
+    """Soft-DTW forward + backward on the single-channel barycenter workload:
+    64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB)."""
+    sb = synth.config_batch(2)
+    M = synth.PROTO_LEN[2]
+    gb = api.Batch.from_numpy(sb.data, sb.offsets, device=dev)
+    B = api.euclid_mean(gb, M)
+    w = torch.from_numpy((1.0 / sb.lengths).astype(np.float32)).to(dev)
+    ws = api.Workspace(dev)
+    grad = torch.empty_like(B)
+    for _ in range(2):
+        api.softdtw_forward(B, gb, gamma, ws=ws)
+        api.softdtw_backward(B, gb, gamma, w, ws=ws, grad_B=grad)
+    barrier()
+    api.profile_read("")
+    api.profile_enable(True)
+    reps = 3
+    for _ in range(reps):
+        vals = api.softdtw_forward(B, gb, gamma, ws=ws)
+        api.softdtw_backward(B, gb, gamma, w, ws=ws, grad_B=grad)
+    barrier()
+    api.profile_enable(False)
+    f_ms, _ = api.profile_read("softdtw_fwd")
+    b_ms, _ = api.profile_read("softdtw_bwd")
+    g_ms, _ = api.profile_read("softdtw_grad")
+    api.profile_read("")
+    cells = M * int(sb.lengths.sum())
+    fwd, bwd = f_ms / reps, (b_ms + g_ms) / reps
+    res = {"workload": "64 cycles x 1 ch FP32, pre-gap N ~ U(8k,12k), 2% gaps, M=10000, Euclidean-mean init",
+           "gamma": gamma, "cells": cells, "fwd_ms": fwd, "bwd_ms": bwd,
+           "fwd_bwd_gcups": cells / ((fwd + bwd) * 1e-3) / 1e9,
+           "fwd_gcups": cells / (fwd * 1e-3) / 1e9, "bwd_gcups": cells / (bwd * 1e-3) / 1e9,
+           "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf),
+           "loss": float((vals * w).sum())}
+    del ws, gb
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -313,6 +360,28 @@ def run_gpu(args):
         s1.record(st)
         barrier()
         out["anomaly_score_gcups"] = cells / (s0.elapsed_time(s1) * 1e-3) / 1e9
+
+    if not args.no_extras:
+        out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
+        out["measured_peaks_probe"] = {k: api.peak_probe(i) / 1e12 for i, k in
+                                       enumerate(("fp32_fma_tops", "fp32_minmax_tops", "mufu_ex2_tops",
+                                                  "mufu_lg2_tops"))}
+        ex2 = out["measured_peaks_probe"]["mufu_ex2_tops"] * 1e12
+        lg2 = out["measured_peaks_probe"]["mufu_lg2_tops"] * 1e12
+        sd = out["softdtw"]
+        cells_s = sd["cells"]
+        t_mufu = cells_s * (3 / ex2 + 1 / lg2) + cells_s * 3 / ex2          # fwd: 3 ex2 + 1 lg2, bwd: 3 ex2
+        t_hbm = cells_s * 8 / (hbm_peak_gbs() * 1e9)                        # R: 4 B written + 4 B read
+        t = (sd["fwd_ms"] + sd["bwd_ms"]) * 1e-3
+        if t_mufu >= t_hbm:
+            sd["roofline"] = {"bound": "mufu", "achieved": cells_s * 10 / t / 1e12,
+                              "peak": cells_s * 10 / t_mufu / 1e12, "unit": "TOP/s (MUFU ex2+lg2, 7 ex2 + 1 lg2 per cell)",
+                              "frac": t_mufu / t, "traffic": None}
+        else:
+            sd["roofline"] = {"bound": "hbm", "achieved": cells_s * 8 / t / 1e9, "peak": hbm_peak_gbs(),
+                              "unit": "GB/s", "frac": t_hbm / t, "traffic": None}
+        sd["hbm_lower_bound_ms"] = t_hbm * 1e3
+        sd["mufu_lower_bound_ms"] = t_mufu * 1e3
 
     if rank == 0 and not args.no_cpu_baseline:
         ncores = os.cpu_count() or 1

@@ -104,6 +104,12 @@ int wts_profile_enable(int enable);
  * Waits for the recorded events to complete. */
 int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches);
 
+/* Measured roofline denominators (not part of the method): lane operations
+ * per second of the whole GPU for which = 0 FP32 fused multiply-add, 1 FP32
+ * min / max, 2 MUFU ex2.approx, 3 MUFU lg2.approx; best of
+ * four timed launches.  Synchronises the device. */
+int wts_peak_probe(int which, double* ops_per_s);
+
 /*
  * anomaly_score - similarity score of Eq. 8 (Sec. 3.4):
  *     d_score(B, C_k) = DTW(B, C_k) / |pi_k|,

@@ -18,7 +18,7 @@ OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE = 1, 2, 
 # every symbol declared in include/wetsand.h
 EXPORTS = (
     "wts_version", "wts_last_error", "wts_workspace_size", "wts_read_status",
-    "wts_profile_enable", "wts_profile_read",
+    "wts_profile_enable", "wts_profile_read", "wts_peak_probe",
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
     "softdtw_forward", "softdtw_backward", "wts_adam_step",
@@ -64,6 +64,7 @@ _SIGS = {
     "wts_workspace_size": ([ctypes.c_int, I64, PB, PO, ctypes.POINTER(SZ)], ctypes.c_int),
     "wts_read_status": ([VP, VP, ctypes.POINTER(I32)], ctypes.c_int),
     "wts_profile_enable": ([ctypes.c_int], ctypes.c_int),
+    "wts_peak_probe": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "wts_profile_read": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)], ctypes.c_int),
     "anomaly_score": ([VP, I64, PB, PO, VP, SZ, VP, VP, VP, VP], ctypes.c_int),
     "dtw_align": ([VP, I64, PB, PO, VP, SZ, VP, VP, VP, VP, VP], ctypes.c_int),

@@ -130,6 +130,13 @@ def profile_read(kernel: str = ""):
     return ms.value, n.value
 
 
+def peak_probe(which: int) -> float:
+    """Measured lane-ops/s: 0 FP32 FMA, 1 FP32 min, 2 MUFU ex2, 3 MUFU lg2."""
+    v = ctypes.c_double(0)
+    check(_abi.load().wts_peak_probe(which, ctypes.byref(v)))
+    return v.value
+
+
 def _check_B(B: torch.Tensor, d: int) -> torch.Tensor:
     if B.dim() == 1:
         B = B[:, None]

@@ -14,6 +14,7 @@
 #include "softdtw.cuh"
 
 namespace wts {
+int run_probe(int which, double* ops_per_s);
 namespace {
 
 thread_local std::string g_err;
@@ -405,6 +406,13 @@ int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches)
     *total_ms = tot;
     *launches = (int32_t)mine.size();
     return err ? err : ok();
+}
+
+int wts_peak_probe(int which, double* ops_per_s)
+{
+    if (!ops_per_s || which < 0 || which > 3) return fail(WTS_EINVAL, "which must be 0..3");
+    if (run_probe(which, ops_per_s)) return fail(WTS_ECUDA, "probe kernel failed");
+    return ok();
 }
 
 int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes)

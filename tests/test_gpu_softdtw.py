@@ -1,11 +1,16 @@
-"""GPU parity of Soft-DTW forward / backward (Eqs. 3-7) against the FP64
-oracle, through the C ABI, plus the autograd wrapper and the Adam barycenter.
+"""GPU parity of Soft-DTW forward / backward (Eqs. 3-7) against the oracle,
+through the C ABI, plus the autograd wrapper and the Adam barycenter.
 
-Tolerances (derived in the design notes): values within 2e-5 relative of the
-FP64 oracle at these sizes; gradients within 1e-3 * gamma^-1 * 2^-24 * ... are
-not useful bounds in FP32, so the gradient bar is stated against the infinity
-norm of the FP64 gradient per case (GRAD_TOL below), and against central
-differences of the FP64 oracle's value.
+Tolerances, derived from the arithmetic:
+* values: within 2e-5 of the FP64 oracle, relative to max(|value|, 1)
+  (FP32 rounding of r along a path of M+N cells plus the ex2 / lg2
+  approximation errors, ~1e-7 per cell);
+* gradients: the exponent of every weight exp(((r(s) - r) - delta(s))/gamma)
+  carries the FP32 rounding of r, of order ulp(r)/gamma, so no fixed relative
+  bound holds at small gamma or large r.  The bar is that the kernel adds
+  nothing beyond that: its error against the FP64 oracle (infinity norm,
+  relative) is at most twice that of the same recursion evaluated in plain
+  FP32 by the oracle's FP32 mode, plus 1e-5.
 """
 import numpy as np
 import pytest
@@ -28,7 +33,12 @@ def wts():
 
 
 VALUE_TOL = 2e-5
-GRAD_TOL = {1.0: 2e-4, 0.1: 1e-3, 0.01: 1e-2}
+
+
+def _grad_bar(B, b, gamma, weights, go):
+    """Twice the relative error of a plain FP32 evaluation, plus 1e-5."""
+    g32 = oracle.softdtw_batch(B, b.data, b.offsets, gamma, weights=weights.astype(np.float32), prec="f32")[2]
+    return 2.0 * np.abs(g32.astype(np.float64) - go).max() / np.abs(go).max() + 1e-5
 
 
 def _case(seed, M, lens, d):
@@ -65,7 +75,7 @@ def test_softdtw_value_and_gradient(wts, case, gamma):
     gg = g.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(vg - vo) <= VALUE_TOL * np.maximum(np.abs(vo), 1.0)), np.abs(vg - vo).max()
     err = np.abs(gg - go).max() / np.abs(go).max()
-    assert err <= GRAD_TOL[gamma], err
+    assert err <= _grad_bar(B, b, gamma, 1.0 / np.asarray(lens, dtype=np.float64), go), err
 
 
 def test_gradient_against_finite_differences(wts):
@@ -96,7 +106,7 @@ def test_autograd_function(wts):
     (vals * w).sum().backward()
     vo, lo, go = oracle.softdtw_batch(B, b.data, b.offsets, 0.5, weights=np.array([0.3, -1.7]))
     err = np.abs(Bt.grad.cpu().numpy() - go).max() / np.abs(go).max()
-    assert err <= GRAD_TOL[1.0]
+    assert err <= _grad_bar(B, b, 0.5, np.array([0.3, -1.7]), go)
 
 
 def test_soft_barycenter_decreases_objective(wts):
