@@ -365,7 +365,7 @@ def run_gpu(args):
         out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
         out["measured_peaks_probe"] = {k: api.peak_probe(i) / 1e12 for i, k in
                                        enumerate(("fp32_fma_tops", "fp32_minmax_tops", "mufu_ex2_tops",
-                                                  "mufu_lg2_tops"))}
+                                                  "mufu_lg2_tops", "fp32x2_fma_tops", "fp32_min3_tops"))}
         ex2 = out["measured_peaks_probe"]["mufu_ex2_tops"] * 1e12
         lg2 = out["measured_peaks_probe"]["mufu_lg2_tops"] * 1e12
         sd = out["softdtw"]

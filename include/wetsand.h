@@ -73,7 +73,7 @@ typedef struct wts_batch {
 /* Launch options; a zeroed struct (or NULL) selects the defaults. */
 typedef struct wts_options {
     int32_t rows_per_thread;       /* prototype rows held per lane: 0 = default (32 if d <= 2, else 16); 16 or 32 (32 needs d <= 3) */
-    int32_t warps_per_block;       /* 0 = 4; 1..8 */
+    int32_t warps_per_block;       /* 0 = 4; 1..4 */
     int32_t max_blocks;            /* 0 = as many as are resident at once (persistent grid); else a cap */
     int32_t keep_batch_order;      /* 0 = schedule the longest pairs first; 1 = batch order */
     int32_t reserved[12];
@@ -106,7 +106,8 @@ int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches);
 
 /* Measured roofline denominators (not part of the method): lane operations
  * per second of the whole GPU for which = 0 FP32 fused multiply-add, 1 FP32
- * min / max, 2 MUFU ex2.approx, 3 MUFU lg2.approx; best of
+ * min / max, 2 MUFU ex2.approx, 3 MUFU lg2.approx, 4 packed f32x2 fused
+ * multiply-add (two lane-ops each), 5 three-input FP32 min; best of
  * four timed launches.  Synchronises the device. */
 int wts_peak_probe(int which, double* ops_per_s);
 

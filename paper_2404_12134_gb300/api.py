@@ -131,7 +131,8 @@ def profile_read(kernel: str = ""):
 
 
 def peak_probe(which: int) -> float:
-    """Measured lane-ops/s: 0 FP32 FMA, 1 FP32 min, 2 MUFU ex2, 3 MUFU lg2."""
+    """Measured lane-ops/s: 0 FP32 FMA, 1 FP32 min/max, 2 MUFU ex2, 3 MUFU lg2,
+    4 packed f32x2 FMA (2 lane-ops each), 5 three-input min."""
     v = ctypes.c_double(0)
     check(_abi.load().wts_peak_probe(which, ctypes.byref(v)))
     return v.value

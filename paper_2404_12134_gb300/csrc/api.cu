@@ -107,7 +107,7 @@ int check_opt(const wts_options* opt, int D)
     if (opt->rows_per_thread && opt->rows_per_thread != 16 && opt->rows_per_thread != 32)
         return fail(WTS_EINVAL, "rows_per_thread must be 0, 16 or 32");
     if (opt->rows_per_thread == 32 && D > 3) return fail(WTS_EINVAL, "rows_per_thread=32 needs d <= 3");
-    if (opt->warps_per_block < 0 || opt->warps_per_block > 8) return fail(WTS_EINVAL, "warps_per_block must be 0..8");
+    if (opt->warps_per_block < 0 || opt->warps_per_block > 4) return fail(WTS_EINVAL, "warps_per_block must be 0..4");
     if (opt->max_blocks < 0) return fail(WTS_EINVAL, "max_blocks must be >= 0");
     return WTS_OK;
 }
@@ -410,7 +410,7 @@ int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches)
 
 int wts_peak_probe(int which, double* ops_per_s)
 {
-    if (!ops_per_s || which < 0 || which > 3) return fail(WTS_EINVAL, "which must be 0..3");
+    if (!ops_per_s || which < 0 || which > 5) return fail(WTS_EINVAL, "which must be 0..5");
     if (run_probe(which, ops_per_s)) return fail(WTS_ECUDA, "probe kernel failed");
     return ok();
 }

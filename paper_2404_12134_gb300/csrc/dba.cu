@@ -11,8 +11,8 @@ constexpr int kBtWords = 4096;   // 16 KB of direction words cached per warp
 // Walk the stored predecessor codes back from (M-1, N-1) to (0, 0).
 // Directions of band b live at dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]
 // for the word w of lane t at step s, and a cell (i, j) of the band sits in
-// lane t = (i mod BR) / R at step s = j + t, bits 2*(i mod 16) of word
-// (i mod R) / 16.  Along the walk s only decreases inside a band, so a window
+// lane t = (i mod BR) / R at step s = j + t, as bit k = i mod R ("not diag")
+// and bit R + k ("not up") of those W = R / 16 words.  Along the walk s only decreases inside a band, so a window
 // of kBtWords / (32 W) steps is loaded into shared memory (coalesced) and the walk reads
 // it; every lane walks the same path (broadcast reads), lane 0 writes.
 // Row i's range is [jlo(i), jhi(i)]: jhi when the walk enters the row, jlo
@@ -52,11 +52,15 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
                 for (int x = lane; x < n; x += 32) win[x] = __ldcs(src + x);
                 __syncwarp();
             }
-            const uint32_t w = win[((s - wlo) * 32 + t) * W + (k >> 4)];
-            const int code = (w >> (2 * (k & 15))) & 3;
+            // plane 0 ("not diag") is bit k, plane 1 ("not up") bit R + k of
+            // the W words of (step s, lane t)
+            const uint32_t* wp = win + ((s - wlo) * 32 + t) * W;
+            const uint32_t nd = (wp[k >> 5] >> (k & 31)) & 1u;
+            const uint32_t nu = (wp[(R + k) >> 5] >> ((R + k) & 31)) & 1u;
+            const int code = nd == 0 ? 0 : (nu == 0 ? 1 : 2);
             // a valid code matrix only moves left on row 0 and only up on
             // column 0; anything else is reported as |pi| = -1
-            if ((i == 0 && code != 2) || (j == 0 && code != 1) || code == 3) { len = -1; break; }
+            if ((i == 0 && code != 2) || (j == 0 && code != 1)) { len = -1; break; }
             if (code == 0) {
                 if (lane == 0) jlo[i] = j;
                 --i; --j;

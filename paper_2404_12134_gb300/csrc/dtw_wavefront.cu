@@ -6,91 +6,105 @@
 //   delta(i,j) = sum_c (b_ic - y_jc)^2   (squared Euclidean local cost).
 //
 // Ties between predecessors resolve diag first, then up (i-1,j), then left
-// (i,j-1); the CPU oracle takes the same decision in the same float
-// arithmetic (subtract, then one fused multiply-add per channel from 0, then
-// one add), so paths match bit for bit.
+// (i,j-1).  With m = min(dg, up, lf): the predecessor is diag iff dg == m,
+// else up iff up == m, else left.  The CPU oracle takes the same decision in
+// the same float arithmetic (subtract, then one fused multiply-add per channel
+// from 0, then one add), so paths match bit for bit.
 //
 // One warp owns a band of 32*R rows of one pair; lane t holds R rows, their
-// prototype samples and their last column of r in registers.  Lanes are
-// skewed by one column (lane t is at column s - t in step s), so the value
-// above a lane's first row comes from lane t-1 by __shfl_up_sync, and the
-// cycle sample y_j enters at lane 0 and walks down the lanes with it.  Lane 0
-// of band b > 0 reads the bottom row of band b-1 from a hand-off row in global
-// memory (L2), 32 columns at a time, after the producer has published them.
+// prototype samples (as row pairs, for the packed f32x2 arithmetic) and their
+// last column of r in registers.  Lanes are skewed by one column (lane t is at
+// column s - t in step s), so the value above a lane's first row comes from
+// lane t-1 by __shfl_up_sync.  Cycle samples are staged per warp in a 64-column
+// shared-memory ring as duplicated pairs {y, y}, refilled every 32 steps.  Lane
+// 0 of band b > 0 reads the bottom row of band b-1 from a hand-off row in
+// global memory (L2), 32 columns at a time, after the producer has published
+// them (release / acquire on a progress counter, once per 32 steps).
 // Each warp takes (pair, band) items in order from a global cursor, so the
 // producer of any item it waits for was started earlier: no deadlock, with or
 // without co-residency.  Every wait is bounded (wait_progress).
+//
+// Predecessor codes (kModeDirs) are two bit-planes per lane and step: bit
+// p*R + k of the lane's W = R/16 words is plane p of row k, plane 0 = "not
+// diag", plane 1 = "not up" (meaningful only when plane 0 is set).
 #include "dtw_wavefront.cuh"
 
 namespace wts {
 
 namespace {
 
-template <int D, int R, int MODE>
-__device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, int band, int lane)
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pack2(float lo, float hi)
 {
-    constexpr int BR = 32 * R;
-    constexpr int W = R / 16;                      // direction words per lane per step
-    const int M = pd.M, N = pd.N, d = p.d;
-    const int i0 = band * BR + lane * R;
-    const bool top = band == 0;
-    const bool last = band == pd.nbands - 1;
-    const float INF = inf_f();
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
 
-    float b[R][D];
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            b[k][c] = (i0 + k < M && c < d) ? __ldg(pd.X + (int64_t)(i0 + k) * d + c) : 0.f;
+__device__ __forceinline__ void unpack2(u64 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 
-    float col[R];
-    int cnt[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) { col[k] = INF; cnt[k] = 0; }
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
+{
+    u64 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 
-    float y[D], ybuf[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) { y[c] = 0.f; ybuf[c] = 0.f; }
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
+{
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 
-    float topv = INF;
-    int topc = 0;
-    // value and path count of r(i0-1, j-1) for the first row of this lane:
-    // r(0,0) = 0 (0 cells) for the first row of the matrix, +inf otherwise
-    float prev_up = (top && lane == 0) ? 0.f : INF;
-    int prev_upc = 0;
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
+{
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
 
-    const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
-    float* hcur = last ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
-    const int* cprev = (MODE == kModePlen && !top) ? p.hcnt + pd.hbuf_off + (int64_t)(band - 1) * N : nullptr;
-    int* ccur = (MODE == kModePlen && !last) ? p.hcnt + pd.hbuf_off + (int64_t)band * N : nullptr;
-    const int* fprev = top ? nullptr : p.flags + pd.flag_off + band - 1;
-    int* fcur = p.flags + pd.flag_off + band;
-    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)band * (N + 31) * 32 * W : nullptr;
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
-    const int steps = N + 31;
-    for (int s = 0; s < steps; ++s) {
-        if ((s & 31) == 0 && s < N) {
-            // the next 32 columns of the lane-0 feeds: cycle samples and the
-            // bottom row of the band above
-            const int jj = s + lane;
-#pragma unroll
-            for (int c = 0; c < D; ++c)
-                ybuf[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
-            if (!top) {
-                const int need = min(s + 32, N);
-                if (!wait_progress(fprev, need, p.hdr, 1)) return;
-                topv = jj < N ? __ldcg(hprev + jj) : INF;
-                if (MODE == kModePlen) topc = jj < N ? __ldcg(cprev + jj) : 0;
-            }
-        }
-        const int src = s & 31;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const float fresh = __shfl_sync(FULL, ybuf[c], src);
-            const float moved = __shfl_up_sync(FULL, y[c], 1);
-            y[c] = lane == 0 ? fresh : moved;
-        }
+// all ones if a != b, else 0
+__device__ __forceinline__ uint32_t ne_mask(float a, float b)
+{
+    uint32_t r;
+    asm("set.ne.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+constexpr int kRing = 64;    // columns of cycle samples staged per warp
+
+template <int D, int R, int MODE>
+struct Band {
+    static constexpr int BR = 32 * R;
+    static constexpr int W = R / 16;        // code words per lane per step
+    static constexpr int Q = R / 2;         // row pairs
+
+    u64 bp[Q][D];                           // prototype rows as pairs
+    float col[R];                           // r at the lane's last column
+    int cnt[R];                             // path cells (kModePlen)
+    float prev_up;                          // r(i0-1, j-1) for the first row
+    int prev_upc;
+    float topv;                             // lane l: r(band top - 1, s0 + l)
+    int topc;
+
+    // One step: lane at column j = s - lane (in range when FULLCHUNK).
+    template <bool FULLCHUNK>
+    __device__ __forceinline__ void step(const u64* ring, int s, int src, int lane, int N, bool top,
+                                         float* hcur, int* ccur, uint32_t* dout)
+    {
+        const float INF = inf_f();
         const float above = __shfl_up_sync(FULL, col[R - 1], 1);
         const float tv = __shfl_sync(FULL, topv, src);
         const float up_in = lane == 0 ? (top ? INF : tv) : above;
@@ -104,70 +118,140 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
             dgc_in = prev_upc;
             prev_upc = upc_in;
         }
-
         const int j = s - lane;
         uint32_t word[W > 0 ? W : 1];
 #pragma unroll
         for (int w = 0; w < (W > 0 ? W : 1); ++w) word[w] = 0u;
-        if (j >= 0 && j < N) {
+        if (FULLCHUNK || (j >= 0 && j < N)) {
+            const u64* yr = ring + ((s - lane) & (kRing - 1));
+            u64 yy[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) yy[c] = yr[c * kRing];
+            float dl[R];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                u64 t = fsub2(bp[q][0], yy[0]);
+                u64 acc = fmul2(t, t);
+#pragma unroll
+                for (int c = 1; c < D; ++c) {
+                    t = fsub2(bp[q][c], yy[c]);
+                    acc = ffma2(t, t, acc);
+                }
+                unpack2(acc, dl[2 * q], dl[2 * q + 1]);
+            }
             float dg = dg_in, up = up_in;
             int cdg = dgc_in, cup = upc_in;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const float lf = col[k];
-                float t = __fsub_rn(b[k][0], y[0]);
-                float acc = __fmul_rn(t, t);
-#pragma unroll
-                for (int c = 1; c < D; ++c) {
-                    t = __fsub_rn(b[k][c], y[c]);
-                    acc = __fmaf_rn(t, t, acc);
-                }
-                const float m1 = fminf(up, lf);
-                const float m = fminf(dg, m1);
-                const float r = __fadd_rn(acc, m);
-                if (MODE != kModeCost) {
-                    const bool is_dg = dg <= m1;
-                    const bool is_up = up <= lf;
-                    if (MODE == kModeDirs) {
-                        const uint32_t code = is_dg ? 0u : (is_up ? 1u : 2u);
-                        word[k >> 4] |= code << (2 * (k & 15));
-                    } else {
-                        const int cl = cnt[k];
-                        const int cn = 1 + (is_dg ? cdg : (is_up ? cup : cl));
-                        cdg = cl;
-                        cup = cn;
-                        cnt[k] = cn;
-                    }
+                const float m = min3f(dg, up, lf);
+                const float r = __fadd_rn(dl[k], m);
+                if (MODE == kModeDirs) {
+                    word[k >> 5] |= ne_mask(dg, m) & (1u << (k & 31));
+                    word[(R + k) >> 5] |= ne_mask(up, m) & (1u << ((R + k) & 31));
+                } else if (MODE == kModePlen) {
+                    const int cl = cnt[k];
+                    const int cn = 1 + (dg == m ? cdg : (up == m ? cup : cl));
+                    cdg = cl;
+                    cup = cn;
+                    cnt[k] = cn;
                 }
                 dg = lf;
                 up = r;
                 col[k] = r;
             }
-            if (hcur != nullptr && lane == 31) {
+            if (lane == 31 && hcur != nullptr) {
                 __stcg(hcur + j, col[R - 1]);
                 if (MODE == kModePlen) __stcg(ccur + j, cnt[R - 1]);
-                if (((j + 1) & 31) == 0 || j == N - 1) st_release(fcur, j + 1);
             }
         }
         if (MODE == kModeDirs) {
             if (W == 1) {
                 __stcs(dout + (int64_t)s * 32 + lane, word[0]);
             } else {
-                uint2 v = make_uint2(word[0], word[W > 1 ? 1 : 0]);
-                __stcs(reinterpret_cast<uint2*>(dout) + (int64_t)s * 32 + lane, v);
+                __stcs(reinterpret_cast<uint2*>(dout) + (int64_t)s * 32 + lane,
+                       make_uint2(word[0], word[W > 1 ? 1 : 0]));
             }
         }
+    }
+};
+
+template <int D, int R, int MODE>
+__device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, int band, int lane, u64* ring)
+{
+    using BandT = Band<D, R, MODE>;
+    constexpr int BR = BandT::BR;
+    constexpr int W = BandT::W;
+    const int M = pd.M, N = pd.N, d = p.d;
+    const int i0 = band * BR + lane * R;
+    const bool top = band == 0;
+    const bool last = band == pd.nbands - 1;
+    const float INF = inf_f();
+
+    BandT st;
+#pragma unroll
+    for (int q = 0; q < BandT::Q; ++q)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int ia = i0 + 2 * q, ib = ia + 1;
+            const float va = (ia < M && c < d) ? __ldg(pd.X + (int64_t)ia * d + c) : 0.f;
+            const float vb = (ib < M && c < d) ? __ldg(pd.X + (int64_t)ib * d + c) : 0.f;
+            st.bp[q][c] = pack2(va, vb);
+        }
+#pragma unroll
+    for (int k = 0; k < R; ++k) { st.col[k] = INF; st.cnt[k] = 0; }
+    // r(i0-1, j-1) at j = 0: r(0,0) = 0 (0 cells) for the matrix's first row, +inf otherwise
+    st.prev_up = (top && lane == 0) ? 0.f : INF;
+    st.prev_upc = 0;
+    st.topv = INF;
+    st.topc = 0;
+
+    const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
+    float* hcur = last ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
+    const int* cprev = (MODE == kModePlen && !top) ? p.hcnt + pd.hbuf_off + (int64_t)(band - 1) * N : nullptr;
+    int* ccur = (MODE == kModePlen && !last) ? p.hcnt + pd.hbuf_off + (int64_t)band * N : nullptr;
+    const int* fprev = top ? nullptr : p.flags + pd.flag_off + band - 1;
+    int* fcur = p.flags + pd.flag_off + band;
+    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)band * (N + 31) * 32 * W : nullptr;
+
+    const int steps = N + 31;
+    for (int s0 = 0; s0 < steps; s0 += 32) {
+        if (s0 < N) {
+            // columns s0 .. s0+31 of the lane-0 feeds
+            const int jj = s0 + lane;
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const float v = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+                ring[c * kRing + (jj & (kRing - 1))] = pack2(v, v);
+            }
+            if (!top) {
+                if (!wait_progress(fprev, min(s0 + 32, N), p.hdr, 1)) return;
+                st.topv = jj < N ? __ldcg(hprev + jj) : INF;
+                if (MODE == kModePlen) st.topc = jj < N ? __ldcg(cprev + jj) : 0;
+            }
+            __syncwarp();
+        }
+        if (s0 >= 31 && s0 + 32 <= N) {
+#pragma unroll 2
+            for (int u = 0; u < 32; ++u) st.template step<true>(ring, s0 + u, u, lane, N, top, hcur, ccur, dout);
+        } else {
+            const int n = min(32, steps - s0);
+            for (int u = 0; u < n; ++u) st.template step<false>(ring, s0 + u, u, lane, N, top, hcur, ccur, dout);
+        }
+        // lane 31 has finished columns up to s0 (its column at step s0 + 31)
+        if (lane == 31 && hcur != nullptr && s0 >= 0) st_release(fcur, min(s0 + 1, N));
     }
 
     if (last) {
         const int ilast = M - 1 - band * BR;
         if (lane == ilast / R) {
             const int kk = ilast % R;
-            float v = col[0];
-            int c = cnt[0];
+            float v = st.col[0];
+            int c = st.cnt[0];
 #pragma unroll
             for (int k = 1; k < R; ++k)
-                if (k == kk) { v = col[k]; c = cnt[k]; }
+                if (k == kk) { v = st.col[k]; c = st.cnt[k]; }
             if (p.cost_out) p.cost_out[pd.out] = v;
             if (MODE == kModePlen) {
                 if (p.plen_out) p.plen_out[pd.out] = c;
@@ -184,10 +268,17 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     }
 }
 
+// Blocks of at most 4 warps; three resident blocks (12 warps, <= 170 registers)
+// where the prototype rows fit, two otherwise.
+template <int D, int R>
+constexpr int min_blocks() { return (R == 16 && D <= 6) ? 3 : 2; }
+
 template <int D, int R, int MODE>
-__global__ void __launch_bounds__(256) dtw_wavefront_kernel(DPParams p)
+__global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(DPParams p)
 {
+    extern __shared__ u64 ring_all[];
     const int lane = threadIdx.x & 31;
+    u64* ring = ring_all + (threadIdx.x >> 5) * D * kRing;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&p.hdr->item_counter, 1);
@@ -196,17 +287,30 @@ __global__ void __launch_bounds__(256) dtw_wavefront_kernel(DPParams p)
         if (ld_volatile(&p.hdr->abort)) break;
         const int q = find_slot(p.prefix, p.P, item);
         const PairDesc pd = p.pairs[p.order[q]];
-        run_band<D, R, MODE>(p, pd, item - p.prefix[q], lane);
+        run_band<D, R, MODE>(p, pd, item - p.prefix[q], lane, ring);
     }
 }
+
+template <int D>
+constexpr size_t ring_bytes(int block) { return (size_t)(block / 32) * D * kRing * sizeof(u64); }
 
 template <int D, int R>
 cudaError_t launch_mode(int mode, const DPParams& p, int grid, int block, cudaStream_t st)
 {
+    const size_t smem = ring_bytes<D>(block);
     switch (mode) {
-        case kModeCost: dtw_wavefront_kernel<D, R, kModeCost><<<grid, block, 0, st>>>(p); break;
-        case kModePlen: dtw_wavefront_kernel<D, R, kModePlen><<<grid, block, 0, st>>>(p); break;
-        case kModeDirs: dtw_wavefront_kernel<D, R, kModeDirs><<<grid, block, 0, st>>>(p); break;
+        case kModeCost:
+            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeCost>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            dtw_wavefront_kernel<D, R, kModeCost><<<grid, block, smem, st>>>(p);
+            break;
+        case kModePlen:
+            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModePlen>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            dtw_wavefront_kernel<D, R, kModePlen><<<grid, block, smem, st>>>(p);
+            break;
+        case kModeDirs:
+            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            dtw_wavefront_kernel<D, R, kModeDirs><<<grid, block, smem, st>>>(p);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -216,10 +320,20 @@ template <int D, int R>
 int occ_mode(int mode, int block)
 {
     int n = 0;
+    const size_t smem = ring_bytes<D>(block);
     switch (mode) {
-        case kModeCost: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeCost>, block, 0); break;
-        case kModePlen: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModePlen>, block, 0); break;
-        case kModeDirs: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeDirs>, block, 0); break;
+        case kModeCost:
+            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeCost>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeCost>, block, smem);
+            break;
+        case kModePlen:
+            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModePlen>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModePlen>, block, smem);
+            break;
+        case kModeDirs:
+            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeDirs>, block, smem);
+            break;
         default: break;
     }
     return n;
