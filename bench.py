@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--T", type=int, default=200, help="cycles (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
+    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft"],
+                    help="soft: only the soft-DTW leg (with --T cycles of its workload); for profiling")
     return ap.parse_args()
 
 
@@ -165,10 +167,10 @@ def hbm_peak_gbs() -> float:
         return 6800.0
 
 
-def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0):
+def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None):
     """Soft-DTW forward + backward on the single-channel barycenter workload:
     64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB)."""
-    sb = synth.config_batch(2)
+    sb = synth.config_batch(2, T=T)
     M = synth.PROTO_LEN[2]
     gb = api.Batch.from_numpy(sb.data, sb.offsets, device=dev)
     B = api.euclid_mean(gb, M)
@@ -217,6 +219,13 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
+    if args.leg == "soft":
+        def sync():
+            torch.cuda.synchronize()
+        res = softdtw_leg(api, torch, dev, torch.cuda.current_stream(), sync, T=min(args.T, 64))
+        if rank == 0:
+            print(json.dumps({"leg": "soft", "softdtw": res}), flush=True)
+        return 0
 
     b, subset = make_workload(args.T)
     cells = M_PROTO * int(b.lengths.sum())

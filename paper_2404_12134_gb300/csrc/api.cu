@@ -152,26 +152,25 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         }
         const int64_t nb = cdiv(Mp, L->BR);
         items += nb;
-        h += pair_hbuf_floats(nb, Np);
+        h += pair_hbuf_slots(nb, Np);
         if (op == kOpAlign || op == kOpDba) dw += pair_dir_words(nb, Np, L->R);
         if (op == kOpSoft) rs += pair_rstore_floats(nb, Np, L->R);
     }
     if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
     L->n_items = items;
-    L->n_flags = items;
-    L->hbuf_floats = h;
+    L->hbuf_slots = h;
     L->dir_words = dw;
     L->rstore_floats = rs;
+    // hand-off slot: r (4 bytes), or {r, path cells} (8 bytes) when |pi| is counted
+    L->hbuf_bytes = (size_t)h * (op == kOpScore ? 8 : 4);
+    L->ebuf_bytes = op == kOpSoft ? (size_t)h * 16 : 0;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
     L->off_hdr = take(sizeof(WsHeader));
-    L->off_flags = take((size_t)items * sizeof(int));            // zeroed with the header
-    if (op == kOpSoft) L->off_flags2 = take((size_t)items * sizeof(int));
     L->off_pairs = take((size_t)L->P * sizeof(PairDesc));
     L->off_order = take((size_t)L->P * sizeof(int32_t));
     L->off_prefix = take((size_t)(L->P + 1) * sizeof(int32_t));
-    L->off_hbuf = take((size_t)h * sizeof(float));
-    if (op == kOpScore) L->off_hcnt = take((size_t)h * sizeof(int));
+    L->off_hbuf = take(L->hbuf_bytes);
     if (op == kOpAlign || op == kOpDba) L->off_dirs = take((size_t)dw * sizeof(uint32_t));
     if (op == kOpDba) {
         L->off_jlo = take((size_t)L->T * M * sizeof(int32_t));
@@ -181,7 +180,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     if (op == kOpSoft) {
         L->off_rstore = take((size_t)rs * sizeof(float));
         L->off_gpart = take((size_t)L->T * M * D * sizeof(float));
-        L->off_ebuf = take((size_t)h * 3 * sizeof(float));
+        L->off_ebuf = take(L->ebuf_bytes);
         L->off_pcost = take((size_t)L->T * sizeof(float));
     }
     L->total = off;
@@ -214,11 +213,12 @@ int device_info(DevInfo* di)
 int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const wts_options* opt,
             cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(ws, 0, L.off_flags + (size_t)L.n_flags * sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(ws + L.off_hdr, 0, sizeof(WsHeader), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace header)");
-    if (L.off_flags2) {
-        e = cudaMemsetAsync(ws + L.off_flags2, 0, (size_t)L.n_flags * sizeof(int), st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace flags)");
+    // hand-off rows start as NaN: a slot is valid once its producer wrote it
+    if (L.hbuf_bytes) {
+        e = cudaMemsetAsync(ws + L.off_hbuf, 0xFF, L.hbuf_bytes, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(hand-off rows)");
     }
     SetupParams sp{};
     sp.op = L.op;
@@ -271,9 +271,7 @@ DPParams base_params(const Layout& L, char* ws)
     p.n_items = (int)L.n_items;
     p.d = L.d;
     p.hdr = reinterpret_cast<WsHeader*>(ws + L.off_hdr);
-    p.flags = reinterpret_cast<int*>(ws + L.off_flags);
-    p.hbuf = reinterpret_cast<float*>(ws + L.off_hbuf);
-    p.hcnt = L.off_hcnt ? reinterpret_cast<int*>(ws + L.off_hcnt) : nullptr;
+    p.hbuf = ws + L.off_hbuf;
     p.dirs = L.off_dirs ? reinterpret_cast<uint32_t*>(ws + L.off_dirs) : nullptr;
     p.T = L.T;
     return p;
@@ -332,8 +330,6 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma)
     p.d = L.d;
     p.gamma = gamma;
     p.hdr = reinterpret_cast<WsHeader*>(ws + L.off_hdr);
-    p.flags = reinterpret_cast<int*>(ws + L.off_flags);
-    p.flags2 = reinterpret_cast<int*>(ws + L.off_flags2);
     p.hbuf = reinterpret_cast<float*>(ws + L.off_hbuf);
     p.ebuf = reinterpret_cast<float*>(ws + L.off_ebuf);
     p.rstore = reinterpret_cast<float*>(ws + L.off_rstore);
@@ -564,8 +560,8 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     cudaError_t e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.off_flags2, 0, (size_t)L.n_flags * sizeof(int), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward counters)");
+    if (e == cudaSuccess && L.ebuf_bytes) e = cudaMemsetAsync(ws + L.off_ebuf, 0xFF, L.ebuf_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward hand-off rows)");
     SoftParams p = soft_params(L, ws, gamma);
     int grid = 0, block = 0;
     if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;

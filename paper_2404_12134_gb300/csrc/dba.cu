@@ -7,27 +7,56 @@ namespace {
 
 constexpr int kBtWarps = 2;      // warps per backtrack CTA
 constexpr int kBtWords = 4096;   // 16 KB of direction words cached per warp
+constexpr long long kBtSpin = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
+{
+    for (long long it = 0; it < kBtSpin; ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 
 // Walk the stored predecessor codes back from (M-1, N-1) to (0, 0).
 // Directions of band b live at dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]
 // for the word w of lane t at step s, and a cell (i, j) of the band sits in
 // lane t = (i mod BR) / R at step s = j + t, as bit k = i mod R ("not diag")
-// and bit R + k ("not up") of those W = R / 16 words.  Along the walk s only decreases inside a band, so a window
-// of kBtWords / (32 W) steps is loaded into shared memory (coalesced) and the walk reads
-// it; every lane walks the same path (broadcast reads), lane 0 writes.
+// and bit R + k ("not up") of those W = R / 16 words.  Along the walk s only
+// decreases inside a band, so a window of kBtWords / (32 W) consecutive steps
+// (one contiguous block of global memory) is brought into shared memory by one
+// bulk asynchronous copy (completion on an mbarrier, bounded wait) and the walk
+// reads it; every lane walks the same path (broadcast reads), lane 0 writes.
 // Row i's range is [jlo(i), jhi(i)]: jhi when the walk enters the row, jlo
 // when it leaves it (Definition "Alignment path": monotone, so each row's
 // columns are contiguous).
 template <int W>
 __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
 {
+    constexpr int R = 16 * W;
+    constexpr int LOG_R = W == 1 ? 4 : 5;
     constexpr int kBtWin = kBtWords / (32 * W);     // steps of one band in the window
-    __shared__ uint32_t win_all[kBtWarps][kBtWords];
+    __shared__ __align__(128) uint32_t win_all[kBtWarps][kBtWords];
+    __shared__ __align__(8) uint64_t bars[kBtWarps];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     uint32_t* win = win_all[wid];
-    const int R = p.R, BR = 32 * p.R;
-    for (int q = blockIdx.x * kBtWarps + wid; q < p.P; q += gridDim.x * kBtWarps) {
+    uint64_t* bar = &bars[wid];
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    uint32_t phase = 0;
+    bool failed = false;
+    for (int q = blockIdx.x * kBtWarps + wid; q < p.P && !failed; q += gridDim.x * kBtWarps) {
         const PairDesc pd = p.pairs[q];
         const int N = pd.N;
         int32_t* jlo = p.jlo + (int64_t)pd.out * p.M;
@@ -38,19 +67,34 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
         for (;;) {
             ++len;
             if (i == 0 && j == 0) break;
-            const int b = i / BR;
-            const int t = (i - b * BR) / R;
-            const int k = i % R;
+            const int b = i >> (LOG_R + 5);
+            const int t = (i >> LOG_R) & 31;
+            const int k = i & (R - 1);
             const int s = j + t;
             if (b != band || s < wlo || s > whi) {
                 band = b;
                 whi = s;
                 wlo = max(0, s - kBtWin + 1);
                 const uint32_t* src = p.dirs + pd.dir_off + (int64_t)b * (N + 31) * 32 * W + (int64_t)wlo * 32 * W;
-                const int n = (whi - wlo + 1) * 32 * W;
+                const uint32_t bytes = (uint32_t)(whi - wlo + 1) * 32 * W * 4;
                 __syncwarp();
-                for (int x = lane; x < n; x += 32) win[x] = __ldcs(src + x);
-                __syncwarp();
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 :: "r"(smem_u32(win)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+                }
+                const bool ok = mbar_wait(bar, phase);
+                phase ^= 1u;
+                if (!ok) {
+                    // the copy did not land in time: give up on this pair,
+                    // wait (bounded) for the copy still in flight, stop
+                    mbar_wait(bar, phase ^ 1u);
+                    len = -1;
+                    failed = true;
+                    break;
+                }
             }
             // plane 0 ("not diag") is bit k, plane 1 ("not up") bit R + k of
             // the W words of (step s, lane t)

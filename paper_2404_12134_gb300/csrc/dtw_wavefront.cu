@@ -16,10 +16,12 @@
 // last column of r in registers.  Lanes are skewed by one column (lane t is at
 // column s - t in step s), so the value above a lane's first row comes from
 // lane t-1 by __shfl_up_sync.  Cycle samples are staged per warp in a 64-column
-// shared-memory ring as duplicated pairs {y, y}, refilled every 32 steps.  Lane
-// 0 of band b > 0 reads the bottom row of band b-1 from a hand-off row in
-// global memory (L2), 32 columns at a time, after the producer has published
-// them (release / acquire on a progress counter, once per 32 steps).
+// shared-memory ring as duplicated pairs {y, y}, refilled every 32 steps from
+// registers loaded one chunk ahead.  Lane 0 of band b > 0 reads the bottom row
+// of band b-1 from a hand-off row in global memory (L2), 32 columns at a time,
+// also one chunk ahead; each slot is NaN until its producer has written it
+// (the row is pre-filled before the launch), so the consumer re-reads only the
+// slots that are not there yet.
 // Each warp takes (pair, band) items in order from a global cursor, so the
 // producer of any item it waits for was started earlier: no deadlock, with or
 // without co-residency.  Every wait is bounded (wait_progress).
@@ -102,7 +104,7 @@ struct Band {
     // One step: lane at column j = s - lane (in range when FULLCHUNK).
     template <bool FULLCHUNK>
     __device__ __forceinline__ void step(const u64* ring, int s, int src, int lane, int N, bool top,
-                                         float* hcur, int* ccur, uint32_t* dout)
+                                         void* hcur, uint32_t* dout)
     {
         const float INF = inf_f();
         const float above = __shfl_up_sync(FULL, col[R - 1], 1);
@@ -161,8 +163,10 @@ struct Band {
                 col[k] = r;
             }
             if (lane == 31 && hcur != nullptr) {
-                __stcg(hcur + j, col[R - 1]);
-                if (MODE == kModePlen) __stcg(ccur + j, cnt[R - 1]);
+                if (MODE == kModePlen)
+                    __stcg(reinterpret_cast<u64*>(hcur) + j, pack2(col[R - 1], __int_as_float(cnt[R - 1])));
+                else
+                    __stcg(reinterpret_cast<float*>(hcur) + j, col[R - 1]);
             }
         }
         if (MODE == kModeDirs) {
@@ -206,41 +210,55 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     st.topv = INF;
     st.topc = 0;
 
-    const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
-    float* hcur = last ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
-    const int* cprev = (MODE == kModePlen && !top) ? p.hcnt + pd.hbuf_off + (int64_t)(band - 1) * N : nullptr;
-    int* ccur = (MODE == kModePlen && !last) ? p.hcnt + pd.hbuf_off + (int64_t)band * N : nullptr;
-    const int* fprev = top ? nullptr : p.flags + pd.flag_off + band - 1;
-    int* fcur = p.flags + pd.flag_off + band;
+    // hand-off rows: slot size 4 bytes (r), or 8 bytes ({r, cells}) with |pi|
+    constexpr int SLOT = MODE == kModePlen ? 8 : 4;
+    char* hb = static_cast<char*>(p.hbuf);
+    const char* hprev = top ? nullptr : hb + (pd.hbuf_off + (int64_t)(band - 1) * N) * SLOT;
+    void* hcur = last ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
     uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)band * (N + 31) * 32 * W : nullptr;
+
+    // lane-0 feeds, one chunk of 32 columns ahead: cycle samples and the
+    // bottom row of the band above (NaN until its producer has written it)
+    float ynext[D];
+    u64 tnext = 0;
+    auto load_y = [&](int jj) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ynext[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+    };
+    auto load_t = [&](int jj) -> u64 {
+        if (jj >= N) return 0;
+        if (SLOT == 8) return __ldcv(reinterpret_cast<const u64*>(hprev) + jj);
+        return (u64)__float_as_uint(__ldcv(reinterpret_cast<const float*>(hprev) + jj));
+    };
+    load_y(lane);
+    if (!top) tnext = load_t(lane);
 
     const int steps = N + 31;
     for (int s0 = 0; s0 < steps; s0 += 32) {
         if (s0 < N) {
-            // columns s0 .. s0+31 of the lane-0 feeds
             const int jj = s0 + lane;
             __syncwarp();
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const float v = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
-                ring[c * kRing + (jj & (kRing - 1))] = pack2(v, v);
-            }
+            for (int c = 0; c < D; ++c) ring[c * kRing + (jj & (kRing - 1))] = pack2(ynext[c], ynext[c]);
             if (!top) {
-                if (!wait_progress(fprev, min(s0 + 32, N), p.hdr, 1)) return;
-                st.topv = jj < N ? __ldcg(hprev + jj) : INF;
-                if (MODE == kModePlen) st.topc = jj < N ? __ldcg(cprev + jj) : 0;
+                u64 t = tnext;
+                const bool ok = wait_filled(jj < N && is_nan_bits((uint32_t)t),
+                                            [&]() { t = load_t(jj); return is_nan_bits((uint32_t)t); }, p.hdr, 1);
+                if (!ok) return;
+                st.topv = jj < N ? __uint_as_float((uint32_t)t) : INF;
+                if (MODE == kModePlen) st.topc = (int)(t >> 32);
             }
+            load_y(jj + 32);
+            if (!top) tnext = load_t(jj + 32);
             __syncwarp();
         }
         if (s0 >= 31 && s0 + 32 <= N) {
 #pragma unroll 2
-            for (int u = 0; u < 32; ++u) st.template step<true>(ring, s0 + u, u, lane, N, top, hcur, ccur, dout);
+            for (int u = 0; u < 32; ++u) st.template step<true>(ring, s0 + u, u, lane, N, top, hcur, dout);
         } else {
             const int n = min(32, steps - s0);
-            for (int u = 0; u < n; ++u) st.template step<false>(ring, s0 + u, u, lane, N, top, hcur, ccur, dout);
+            for (int u = 0; u < n; ++u) st.template step<false>(ring, s0 + u, u, lane, N, top, hcur, dout);
         }
-        // lane 31 has finished columns up to s0 (its column at step s0 + 31)
-        if (lane == 31 && hcur != nullptr && s0 >= 0) st_release(fcur, min(s0 + 1, N));
     }
 
     if (last) {

@@ -20,9 +20,8 @@ struct DPParams {
     int n_items;
     int d;
     WsHeader* hdr;
-    int* flags;          // progress counters (columns of the band's bottom row published)
-    float* hbuf;         // hand-off rows
-    int* hcnt;           // hand-off path-cell counts (kModePlen)
+    void* hbuf;          // hand-off rows: float r per column, or {float r, int cells} (kModePlen);
+                         // pre-filled with 0xFF bytes (NaN) before the launch
     uint32_t* dirs;      // direction words (kModeDirs)
     float* cost_out;     // [*] indexed by PairDesc::out (may be null)
     int32_t* plen_out;   // [*] (kModePlen, may be null)

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
 {
     const int P = sp.P;
     // pass 1: descriptors and storage offsets in pair order
-    int64_t run_h = 0, run_d = 0, run_r = 0, run_f = 0;
+    int64_t run_h = 0, run_d = 0, run_r = 0;
     for (int base = 0; base < P; base += kSetupThreads) {
         const int p = base + threadIdx.x;
         PairDesc pd{};
@@ -75,23 +75,21 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
             pd.N = (int32_t)N;
             pd.nbands = (int32_t)nb;
             pd.out = p;
-            h = pair_hbuf_floats(nb, N);
+            h = pair_hbuf_slots(nb, N);
             if (sp.op == kOpAlign || sp.op == kOpDba) dw = pair_dir_words(nb, N, sp.R);
             if (sp.op == kOpSoft) rs = pair_rstore_floats(nb, N, sp.R);
         }
-        int64_t eh, ed, er, ef;
+        int64_t eh, ed, er;
         int64_t th = block_exclusive_scan(h, &eh);
         int64_t td = block_exclusive_scan(dw, &ed);
         int64_t tr = block_exclusive_scan(rs, &er);
-        int64_t tf = block_exclusive_scan(nb, &ef);
         if (p < P) {
             pd.hbuf_off = run_h + eh;
             pd.dir_off = run_d + ed;
             pd.aux_off = run_r + er;
-            pd.flag_off = (int32_t)(run_f + ef);
             sp.pairs[p] = pd;
         }
-        run_h += th; run_d += td; run_r += tr; run_f += tf;
+        run_h += th; run_d += td; run_r += tr;
     }
     __syncthreads();
     // pass 2: order (longest first by cells, ties by index) via rank counting

@@ -27,7 +27,7 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Per-pair storage, shared by host sizing and the device setup kernel.
-__host__ __device__ inline int64_t pair_hbuf_floats(int64_t nb, int64_t N) { return (nb - 1) * N; }
+__host__ __device__ inline int64_t pair_hbuf_slots(int64_t nb, int64_t N) { return (nb - 1) * N; }
 __host__ __device__ inline int64_t pair_dir_words(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * (R / 16); }
 __host__ __device__ inline int64_t pair_rstore_floats(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * R; }
 
@@ -38,9 +38,10 @@ struct Layout {
     int d = 0, D = 0, R = 0, BR = 0;
     int64_t M = 0;        // prototype length (shared-prototype ops)
     int64_t n_items = 0;  // total (pair, band) items
-    int64_t hbuf_floats = 0, dir_words = 0, rstore_floats = 0, n_flags = 0;
-    size_t off_hdr = 0, off_pairs = 0, off_order = 0, off_prefix = 0, off_flags = 0, off_flags2 = 0;
-    size_t off_hbuf = 0, off_hcnt = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0;
+    int64_t hbuf_slots = 0, dir_words = 0, rstore_floats = 0;
+    size_t hbuf_bytes = 0, ebuf_bytes = 0;
+    size_t off_hdr = 0, off_pairs = 0, off_order = 0, off_prefix = 0;
+    size_t off_hbuf = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0;
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
     size_t total = 0;
 };

@@ -36,6 +36,15 @@ __device__ __forceinline__ float ex2a(float x)
     return y;
 }
 
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pack2(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
 __device__ __forceinline__ float lg2a(float x)
 {
     float y;
@@ -94,21 +103,33 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 
     const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
     float* hcur = last ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
-    const int* fprev = top ? nullptr : p.flags + pd.flag_off + band - 1;
-    int* fcur = p.flags + pd.flag_off + band;
     float* rs = p.rstore + pd.aux_off + (int64_t)band * (N + 31) * 32 * R;
+
+    // lane-0 feeds one chunk of 32 columns ahead (the top row is NaN until written)
+    float ynext[D];
+    float tnext = INF;
+    auto load_y = [&](int jj) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ynext[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+    };
+    load_y(lane);
+    if (!top && lane < N) tnext = __ldcv(hprev + lane);
 
     const int steps = N + 31;
     for (int s = 0; s < steps; ++s) {
         if ((s & 31) == 0 && s < N) {
             const int jj = s + lane;
 #pragma unroll
-            for (int c = 0; c < D; ++c)
-                ybuf[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+            for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
             if (!top) {
-                if (!wait_progress(fprev, min(s + 32, N), p.hdr, 3)) return;
-                topv = jj < N ? __ldcg(hprev + jj) : INF;
+                float t = tnext;
+                const bool ok = wait_filled(jj < N && isnan(t), [&]() { t = __ldcv(hprev + jj); return isnan(t); },
+                                            p.hdr, 3);
+                if (!ok) return;
+                topv = jj < N ? t : INF;
+                tnext = jj + 32 < N ? __ldcv(hprev + jj + 32) : INF;
             }
+            load_y(jj + 32);
         }
         const int src = s & 31;
 #pragma unroll
@@ -141,10 +162,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
                 up = r;
                 col[k] = r;
             }
-            if (hcur != nullptr && lane == 31) {
-                __stcg(hcur + j, col[R - 1]);
-                if (((j + 1) & 31) == 0 || j == N - 1) st_release(fcur, j + 1);
-            }
+            if (hcur != nullptr && lane == 31) __stcg(hcur + j, col[R - 1]);
         }
         float4* dst = reinterpret_cast<float4*>(rs + (int64_t)s * 32 * R);
 #pragma unroll
@@ -194,31 +212,62 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     float cr = NINF, cd = 0.f, ce = 0.f;          // chunk of the row below the band
     float pbr = NINF, pbd = 0.f, pbe = 0.f;       // row below, one column to the right
 
-    // boundary slot b holds the top row of band b+1
-    const float* enext = last ? nullptr : p.ebuf + 3 * (pd.hbuf_off + (int64_t)band * N);
-    float* emine = top ? nullptr : p.ebuf + 3 * (pd.hbuf_off + (int64_t)(band - 1) * N);
-    const int* fnext = last ? nullptr : p.flags2 + pd.flag_off + band + 1;
-    int* fmine = p.flags2 + pd.flag_off + band;
+    // boundary slot b holds the top row of band b+1: per column two 8-byte
+    // words {r, delta} and {e, 0}, each NaN until written
+    const u64* enext = last ? nullptr : reinterpret_cast<const u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)band * N);
+    u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
     const float* rs = p.rstore + pd.aux_off + (int64_t)band * (N + 31) * 32 * R;
+
+    // R of this lane's rows at the column of step ss (written by forward step
+    // N+30-ss), loaded one step ahead of its use
+    float4 rnext[R / 4];
+    auto load_r = [&](int ss) {
+        const int jj = N - 1 - ss + (31 - lane);
+        if (jj >= 0 && jj < N) {
+            const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - ss) * 32 * R);
+#pragma unroll
+            for (int k4 = 0; k4 < R / 4; ++k4) rnext[k4] = __ldcs(src4 + k4 * 32 + lane);
+        }
+    };
+    load_r(0);
+    // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l
+    float ynext[D];
+    u64 wa = 0, wb = 0;
+    auto load_y = [&](int jj) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ynext[c] = (jj >= 0 && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+    };
+    auto load_e = [&](int jj) {
+        if (jj >= 0) { wa = __ldcv(enext + 2 * jj); wb = __ldcv(enext + 2 * jj + 1); }
+    };
+    load_y(N - 1 - lane);
+    if (!last) load_e(N - 1 - lane);
 
     const int steps = N + 31;
     for (int s = 0; s < steps; ++s) {
+        float4 rcur[R / 4];
+#pragma unroll
+        for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = rnext[k4];
+        if (s + 1 < steps) load_r(s + 1);
         if ((s & 31) == 0 && s < N) {
-            // lane l holds column N-1-s-l of the lane-31 feeds
             const int jj = N - 1 - s - lane;
 #pragma unroll
-            for (int c = 0; c < D; ++c)
-                ybuf[c] = (jj >= 0 && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+            for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
             if (!last) {
-                if (!wait_progress(fnext, min(s + 32, N), p.hdr, 4)) return;
+                const bool ok = wait_filled(jj >= 0 && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
+                                            [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
+                                            p.hdr, 4);
+                if (!ok) return;
                 if (jj >= 0) {
-                    cr = __ldcg(enext + 3 * jj);
-                    cd = __ldcg(enext + 3 * jj + 1);
-                    ce = __ldcg(enext + 3 * jj + 2);
+                    cr = __uint_as_float((uint32_t)wa);
+                    cd = __uint_as_float((uint32_t)(wa >> 32));
+                    ce = __uint_as_float((uint32_t)wb);
                 } else {
                     cr = NINF; cd = 0.f; ce = 0.f;
                 }
+                load_e(jj - 32);
             }
+            load_y(jj - 32);
         }
         const int src = s & 31;
 #pragma unroll
@@ -243,11 +292,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 
         const int j = N - 1 - s + (31 - lane);
         if (j >= 0 && j < N) {
-            const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - s) * 32 * R);
             float nr = br, nd = bd, ne = be;       // below, column j
 #pragma unroll
             for (int k4 = R / 4 - 1; k4 >= 0; --k4) {
-                const float4 v4 = __ldcs(src4 + k4 * 32 + lane);
+                const float4 v4 = rcur[k4];
                 const float rv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                 for (int kq = 3; kq >= 0; --kq) {
@@ -273,10 +321,8 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 }
             }
             if (emine != nullptr && lane == 0) {
-                __stcg(emine + 3 * j, rp[0]);
-                __stcg(emine + 3 * j + 1, dp[0]);
-                __stcg(emine + 3 * j + 2, ep[0]);
-                if (((N - j) & 31) == 0 || j == 0) st_release(fmine, N - j);
+                __stcg(emine + 2 * j, pack2(rp[0], dp[0]));
+                __stcg(emine + 2 * j + 1, pack2(ep[0], 0.f));
             }
         }
     }

@@ -15,10 +15,9 @@ struct SoftParams {
     int d;
     float gamma;
     WsHeader* hdr;
-    int* flags;          // forward progress (columns of a band's bottom row published)
-    int* flags2;         // backward progress (columns, counted from the right, of a band's top row)
-    float* hbuf;         // forward hand-off rows (r of a band's bottom row)
-    float* ebuf;         // backward hand-off rows: (r, delta, e) of a band's top row, 3 floats per column
+    float* hbuf;         // forward hand-off rows (r of a band's bottom row); pre-filled with NaN
+    float* ebuf;         // backward hand-off rows: {r, delta} {e, 0} of a band's top row, 16 bytes
+                         // per column; pre-filled with NaN
     float* rstore;       // R, per band [(N+31) steps][R/4][32 lanes][4]
     float* value_out;    // [P] Soft-DTW value per pair (forward)
     float* gpart;        // [P][M][d] per-pair gradient sum_j e_ij * 2 (b_i - y_j) (backward)

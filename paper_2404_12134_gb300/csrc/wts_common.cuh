@@ -9,7 +9,7 @@
 // finished by lane t-1 one step earlier and arrives by a register shuffle.
 // Bands of the same pair are chained through a full-row hand-off buffer in
 // global memory (the bottom row of band b is the top boundary of band b+1),
-// guarded by a per-band progress counter with release/acquire ordering.
+// each slot filled once and polled by the consumer (see wait_filled).
 #pragma once
 
 #include <cstdint>
@@ -32,10 +32,8 @@ struct PairDesc {
     int32_t nbands;      // ceil(M / BR)
     int32_t out;         // output slot (cycle index, or pair index for pairwise)
     int64_t dir_off;     // first direction word of this pair
-    int64_t hbuf_off;    // first float of this pair's hand-off rows ((nbands-1) * N)
-    int64_t aux_off;     // first element of per-pair auxiliary storage (R store / flags base)
-    int32_t flag_off;    // first progress counter of this pair (nbands counters)
-    int32_t pad;
+    int64_t hbuf_off;    // first slot of this pair's hand-off rows ((nbands-1) * N slots)
+    int64_t aux_off;     // first element of per-pair auxiliary storage (R store)
 };
 
 // Header at the start of every workspace.
@@ -49,18 +47,6 @@ struct WsHeader {
 
 __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
 
-__device__ __forceinline__ int ld_acquire(const int* p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int* p, int v)
-{
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ int ld_volatile(const int* p)
 {
     int v;
@@ -68,16 +54,26 @@ __device__ __forceinline__ int ld_volatile(const int* p)
     return v;
 }
 
-// Wait (warp-uniform) until *flag >= need.  Every lane polls the same word.
-// Gives up after kSpinLimit polls or when another warp has raised the abort
-// word: then records a timeout and returns false.
-__device__ __forceinline__ bool wait_progress(const int* flag, int need, WsHeader* hdr, int where)
+// Hand-off rows between bands are pre-filled with 0xFF bytes (a NaN pattern)
+// before every launch; a producer writes each slot once with a plain store and
+// a consumer polls the slot until it is no longer NaN.  Each slot is one
+// single-copy-atomic word (4 or 8 bytes), so no flag and no fence is needed.
+// Costs are never NaN for finite inputs.
+__device__ __forceinline__ bool is_nan_bits(uint32_t bits) { return (bits & 0x7fffffffu) > 0x7f800000u; }
+
+// Spin (warp-uniform) until no lane reports `missing`; `reload` re-reads the
+// lane's slot and returns whether it is still missing.  Bounded: after
+// kSpinLimit rounds, or once another warp raised the abort word, records a
+// timeout and returns false.
+template <typename Reload>
+__device__ __forceinline__ bool wait_filled(bool missing, Reload reload, WsHeader* hdr, int where)
 {
-    if (ld_acquire(flag) >= need) return true;
+    if (!__any_sync(FULL, missing)) return true;
     long long spins = 0;
     for (;;) {
-        __nanosleep(128);
-        if (ld_acquire(flag) >= need) return true;
+        __nanosleep(64);
+        if (missing) missing = reload();
+        if (!__any_sync(FULL, missing)) return true;
         if (ld_volatile(&hdr->abort)) return false;
         if (++spins > kSpinLimit) {
             if ((threadIdx.x & 31) == 0) {
