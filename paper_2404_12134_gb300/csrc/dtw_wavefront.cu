@@ -15,9 +15,9 @@
 // prototype samples (as row pairs, for the packed f32x2 arithmetic) and their
 // last column of r in registers.  Lanes are skewed by one column (lane t is at
 // column s - t in step s), so the value above a lane's first row comes from
-// lane t-1 by __shfl_up_sync.  Cycle samples are staged per warp in a 64-column
-// shared-memory ring as duplicated pairs {y, y}, refilled every 32 steps from
-// registers loaded one chunk ahead.  Lane 0 of band b > 0 reads the bottom row
+// lane t-1 by __shfl_up_sync.  Cycle samples are staged per warp in a
+// 128-column shared-memory ring as duplicated pairs {y, y}, refilled every 32
+// steps from registers loaded ahead.  Lane 0 of band b > 0 reads the bottom row
 // of band b-1 from a hand-off row in global memory (L2), 32 columns at a time,
 // also one chunk ahead; each slot is NaN until its producer has written it
 // (the row is pre-filled before the launch), so the consumer re-reads only the
@@ -85,7 +85,7 @@ __device__ __forceinline__ uint32_t ne_mask(float a, float b)
     return r;
 }
 
-constexpr int kRing = 64;    // columns of cycle samples staged per warp
+constexpr int kRing = 128;   // columns of cycle samples staged per warp
 
 template <int D, int R, int MODE>
 struct Band {
@@ -95,13 +95,37 @@ struct Band {
 
     u64 bp[Q][D];                           // prototype rows as pairs
     float col[R];                           // r at the lane's last column
+    float dl[R];                            // local costs of the lane's next column
     int cnt[R];                             // path cells (kModePlen)
     float prev_up;                          // r(i0-1, j-1) for the first row
     int prev_upc;
     float topv;                             // lane l: r(band top - 1, s0 + l)
     int topc;
 
-    // One step: lane at column j = s - lane (in range when FULLCHUNK).
+    // Local costs of column jc for the lane's rows, pair q (two rows at once).
+    __device__ __forceinline__ void cost_pair(const u64* yy, int q)
+    {
+        u64 t = fsub2(bp[q][0], yy[0]);
+        u64 acc = fmul2(t, t);
+#pragma unroll
+        for (int c = 1; c < D; ++c) {
+            t = fsub2(bp[q][c], yy[c]);
+            acc = ffma2(t, t, acc);
+        }
+        unpack2(acc, dl[2 * q], dl[2 * q + 1]);
+    }
+
+    __device__ __forceinline__ void load_samples(const u64* ring, int jc, u64* yy)
+    {
+        const u64* yr = ring + (jc & (kRing - 1));
+#pragma unroll
+        for (int c = 0; c < D; ++c) yy[c] = yr[c * kRing];
+    }
+
+    // One step: the lane's column j = s - lane (in range when FULLCHUNK).
+    // dl holds the local costs of column j on entry and those of column j+1 on
+    // exit: the next column's costs are computed between the links of this
+    // column's min-plus chain, which is serial down the rows.
     template <bool FULLCHUNK>
     __device__ __forceinline__ void step(const u64* ring, int s, int src, int lane, int N, bool top,
                                          void* hcur, uint32_t* dout)
@@ -121,26 +145,12 @@ struct Band {
             prev_upc = upc_in;
         }
         const int j = s - lane;
+        u64 yy[D];
+        load_samples(ring, j + 1, yy);
         uint32_t word[W > 0 ? W : 1];
 #pragma unroll
         for (int w = 0; w < (W > 0 ? W : 1); ++w) word[w] = 0u;
         if (FULLCHUNK || (j >= 0 && j < N)) {
-            const u64* yr = ring + ((s - lane) & (kRing - 1));
-            u64 yy[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) yy[c] = yr[c * kRing];
-            float dl[R];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                u64 t = fsub2(bp[q][0], yy[0]);
-                u64 acc = fmul2(t, t);
-#pragma unroll
-                for (int c = 1; c < D; ++c) {
-                    t = fsub2(bp[q][c], yy[c]);
-                    acc = ffma2(t, t, acc);
-                }
-                unpack2(acc, dl[2 * q], dl[2 * q + 1]);
-            }
             float dg = dg_in, up = up_in;
             int cdg = dgc_in, cup = upc_in;
 #pragma unroll
@@ -161,6 +171,7 @@ struct Band {
                 dg = lf;
                 up = r;
                 col[k] = r;
+                if (k & 1) cost_pair(yy, k >> 1);      // rows k-1, k of column j+1
             }
             if (lane == 31 && hcur != nullptr) {
                 if (MODE == kModePlen)
@@ -168,6 +179,9 @@ struct Band {
                 else
                     __stcg(reinterpret_cast<float*>(hcur) + j, col[R - 1]);
             }
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) cost_pair(yy, q);
         }
         if (MODE == kModeDirs) {
             if (W == 1) {
@@ -217,29 +231,51 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     void* hcur = last ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
     uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)band * (N + 31) * 32 * W : nullptr;
 
-    // lane-0 feeds, one chunk of 32 columns ahead: cycle samples and the
-    // bottom row of the band above (NaN until its producer has written it)
+    // Cycle samples go through the ring two chunks of 32 columns ahead of the
+    // step that first reads them (a step also reads the next column), loaded
+    // into registers one chunk before that; the bottom row of the band above
+    // (NaN until its producer has written it) is read one chunk ahead.
     float ynext[D];
     u64 tnext = 0;
     auto load_y = [&](int jj) {
 #pragma unroll
         for (int c = 0; c < D; ++c) ynext[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
     };
+    auto put_y = [&](int jj) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ring[c * kRing + (jj & (kRing - 1))] = pack2(ynext[c], ynext[c]);
+    };
     auto load_t = [&](int jj) -> u64 {
         if (jj >= N) return 0;
         if (SLOT == 8) return __ldcv(reinterpret_cast<const u64*>(hprev) + jj);
         return (u64)__float_as_uint(__ldcv(reinterpret_cast<const float*>(hprev) + jj));
     };
+    __syncwarp();
     load_y(lane);
+    put_y(lane);
+    load_y(lane + 32);
+    put_y(lane + 32);
+    load_y(lane + 64);
     if (!top) tnext = load_t(lane);
+    __syncwarp();
+    {
+        // local costs of the lane's first column (j = -lane: only lane 0's is used)
+        u64 yy[D];
+        st.load_samples(ring, -lane, yy);
+#pragma unroll
+        for (int q = 0; q < BandT::Q; ++q) st.cost_pair(yy, q);
+    }
 
     const int steps = N + 31;
     for (int s0 = 0; s0 < steps; s0 += 32) {
         if (s0 < N) {
             const int jj = s0 + lane;
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < D; ++c) ring[c * kRing + (jj & (kRing - 1))] = pack2(ynext[c], ynext[c]);
+            if (s0 > 0) {
+                __syncwarp();
+                put_y(jj + 32);
+                load_y(jj + 64);
+                __syncwarp();
+            }
             if (!top) {
                 u64 t = tnext;
                 const bool ok = wait_filled(jj < N && is_nan_bits((uint32_t)t),
@@ -247,10 +283,8 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
                 if (!ok) return;
                 st.topv = jj < N ? __uint_as_float((uint32_t)t) : INF;
                 if (MODE == kModePlen) st.topc = (int)(t >> 32);
+                tnext = load_t(jj + 32);
             }
-            load_y(jj + 32);
-            if (!top) tnext = load_t(jj + 32);
-            __syncwarp();
         }
         if (s0 >= 31 && s0 + 32 <= N) {
 #pragma unroll 2
@@ -287,9 +321,10 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
 }
 
 // Blocks of at most 4 warps; three resident blocks (12 warps, <= 170 registers)
-// where the prototype rows fit, two otherwise.
+// where the prototype rows fit easily, two otherwise (the software-pipelined
+// step keeps enough independent work per warp).
 template <int D, int R>
-constexpr int min_blocks() { return (R == 16 && D <= 6) ? 3 : 2; }
+constexpr int min_blocks() { return (R == 16 && D <= 4) ? 3 : 2; }
 
 template <int D, int R, int MODE>
 __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(DPParams p)
