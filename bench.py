@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--T", type=int, default=200, help="cycles (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
-    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft"],
-                    help="soft: only the soft-DTW leg (with --T cycles of its workload); for profiling")
+    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score"],
+                    help="soft / score: only that leg (soft: with --T cycles of its workload); for profiling")
     return ap.parse_args()
 
 
@@ -205,6 +205,78 @@ def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None 
     return res
 
 
+def scoring_leg(api, torch, dev, barrier, T: int | None = None, per_pair: bool = True):
+    """Uneven scoring: 1,000 cycles x 3 ch, pre-gap lengths log-normal (median
+    15k, sigma 0.6) clipped to 2k-60k, 5 % anomalous (drift / skipped segment /
+    3x slowdown), scored against the clean base sampled at M = 20,000.  One
+    persistent launch (autotuned options, captured in a CUDA graph) against one
+    launch per pair."""
+    from paper_2404_12134_gb300 import _abi
+    b = synth.config_batch(3, T=T)
+    M = synth.PROTO_LEN[3]
+    B = torch.from_numpy(synth.clean_prototype(b, M)).to(dev)
+    gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
+    cells = M * int(b.lengths.sum())
+    ws = api.Workspace(dev)
+    opts, tune_ms = api.autotune(_abi.OP_ANOMALY_SCORE, B, gb, ws)
+    g, (score, cost, plen) = api.capture(lambda: api.anomaly_score(B, gb, opts, ws=ws))
+    g.replay()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    barrier()
+    batched_ms = e0.elapsed_time(e1) / reps
+    res = {"workload": "1000 cycles x 3 ch FP32, pre-gap N ~ lognormal(15k, 0.6) clipped 2k-60k, 5% anomalous, "
+                       "M=20000 clean prototype",
+           "T": b.T, "cells": cells, "options": {"rows_per_thread": opts.rows_per_thread,
+                                                  "warps_per_block": opts.warps_per_block},
+           "batched_graph_ms": batched_ms, "batched_gcups": cells / (batched_ms * 1e-3) / 1e9,
+           "autotune_best_wavefront_ms": tune_ms}
+    # anomaly labels from the boxplot threshold q3 + 1.5 (q3 - q1) on the scores (Sec. 5.3),
+    # against the injected anomalies: a sanity report, not part of the timed path
+    sc = score.cpu().numpy().astype(np.float64)
+    q1, q3 = np.percentile(sc, [25, 75])
+    flag = sc > q3 + 1.5 * (q3 - q1)
+    truth = b.labels > 0
+    tp = int((flag & truth).sum()); fp = int((flag & ~truth).sum()); fn = int((~flag & truth).sum())
+    prec = tp / max(tp + fp, 1); rec = tp / max(tp + fn, 1)
+    res["boxplot_threshold"] = {"tp": tp, "fp": fp, "fn": fn,
+                                "f2": 5 * prec * rec / max(4 * prec + rec, 1e-12)}
+    if per_pair:
+        singles = []
+        for k in range(b.T):
+            o0, o1 = int(b.offsets[k]), int(b.offsets[k + 1])
+            singles.append(api.Batch(gb.data[o0:o1], torch.tensor([0, o1 - o0], device=dev),
+                                     np.array([0, o1 - o0], dtype=np.int64)))
+        ws1 = api.Workspace(dev)
+        api.anomaly_score(B, singles[0], ws=ws1)
+        barrier()
+        e0.record()
+        for one in singles:
+            api.anomaly_score(B, one, ws=ws1)
+        e1.record()
+        barrier()
+        pp_ms = e0.elapsed_time(e1)
+        g1, _ = api.capture(lambda: [api.anomaly_score(B, one, ws=ws1) for one in singles])
+        g1.replay()
+        barrier()
+        e0.record()
+        g1.replay()
+        e1.record()
+        barrier()
+        ppg_ms = e0.elapsed_time(e1)
+        res.update({"per_pair_eager_ms": pp_ms, "per_pair_eager_gcups": cells / (pp_ms * 1e-3) / 1e9,
+                    "per_pair_graph_ms": ppg_ms, "per_pair_graph_gcups": cells / (ppg_ms * 1e-3) / 1e9,
+                    "speedup_vs_per_pair_eager": pp_ms / batched_ms})
+        del g1, ws1
+    del g, ws
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -219,6 +291,13 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
+    if args.leg == "score":
+        def sync():
+            torch.cuda.synchronize()
+        res = scoring_leg(api, torch, dev, sync, T=args.T if args.T != 200 else None)
+        if rank == 0:
+            print(json.dumps({"leg": "score", "scoring": res}), flush=True)
+        return 0
     if args.leg == "soft":
         def sync():
             torch.cuda.synchronize()
@@ -371,6 +450,7 @@ def run_gpu(args):
         out["anomaly_score_gcups"] = cells / (s0.elapsed_time(s1) * 1e-3) / 1e9
 
     if not args.no_extras:
+        out["scoring"] = scoring_leg(api, torch, dev, barrier)
         out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
         out["measured_peaks_probe"] = {k: api.peak_probe(i) / 1e12 for i, k in
                                        enumerate(("fp32_fma_tops", "fp32_minmax_tops", "mufu_ex2_tops",

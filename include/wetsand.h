@@ -203,6 +203,18 @@ int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, fl
                   float eps, int32_t t, void* stream);
 
 /*
+ * wts_autotune - pick the launch options (rows per lane, warps per block) of
+ * the wavefront for operation op (WTS_OP_ANOMALY_SCORE, WTS_OP_DTW_ALIGN or
+ * WTS_OP_DBA_ITERATE) on this batch by timing each candidate that fits in the
+ * given workspace (one warm-up and one timed pass each, CUDA events on
+ * `stream`; synchronises it).  Results are cached per (op, d, M, T, total
+ * length); a cached answer costs nothing.  best: out (host); best_ms: out
+ * (host, may be NULL), the wavefront time of the chosen options.
+ */
+int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* workspace, size_t workspace_bytes,
+                 void* stream, wts_options* best, float* best_ms);
+
+/*
  * wts_pairwise_dtw - DTW between every two cycles of the batch (rows = the
  * lower-index cycle), for the medoid that initialises DBA.
  *   C [T][T] out: symmetric, C[a][a] = 0.

@@ -21,7 +21,7 @@ EXPORTS = (
     "wts_profile_enable", "wts_profile_read", "wts_peak_probe",
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
-    "softdtw_forward", "softdtw_backward", "wts_adam_step",
+    "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune",
 )
 
 
@@ -74,6 +74,7 @@ _SIGS = {
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),
     "anomaly_score_noalloc": ([VP, I64, PB, PO, VP, VP, VP, VP], ctypes.c_int),
+    "wts_autotune": ([ctypes.c_int, VP, I64, PB, VP, SZ, VP, PO, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "softdtw_forward": ([VP, I64, PB, ctypes.c_float, PO, VP, SZ, VP, VP], ctypes.c_int),
     "softdtw_backward": ([VP, I64, PB, ctypes.c_float, VP, PO, VP, SZ, VP, VP], ctypes.c_int),
     "wts_adam_step": ([VP, VP, VP, VP, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,

@@ -214,6 +214,37 @@ def dba_iterate(B_in: torch.Tensor, batch: Batch, opts=None, ws: Workspace | Non
     return B_out, counts, cost_before, cost
 
 
+def autotune(op: int, B: torch.Tensor, batch: Batch, ws: Workspace | None = None):
+    """Time the candidate launch options of the wavefront for ``op`` on this
+    batch and return (options, wavefront ms).  The workspace is sized for the
+    largest candidate."""
+    B = _check_B(B, batch.d)
+    M = B.shape[0]
+    need = max(workspace_size(op, M, batch, options(rows_per_thread=r))
+               for r in ((16, 32) if batch.d <= 3 else (16,)))
+    buf = _ws(ws, need)
+    best = wts_options()
+    ms = ctypes.c_float(0)
+    check(_abi.load().wts_autotune(op, B.data_ptr(), M, ctypes.byref(batch.c()), buf.data_ptr(), buf.numel(),
+                                   _stream(), ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value
+
+
+def capture(fn):
+    """Capture fn() (library calls on the current stream) in a CUDA graph;
+    returns (graph, fn's outputs).  Replaying the graph re-runs the calls on
+    the same buffers."""
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()                                # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(g):
+        out = fn()
+    return g, out
+
+
 def pairwise_dtw(batch: Batch, opts=None, ws: Workspace | None = None) -> torch.Tensor:
     """[T, T] symmetric matrix of DTW costs between cycles."""
     lib = _abi.load()

@@ -3,8 +3,10 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/wetsand.h"
@@ -587,6 +589,85 @@ int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, fl
         return fail(WTS_EINVAL, "need 0 <= beta < 1 and eps > 0");
     cudaError_t e = launch_adam(x, grad, m, v, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+    return ok();
+}
+
+int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* workspace, size_t workspace_bytes,
+                 void* stream, wts_options* best, float* best_ms)
+{
+    if (!best) return fail(WTS_EINVAL, "best is NULL");
+    int kop, mode;
+    switch (op) {
+        case WTS_OP_ANOMALY_SCORE: kop = kOpScore; mode = kModePlen; break;
+        case WTS_OP_DTW_ALIGN: kop = kOpAlign; mode = kModeDirs; break;
+        case WTS_OP_DBA_ITERATE: kop = kOpDba; mode = kModeDirs; break;
+        default: return fail(WTS_EINVAL, "autotune supports the score, align and DBA operations");
+    }
+    int rc = check_batch(Y, true);
+    if (rc) return rc;
+    if (!B) return fail(WTS_EINVAL, "B is NULL");
+    int64_t sumN = Y->offsets_host[Y->T];
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int64_t, int, int64_t>, std::pair<wts_options, float>> cache;
+    const auto key = std::make_tuple(kop, Y->d, M, (int)Y->T, sumN);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *best = it->second.first;
+            if (best_ms) *best_ms = it->second.second;
+            return ok();
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = pick_D(Y->d);
+    std::vector<wts_options> cands;
+    for (int R : {16, 32}) {
+        if (R == 32 && D > 3) continue;
+        for (int wpb : {1, 2, 4}) {
+            wts_options o{};
+            o.rows_per_thread = R;
+            o.warps_per_block = wpb;
+            cands.push_back(o);
+        }
+    }
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return fail(WTS_ECUDA, "cudaEventCreate");
+    float best_t = 1e30f;
+    wts_options best_o{};
+    int tried = 0;
+    for (const wts_options& o : cands) {
+        Layout L;
+        if (compute_layout(kop, M, Y, &o, &L) != WTS_OK) continue;
+        if (check_ws(L, workspace, workspace_bytes) != WTS_OK) continue;
+        char* ws = (char*)workspace;
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {             // first run warms up
+            if ((rc = prepare(L, ws, B, Y, &o, st))) break;
+            DPParams p = base_params(L, ws);
+            cudaEventRecord(a, st);
+            if ((rc = launch_dp(mode, L, p, &o, st))) break;
+            cudaEventRecord(b, st);
+            if (cudaEventSynchronize(b) != cudaSuccess) { rc = fail(WTS_ECUDA, "autotune run failed"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < t_min) t_min = ms;
+        }
+        if (rc) break;
+        ++tried;
+        if (t_min < best_t) { best_t = t_min; best_o = o; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    if (!tried) return fail(WTS_ENOMEM, "no candidate fits the workspace");
+    {
+        std::lock_guard<std::mutex> g(mu);
+        cache[key] = {best_o, best_t};
+    }
+    *best = best_o;
+    if (best_ms) *best_ms = best_t;
     return ok();
 }
 
