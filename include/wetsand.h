@@ -76,7 +76,12 @@ typedef struct wts_options {
     int32_t warps_per_block;       /* 0 = 4; 1..4 */
     int32_t max_blocks;            /* 0 = as many as are resident at once (persistent grid); else a cap */
     int32_t keep_batch_order;      /* 0 = schedule the longest pairs first; 1 = batch order */
-    int32_t reserved[12];
+    int32_t dir_mode;              /* dtw_align / dba_iterate: 0 = store every cell's 2-bit code (M*N/4 bytes
+                                      per cycle); 1 = checkpoint + recompute: store only the band hand-off rows,
+                                      recompute the codes of ckpt_bands bands at a time during the backtrack
+                                      (one extra forward pass, bit-identical paths) */
+    int32_t ckpt_bands;            /* bands (of 32*rows_per_thread prototype rows) recomputed per group; 0 = 16 */
+    int32_t reserved[10];
 } wts_options;
 
 /* Library version (major * 100 + minor). */

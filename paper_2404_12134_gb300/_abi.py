@@ -41,7 +41,9 @@ class wts_options(ctypes.Structure):
         ("warps_per_block", ctypes.c_int32),
         ("max_blocks", ctypes.c_int32),
         ("keep_batch_order", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 12),
+        ("dir_mode", ctypes.c_int32),
+        ("ckpt_bands", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 10),
     ]
 
 

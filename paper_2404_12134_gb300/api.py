@@ -57,12 +57,15 @@ class Batch:
         return b
 
 
-def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0) -> wts_options:
+def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0, dir_mode=0,
+            ckpt_bands=0) -> wts_options:
     o = wts_options()
     o.rows_per_thread = rows_per_thread
     o.warps_per_block = warps_per_block
     o.max_blocks = max_blocks
     o.keep_batch_order = keep_batch_order
+    o.dir_mode = dir_mode
+    o.ckpt_bands = ckpt_bands
     return o
 
 

@@ -111,6 +111,8 @@ int check_opt(const wts_options* opt, int D)
     if (opt->rows_per_thread == 32 && D > 3) return fail(WTS_EINVAL, "rows_per_thread=32 needs d <= 3");
     if (opt->warps_per_block < 0 || opt->warps_per_block > 4) return fail(WTS_EINVAL, "warps_per_block must be 0..4");
     if (opt->max_blocks < 0) return fail(WTS_EINVAL, "max_blocks must be >= 0");
+    if (opt->dir_mode < 0 || opt->dir_mode > 1) return fail(WTS_EINVAL, "dir_mode must be 0 or 1");
+    if (opt->ckpt_bands < 0) return fail(WTS_EINVAL, "ckpt_bands must be >= 0");
     return WTS_OK;
 }
 
@@ -155,7 +157,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         const int64_t nb = cdiv(Mp, L->BR);
         items += nb;
         h += pair_hbuf_slots(nb, Np);
-        if (op == kOpAlign || op == kOpDba) dw += pair_dir_words(nb, Np, L->R);
+        if (op == kOpAlign || op == kOpDba) {
+            const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
+            dw += pair_dir_words(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
+        }
         if (op == kOpSoft) rs += pair_rstore_floats(nb, Np, L->R);
     }
     if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
@@ -173,7 +178,13 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->off_order = take((size_t)L->P * sizeof(int32_t));
     L->off_prefix = take((size_t)(L->P + 1) * sizeof(int32_t));
     L->off_hbuf = take(L->hbuf_bytes);
-    if (op == kOpAlign || op == kOpDba) L->off_dirs = take((size_t)dw * sizeof(uint32_t));
+    if (op == kOpAlign || op == kOpDba) {
+        L->off_dirs = take((size_t)dw * sizeof(uint32_t));
+        if (opt && opt->dir_mode == 1) {
+            L->group_bands = opt->ckpt_bands ? opt->ckpt_bands : 16;
+            L->off_btstate = take((size_t)L->T * 3 * sizeof(int32_t));
+        }
+    }
     if (op == kOpDba) {
         L->off_jlo = take((size_t)L->T * M * sizeof(int32_t));
         L->off_jhi = take((size_t)L->T * M * sizeof(int32_t));
@@ -237,6 +248,7 @@ int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const
     sp.order = reinterpret_cast<int32_t*>(ws + L.off_order);
     sp.prefix = reinterpret_cast<int32_t*>(ws + L.off_prefix);
     sp.sort = (opt && opt->keep_batch_order) ? 0 : 1;
+    sp.group_bands = L.group_bands;
     {
         Prof pr("setup", st);
         launch_setup(sp, st);
@@ -246,8 +258,9 @@ int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const
     return WTS_OK;
 }
 
-int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* block)
+int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* block, int64_t n_items = -1)
 {
+    if (n_items < 0) n_items = L.n_items;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -256,7 +269,7 @@ int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* 
     int occ = dtw_wavefront_max_blocks_per_sm(mode, L.D, L.R, *block);
     if (occ < 1) return fail(WTS_ECUDA, "no resident block for D=%d R=%d block=%d", L.D, L.R, *block);
     int64_t g = (int64_t)occ * di.sms;
-    const int64_t need = (L.n_items + wpb - 1) / wpb;
+    const int64_t need = (n_items + wpb - 1) / wpb;
     if (g > need) g = need;
     if (opt && opt->max_blocks && g > opt->max_blocks) g = opt->max_blocks;
     *grid = (int)(g < 1 ? 1 : g);
@@ -282,11 +295,11 @@ DPParams base_params(const Layout& L, char* ws)
 int launch_dp(int mode, const Layout& L, const DPParams& p, const wts_options* opt, cudaStream_t st)
 {
     int grid = 0, block = 0;
-    int rc = grid_for(mode, L, opt, &grid, &block);
+    int rc = grid_for(mode, L, opt, &grid, &block, p.n_items);
     if (rc) return rc;
     cudaError_t e;
     {
-        Prof pr("wavefront", st);
+        Prof pr(p.recompute ? "wavefront_recompute" : "wavefront", st);
         e = launch_dtw_wavefront(mode, L.D, L.R, p, grid, block, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "wavefront launch");
@@ -301,8 +314,6 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
     if (rc) return rc;
     DPParams p = base_params(L, ws);
     p.cost_out = cost;
-    rc = launch_dp(kModeDirs, L, p, opt, st);
-    if (rc) return rc;
     BTParams bt{};
     bt.pairs = p.pairs;
     bt.P = L.P;
@@ -313,11 +324,50 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
     bt.plen = plen;
     bt.M = L.M;
     cudaError_t e;
-    {
-        Prof pr("backtrack", st);
-        e = launch_backtrack(bt, st);
+    if (L.group_bands == 0) {
+        // every cell's code stored, one backtrack
+        rc = launch_dp(kModeDirs, L, p, opt, st);
+        if (rc) return rc;
+        bt.band_lo = 0;
+        bt.band_hi = (int)cdiv(L.M, L.BR);
+        {
+            Prof pr("backtrack", st);
+            e = launch_backtrack(bt, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+        return WTS_OK;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+    // checkpoint mode: a cost-only pass leaves every band's bottom row in the
+    // hand-off rows; then, from the last band up, the codes of G bands (all
+    // pairs at once) are recomputed from those rows and the walk continues
+    // through them
+    rc = launch_dp(kModeCost, L, p, opt, st);
+    if (rc) return rc;
+    const int nb = (int)cdiv(L.M, L.BR);
+    const int G = L.group_bands;
+    bt.state = reinterpret_cast<int32_t*>(ws + L.off_btstate);
+    for (int hi = nb; hi > 0; hi -= G) {
+        const int lo = hi - G > 0 ? hi - G : 0;
+        DPParams r = p;
+        r.recompute = 1;
+        r.band_lo = lo;
+        r.band_cnt = hi - lo;
+        r.n_items = L.P * (hi - lo);
+        r.cost_out = nullptr;
+        // every launch starts the work-list cursor from zero
+        e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
+        rc = launch_dp(kModeDirs, L, r, opt, st);
+        if (rc) return rc;
+        bt.band_lo = lo;
+        bt.band_hi = hi;
+        bt.first = hi == nb;
+        {
+            Prof pr("backtrack", st);
+            e = launch_backtrack(bt, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+    }
     return WTS_OK;
 }
 

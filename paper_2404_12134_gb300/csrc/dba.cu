@@ -61,9 +61,17 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
         const int N = pd.N;
         int32_t* jlo = p.jlo + (int64_t)pd.out * p.M;
         int32_t* jhi = p.jhi + (int64_t)pd.out * p.M;
-        int i = pd.M - 1, j = N - 1, len = 0;
+        int i, j, len;
+        if (p.state == nullptr || p.first) {
+            i = pd.M - 1; j = N - 1; len = 0;
+            if (lane == 0) jhi[i] = j;
+        } else {
+            i = p.state[3 * q]; j = p.state[3 * q + 1]; len = p.state[3 * q + 2];
+            if (i < 0 || len < 0) continue;          // finished, or failed earlier
+        }
+        const int i_lo = p.band_lo * 32 * R;
         int band = -1, wlo = 0, whi = -1;
-        if (lane == 0) jhi[i] = j;
+        bool left_group = false;
         for (;;) {
             ++len;
             if (i == 0 && j == 0) break;
@@ -75,7 +83,8 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
                 band = b;
                 whi = s;
                 wlo = max(0, s - kBtWin + 1);
-                const uint32_t* src = p.dirs + pd.dir_off + (int64_t)b * (N + 31) * 32 * W + (int64_t)wlo * 32 * W;
+                const uint32_t* src = p.dirs + pd.dir_off + (int64_t)(b - p.band_lo) * (N + 31) * 32 * W +
+                                      (int64_t)wlo * 32 * W;
                 const uint32_t bytes = (uint32_t)(whi - wlo + 1) * 32 * W * 4;
                 __syncwarp();
                 if (lane == 0) {
@@ -116,10 +125,16 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             } else {
                 --j;
             }
+            if (i < i_lo) { left_group = true; break; }    // the rest lies in bands not loaded
+        }
+        if (left_group) {
+            if (lane == 0) { p.state[3 * q] = i; p.state[3 * q + 1] = j; p.state[3 * q + 2] = len; }
+            continue;
         }
         if (lane == 0) {
-            if (i == 0 && j == 0) jlo[0] = 0;
+            if (i == 0 && j == 0 && len > 0) jlo[0] = 0;
             if (p.plen) p.plen[pd.out] = len;
+            if (p.state) { p.state[3 * q] = -1; p.state[3 * q + 2] = len; }
         }
     }
 }

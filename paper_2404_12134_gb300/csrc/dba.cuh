@@ -15,6 +15,13 @@ struct BTParams {
     int32_t* jhi;
     int32_t* plen;       // [P] (may be null)
     int64_t M;           // row stride of jlo/jhi
+    // codes available for bands [band_lo, band_hi) only (band b at dirs offset
+    // b - band_lo); the walk stops on leaving them and keeps its position in
+    // state[3*q .. 3*q+2] = (i, j, cells so far), resumed by the next call.
+    // state == null: all bands, one walk.
+    int band_lo, band_hi;
+    int32_t* state;
+    int first;           // 1: start every walk at (M-1, N-1)
 };
 
 cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st);

@@ -228,8 +228,10 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     constexpr int SLOT = MODE == kModePlen ? 8 : 4;
     char* hb = static_cast<char*>(p.hbuf);
     const char* hprev = top ? nullptr : hb + (pd.hbuf_off + (int64_t)(band - 1) * N) * SLOT;
-    void* hcur = last ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
-    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)band * (N + 31) * 32 * W : nullptr;
+    // a recomputed band reads its stored top row and produces no hand-off row
+    void* hcur = (last || p.recompute) ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
+    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * W
+                                         : nullptr;
 
     // Cycle samples go through the ring two chunks of 32 columns ahead of the
     // step that first reads them (a step also reads the next column), loaded
@@ -295,7 +297,7 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
         }
     }
 
-    if (last) {
+    if (last && !p.recompute) {
         const int ilast = M - 1 - band * BR;
         if (lane == ilast / R) {
             const int kk = ilast % R;
@@ -338,9 +340,16 @@ __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(
         item = __shfl_sync(FULL, item, 0);
         if (item >= p.n_items) break;
         if (ld_volatile(&p.hdr->abort)) break;
-        const int q = find_slot(p.prefix, p.P, item);
+        int q, band;
+        if (p.recompute) {
+            q = item / p.band_cnt;
+            band = p.band_lo + item % p.band_cnt;
+        } else {
+            q = find_slot(p.prefix, p.P, item);
+            band = item - p.prefix[q];
+        }
         const PairDesc pd = p.pairs[p.order[q]];
-        run_band<D, R, MODE>(p, pd, item - p.prefix[q], lane, ring);
+        run_band<D, R, MODE>(p, pd, band, lane, ring);
     }
 }
 

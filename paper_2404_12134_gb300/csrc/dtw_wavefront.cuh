@@ -29,6 +29,10 @@ struct DPParams {
     float* cost_matrix;  // pairwise mode: [T][T] symmetric, written at (a,b) and (b,a) (may be null)
     int T;               // cycles (pairwise index decode)
     const int32_t* subset;  // pairwise subset (may be null)
+    // checkpoint recomputation: run only bands [band_lo, band_lo + band_cnt) of
+    // every pair, from their stored top rows, writing codes relative to band_lo
+    int recompute;
+    int band_lo, band_cnt;
 };
 
 // Launch the persistent wavefront for D (padded channels) and R (rows/lane).

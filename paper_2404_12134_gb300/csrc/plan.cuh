@@ -41,7 +41,8 @@ struct Layout {
     int64_t hbuf_slots = 0, dir_words = 0, rstore_floats = 0;
     size_t hbuf_bytes = 0, ebuf_bytes = 0;
     size_t off_hdr = 0, off_pairs = 0, off_order = 0, off_prefix = 0;
-    size_t off_hbuf = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0;
+    size_t off_hbuf = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0, off_btstate = 0;
+    int group_bands = 0;  // checkpoint mode: bands whose codes are recomputed at a time (0 = codes stored)
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
     size_t total = 0;
 };
@@ -58,6 +59,7 @@ struct SetupParams {
     int32_t* order;            // [P] longest first
     int32_t* prefix;           // [P+1] first item of the q-th pair in order
     int sort;                  // 1: order longest-first, 0: identity
+    int group_bands;           // > 0: directions for only this many bands per pair (checkpoint mode)
 };
 
 void launch_setup(const SetupParams& sp, cudaStream_t st);

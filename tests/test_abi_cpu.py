@@ -92,3 +92,18 @@ def test_validation_errors(lib):
     assert rc == _abi.WTS_ENOMEM
     rc = lib.dba_iterate(256, 256, 8, ctypes.byref(b), None, 256, 1 << 30, None, None, None, None)
     assert rc == _abi.WTS_EINVAL and b"alias" in lib.wts_last_error()
+
+
+def test_checkpoint_mode_shrinks_workspace(lib):
+    b, offs = _batch([110000] * 4, d=3)
+    o = _abi.wts_options()
+    rc, stored = _size(lib, _abi.OP_DBA_ITERATE, 110000, b)
+    o.dir_mode = 1
+    o.ckpt_bands = 16
+    rc2, ckpt = _size(lib, _abi.OP_DBA_ITERATE, 110000, b, o)
+    assert rc == 0 and rc2 == 0
+    # codes: M*N/4 bytes per cycle stored, vs 16 bands of 512 rows recomputed at a time
+    assert stored > 4 * 110000 * 110000 / 4
+    assert ckpt < stored / 8
+    o.dir_mode = 2
+    assert _size(lib, _abi.OP_DBA_ITERATE, 110000, b, o)[0] == _abi.WTS_EINVAL

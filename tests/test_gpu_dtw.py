@@ -169,3 +169,35 @@ def test_full_size_sampled_pair(wts):
         assert int((jhi[k] - jlo[k] + 1).sum()) == plen[k]
     s, c, L = wts.anomaly_score(torch.from_numpy(B).cuda(), gb)
     assert (c.cpu().numpy() == cost).all() and (L.cpu().numpy() == plen).all()
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 16])
+def test_checkpoint_recompute_paths_identical(wts, G):
+    """dir_mode=1 keeps only the band hand-off rows and recomputes G bands of
+    codes at a time during the backtrack: same paths, costs and |pi|."""
+    rng = np.random.default_rng(104)
+    cyc = [rng.normal(size=(n, 3)).astype(np.float32) for n in (5, 800, 1777, 2100)]
+    B = rng.normal(size=(2600, 3)).astype(np.float32)          # 6 bands of 512 rows, ragged last band
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    Bt = torch.from_numpy(B).cuda()
+    ref = [t.cpu().numpy() for t in wts.dtw_align(Bt, gb)]
+    got = [t.cpu().numpy() for t in wts.dtw_align(Bt, gb, wts.options(dir_mode=1, ckpt_bands=G))]
+    for a, b in zip(ref, got):
+        assert (a == b).all()
+    r = oracle.dtw(B, cyc[3], "f32")
+    assert (got[2][3] == r["jlo"]).all() and (got[3][3] == r["jhi"]).all() and got[1][3] == r["plen"]
+
+
+def test_checkpoint_dba_identical(wts):
+    b = synth.config_batch(1, scale=0.05, T=12)
+    gb = _gb(wts, b.data, b.offsets)
+    B = synth.clean_prototype(b, 1300)
+    Bs = torch.from_numpy(B).cuda()
+    Bc = Bs.clone()
+    opt = wts.options(dir_mode=1, ckpt_bands=2)
+    for it in range(3):
+        Bs2, cs, cbs, _ = wts.dba_iterate(Bs, gb)
+        Bc2, cc, cbc, _ = wts.dba_iterate(Bc, gb, opt)
+        assert torch.equal(Bs2, Bc2) and torch.equal(cs, cc) and float(cbs) == float(cbc), it
+        Bs, Bc = Bs2, Bc2
