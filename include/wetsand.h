@@ -176,7 +176,9 @@ int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, 
  *     m - gamma ln(sum_i exp(-(a_i - m)/gamma)),  m = min_i a_i,
  * with the hardware ex2 / lg2 approximations, in FP32.  Every r(i,j) is kept
  * in the workspace for softdtw_backward (4 bytes per cell plus a skew
- * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)).
+ * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)); with opt->dir_mode = 1
+ * only the band hand-off rows are kept and softdtw_backward recomputes R for
+ * ckpt_bands bands at a time (one extra forward pass).
  *   B [M][d] (d <= 8), gamma > 0 (gamma = 0 is DTW: use anomaly_score),
  *   value [T] out.
  */

@@ -161,7 +161,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
             dw += pair_dir_words(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
         }
-        if (op == kOpSoft) rs += pair_rstore_floats(nb, Np, L->R);
+        if (op == kOpSoft) {
+            const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
+            rs += pair_rstore_floats(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
+        }
     }
     if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
     L->n_items = items;
@@ -191,6 +194,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         L->off_costs = take((size_t)L->T * sizeof(float));
     }
     if (op == kOpSoft) {
+        if (opt && opt->dir_mode == 1) L->group_bands = opt->ckpt_bands ? opt->ckpt_bands : 16;
         L->off_rstore = take((size_t)rs * sizeof(float));
         L->off_gpart = take((size_t)L->T * M * D * sizeof(float));
         L->off_ebuf = take(L->ebuf_bytes);
@@ -389,8 +393,9 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma)
     return p;
 }
 
-int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block)
+int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block, int64_t n_items = -1)
 {
+    if (n_items < 0) n_items = L.n_items;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -399,7 +404,7 @@ int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, 
     const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block);
     if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
     int64_t g = (int64_t)occ * di.sms;
-    const int64_t need = (L.n_items + wpb - 1) / wpb;
+    const int64_t need = (n_items + wpb - 1) / wpb;
     if (g > need) g = need;
     if (opt && opt->max_blocks && g > opt->max_blocks) g = opt->max_blocks;
     *grid = (int)(g < 1 ? 1 : g);
@@ -587,6 +592,7 @@ int softdtw_forward(const float* B, int64_t M, const wts_batch* Y, float gamma, 
     if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
     SoftParams p = soft_params(L, ws, gamma);
     p.value_out = value;
+    p.store_r = L.group_bands == 0;      // checkpoint mode keeps only the hand-off rows
     int grid = 0, block = 0;
     if ((rc = soft_grid(L, 0, opt, &grid, &block))) return rc;
     cudaError_t e;
@@ -616,12 +622,46 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward hand-off rows)");
     SoftParams p = soft_params(L, ws, gamma);
     int grid = 0, block = 0;
-    if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;
-    {
-        Prof pr("softdtw_bwd", st);
-        e = launch_softdtw_bwd(L.D, p, grid, block, st);
+    if (L.group_bands == 0) {
+        if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;
+        {
+            Prof pr("softdtw_bwd", st);
+            e = launch_softdtw_bwd(L.D, p, grid, block, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
+    } else {
+        // checkpoint mode: from the last band up, recompute R for G bands of
+        // every pair from the stored hand-off rows, then run the backward
+        // recursion through them; E hand-off rows persist across groups
+        const int nb = (int)cdiv(M, L.BR);
+        const int G = L.group_bands;
+        for (int hi = nb; hi > 0; hi -= G) {
+            const int lo = hi - G > 0 ? hi - G : 0;
+            SoftParams r = p;
+            r.band_lo = lo;
+            r.band_cnt = hi - lo;
+            r.n_items = L.P * (hi - lo);
+            r.recompute = 1;
+            r.store_r = 1;
+            e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
+            if ((rc = soft_grid(L, 0, opt, &grid, &block, r.n_items))) return rc;
+            {
+                Prof pr("softdtw_fwd_recompute", st);
+                e = launch_softdtw_fwd(L.D, r, grid, block, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "soft-DTW recompute launch");
+            r.recompute = 0;
+            e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
+            if ((rc = soft_grid(L, 1, opt, &grid, &block, r.n_items))) return rc;
+            {
+                Prof pr("softdtw_bwd", st);
+                e = launch_softdtw_bwd(L.D, r, grid, block, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
+        }
     }
-    if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
     {
         Prof pr("softdtw_grad", st);
         e = launch_softdtw_grad_reduce(p.gpart, grad_value, L.T, M, L.d, grad_B, st);

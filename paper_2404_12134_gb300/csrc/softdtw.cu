@@ -102,8 +102,8 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     float prev_up = (top && lane == 0) ? 0.f : INF;
 
     const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
-    float* hcur = last ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
-    float* rs = p.rstore + pd.aux_off + (int64_t)band * (N + 31) * 32 * R;
+    float* hcur = (last || p.recompute) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
+    float* rs = p.store_r ? p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R : nullptr;
 
     // lane-0 feeds one chunk of 32 columns ahead (the top row is NaN until written)
     float ynext[D];
@@ -164,13 +164,15 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
             }
             if (hcur != nullptr && lane == 31) __stcg(hcur + j, col[R - 1]);
         }
-        float4* dst = reinterpret_cast<float4*>(rs + (int64_t)s * 32 * R);
+        if (rs != nullptr) {
+            float4* dst = reinterpret_cast<float4*>(rs + (int64_t)s * 32 * R);
 #pragma unroll
-        for (int k4 = 0; k4 < R / 4; ++k4)
-            dst[k4 * 32 + lane] = make_float4(col[4 * k4], col[4 * k4 + 1], col[4 * k4 + 2], col[4 * k4 + 3]);
+            for (int k4 = 0; k4 < R / 4; ++k4)
+                dst[k4 * 32 + lane] = make_float4(col[4 * k4], col[4 * k4 + 1], col[4 * k4 + 2], col[4 * k4 + 3]);
+        }
     }
 
-    if (last) {
+    if (last && !p.recompute) {
         const int ilast = M - 1 - band * BR;
         if (lane == ilast / R) {
             const int kk2 = ilast % R;
@@ -216,7 +218,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // words {r, delta} and {e, 0}, each NaN until written
     const u64* enext = last ? nullptr : reinterpret_cast<const u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)band * N);
     u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
-    const float* rs = p.rstore + pd.aux_off + (int64_t)band * (N + 31) * 32 * R;
+    const float* rs = p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R;
 
     // R of this lane's rows at the column of step ss (written by forward step
     // N+30-ss), loaded one step ahead of its use
@@ -346,11 +348,21 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
         item = __shfl_sync(FULL, item, 0);
         if (item >= p.n_items) break;
         if (ld_volatile(&p.hdr->abort)) break;
-        const int q = find_slot(p.prefix, p.P, item);
+        int q, k;
+        if (p.band_cnt > 0) {                 // a band range of every pair
+            q = item / p.band_cnt;
+            k = item % p.band_cnt;
+        } else {
+            q = find_slot(p.prefix, p.P, item);
+            k = item - p.prefix[q];
+        }
         const PairDesc pd = p.pairs[p.order[q]];
-        const int k = item - p.prefix[q];
-        if (BWD) bwd_band<D, R>(p, pd, pd.nbands - 1 - k, lane);
-        else fwd_band<D, R>(p, pd, k, lane);
+        if (BWD) {
+            // bands bottom-up: the whole pair, or the range's last band first
+            bwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane);
+        } else {
+            fwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
+        }
     }
 }
 

@@ -21,6 +21,12 @@ struct SoftParams {
     float* rstore;       // R, per band [(N+31) steps][R/4][32 lanes][4]
     float* value_out;    // [P] Soft-DTW value per pair (forward)
     float* gpart;        // [P][M][d] per-pair gradient sum_j e_ij * 2 (b_i - y_j) (backward)
+    // checkpoint mode: R is kept only for bands [band_lo, band_lo + band_cnt)
+    // (band b at R offset b - band_lo); the forward then recomputes those
+    // bands from their stored top rows (recompute = 1, no hand-off writes)
+    int store_r;         // forward: write R
+    int recompute;
+    int band_lo, band_cnt;
 };
 
 // Rows held per lane by the soft-DTW kernels for a padded channel count D.

@@ -130,3 +130,24 @@ def test_gamma_validation(wts):
     from paper_2404_12134_gb300._abi import WtsError
     with pytest.raises(WtsError):
         wts.softdtw_forward(torch.from_numpy(B).cuda(), gb, 0.0)
+
+
+@pytest.mark.parametrize("G", [1, 3])
+def test_checkpoint_mode_identical(wts, G):
+    """dir_mode=1 keeps only the band hand-off rows; softdtw_backward
+    recomputes R for G bands at a time: values and gradients identical."""
+    B, b = _case(10, 1100, [900, 1300, 77], 1)       # 3 bands of 512 rows (16 rows per lane, d = 1)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    w = torch.from_numpy((1.0 / b.lengths).astype(np.float32)).cuda()
+    ws = wts.Workspace()
+    v0 = wts.softdtw_forward(Bt, gb, 0.3, ws=ws)
+    g0 = wts.softdtw_backward(Bt, gb, 0.3, w, ws=ws)
+    opt = wts.options(dir_mode=1, ckpt_bands=G)
+    ws1 = wts.Workspace()
+    v1 = wts.softdtw_forward(Bt, gb, 0.3, opt, ws=ws1)
+    g1 = wts.softdtw_backward(Bt, gb, 0.3, w, opt, ws=ws1)
+    assert torch.equal(v0, v1) and torch.equal(g0, g1)
+    s_ck = wts.workspace_size(wts._abi.OP_SOFTDTW, 1100, gb, opt)
+    s_st = wts.workspace_size(wts._abi.OP_SOFTDTW, 1100, gb)
+    assert s_ck < s_st if G < 3 else s_ck == s_st
