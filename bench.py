@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--T", type=int, default=200, help="cycles (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
-    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score"],
+    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long"],
                     help="soft / score: only that leg (soft: with --T cycles of its workload); for profiling")
     return ap.parse_args()
 
@@ -277,6 +277,70 @@ def scoring_leg(api, torch, dev, barrier, T: int | None = None, per_pair: bool =
     return res
 
 
+def long_leg(api, torch, dev, barrier, iters: int = 2):
+    """Very long cycles: 32 cycles x 3 ch, pre-gap N ~ U(100k, 120k), M =
+    110,000 (medoid of a seeded 8-cycle subset, resampled; untimed).  DBA with
+    every code stored (~95 GB) against checkpoint mode (band rows kept, codes
+    recomputed 16 bands at a time), and soft-DTW forward + backward on 8 of the
+    pairs with checkpointing (stored R would take ~390 GB)."""
+    b = synth.config_batch(4)
+    M = synth.PROTO_LEN[4]
+    gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
+    cells = M * int(b.lengths.sum())
+    sub = b.subset(np.arange(8))
+    gsub = api.Batch.from_numpy(sub.data, sub.offsets, device=dev)
+    idx, _ = api.medoid(api.pairwise_dtw(gsub))
+    k = int(idx)
+    B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M)
+    res = {"workload": "32 cycles x 3 ch FP32, pre-gap N ~ U(100k,120k), 2% gaps, M=110000", "cells_per_iter": cells}
+    outs = {}
+    from paper_2404_12134_gb300 import _abi
+    tuned, _ = api.autotune(_abi.OP_DBA_ITERATE, B0, gb)
+    res["options"] = {"rows_per_thread": tuned.rows_per_thread, "warps_per_block": tuned.warps_per_block}
+    for name, mode in (("stored", 0), ("checkpoint", 1)):
+        opt = api.options(rows_per_thread=tuned.rows_per_thread, warps_per_block=tuned.warps_per_block,
+                          dir_mode=mode, ckpt_bands=16)
+        ws = api.Workspace(dev)
+        B = B0.clone()
+        Bn, cnt, cb, _ = api.dba_iterate(B, gb, opt, ws=ws)          # warm-up
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(iters):
+            Bn, cnt, cb, _ = api.dba_iterate(B, gb, opt, ws=ws)
+            B, Bn = Bn, B
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1) / iters
+        outs[name] = B.clone()
+        res[name] = {"s_per_dba_iter": ms * 1e-3, "gcups": cells / (ms * 1e-3) / 1e9,
+                     "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf)}
+        del ws
+    res["checkpoint_prototype_identical"] = bool(torch.equal(outs["stored"], outs["checkpoint"]))
+    # soft-DTW forward + backward, 8 pairs, checkpointed (64 bands of R per group)
+    gamma = 0.1
+    opt = api.options(dir_mode=1, ckpt_bands=64)
+    ws = api.Workspace(dev)
+    w = torch.from_numpy((1.0 / sub.lengths).astype(np.float32)).to(dev)
+    api.softdtw_forward(B0, gsub, gamma, opt, ws=ws)
+    api.softdtw_backward(B0, gsub, gamma, w, opt, ws=ws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True); e2 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.softdtw_forward(B0, gsub, gamma, opt, ws=ws)
+    e1.record()
+    api.softdtw_backward(B0, gsub, gamma, w, opt, ws=ws)
+    e2.record()
+    barrier()
+    scells = M * int(sub.lengths.sum())
+    f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    res["softdtw_checkpoint"] = {"pairs": 8, "gamma": gamma, "ckpt_bands": 64, "cells": scells, "fwd_ms": f_ms,
+                                 "bwd_incl_recompute_ms": b_ms, "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
+                                 "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf)}
+    del ws
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -297,6 +361,13 @@ def run_gpu(args):
         res = scoring_leg(api, torch, dev, sync, T=args.T if args.T != 200 else None)
         if rank == 0:
             print(json.dumps({"leg": "score", "scoring": res}), flush=True)
+        return 0
+    if args.leg == "long":
+        def sync():
+            torch.cuda.synchronize()
+        res = long_leg(api, torch, dev, sync)
+        if rank == 0:
+            print(json.dumps({"leg": "long", "long": res}), flush=True)
         return 0
     if args.leg == "soft":
         def sync():
@@ -320,6 +391,8 @@ def run_gpu(args):
     del C, gsub
 
     ws = api.Workspace(dev)
+    from paper_2404_12134_gb300 import _abi
+    opts, _ = api.autotune(_abi.OP_DBA_ITERATE, B0, gb, ws)     # untimed, cached
     B = B0.clone()
     Bn = torch.empty_like(B)
     counts = torch.empty(M_PROTO, dtype=torch.int32, device=dev)
@@ -329,7 +402,7 @@ def run_gpu(args):
 
     def step():
         nonlocal B, Bn
-        api.dba_iterate(B, gb, ws=ws, B_out=Bn, counts=counts, cost_before=cb, cost=cost)
+        api.dba_iterate(B, gb, opts, ws=ws, B_out=Bn, counts=counts, cost_before=cb, cost=cost)
         B, Bn = Bn, B
 
     for _ in range(args.warmup):
@@ -383,6 +456,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": b.T, "d": b.d, "M": M_PROTO, "cells_per_step": cells,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "options": {"rows_per_thread": opts.rows_per_thread, "warps_per_block": opts.warps_per_block},
                    "l2": "no flush: each step writes ~31 GB of predecessor codes (>> 129 MB L2)"},
         "s_per_dba_iter": ms / args.steps * 1e-3,
         "dba_cost_after_warmup_and_steps": dba_cost,
@@ -401,7 +475,7 @@ def run_gpu(args):
     achieved = ops / wf_avg_s / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s (FP32 lane ops)",
                        "frac": achieved / peak, "traffic": None,
-                       "kernel": "dtw_wavefront_kernel<D=6,R=16,dirs>",
+                       "kernel": f"dtw_wavefront_kernel<D=6,R={opts.rows_per_thread},dirs>",
                        "peak_note": f"{sms} SMs x 128 FP32 lanes x 2070 MHz (max SM clock)"}
     out["kernel_ms_per_step"] = {"wavefront": wf_ms / args.steps, "backtrack": bt_ms / args.steps,
                                  "dba_average": av_ms / args.steps, "other": rest_ms / args.steps}
@@ -422,7 +496,7 @@ def run_gpu(args):
     def e2e_step():
         d_data.copy_(h_data, non_blocking=True)
         d_B.copy_(h_B, non_blocking=True)
-        api.dba_iterate(d_B, gb_e2e, ws=ws, B_out=Bn, counts=counts, cost_before=cb, cost=cost)
+        api.dba_iterate(d_B, gb_e2e, opts, ws=ws, B_out=Bn, counts=counts, cost_before=cb, cost=cost)
         h_out.copy_(Bn, non_blocking=True)
         h_cost.copy_(cb, non_blocking=True)
 
