@@ -55,6 +55,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's value (whole-job time is set by the last rank to
+    finish); identity on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload(T: int):
     b = synth.config_batch(1, T=T)
     rng = np.random.default_rng(synth.SEED_BASE + 77)
@@ -440,11 +452,7 @@ def run_gpu(args):
     av_ms, av_n = api.profile_read("dba_average")
     rest_ms, rest_n = api.profile_read("")
     launches = wf_n + bt_n + av_n + rest_n
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     status = api.read_status(ws.buf)
     value = world * cells * args.steps / (ms * 1e-3) / 1e9
     dba_cost = float(cb.item())

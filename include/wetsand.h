@@ -81,7 +81,11 @@ typedef struct wts_options {
                                       recompute the codes of ckpt_bands bands at a time during the backtrack
                                       (one extra forward pass, bit-identical paths) */
     int32_t ckpt_bands;            /* bands (of 32*rows_per_thread prototype rows) recomputed per group; 0 = 16 */
-    int32_t reserved[10];
+    int32_t spin_limit;            /* polls before an in-kernel wait gives up (each ~0.1-1 us); 0 = 2^27 */
+    int32_t fault_skip_handoff;    /* fault injection for tests: 1 = producers skip their hand-off rows, so
+                                      consumers wait until spin_limit and the call ends with WTS_ETIMEOUT in
+                                      the workspace status; never set it otherwise */
+    int32_t reserved[8];
 } wts_options;
 
 /* Library version (major * 100 + minor). */

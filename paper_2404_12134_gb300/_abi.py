@@ -43,7 +43,9 @@ class wts_options(ctypes.Structure):
         ("keep_batch_order", ctypes.c_int32),
         ("dir_mode", ctypes.c_int32),
         ("ckpt_bands", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 10),
+        ("spin_limit", ctypes.c_int32),
+        ("fault_skip_handoff", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 8),
     ]
 
 

@@ -58,7 +58,7 @@ class Batch:
 
 
 def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0, dir_mode=0,
-            ckpt_bands=0) -> wts_options:
+            ckpt_bands=0, spin_limit=0, fault_skip_handoff=0) -> wts_options:
     o = wts_options()
     o.rows_per_thread = rows_per_thread
     o.warps_per_block = warps_per_block
@@ -66,6 +66,8 @@ def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order
     o.keep_batch_order = keep_batch_order
     o.dir_mode = dir_mode
     o.ckpt_bands = ckpt_bands
+    o.spin_limit = spin_limit
+    o.fault_skip_handoff = fault_skip_handoff
     return o
 
 

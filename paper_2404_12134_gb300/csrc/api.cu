@@ -113,6 +113,7 @@ int check_opt(const wts_options* opt, int D)
     if (opt->max_blocks < 0) return fail(WTS_EINVAL, "max_blocks must be >= 0");
     if (opt->dir_mode < 0 || opt->dir_mode > 1) return fail(WTS_EINVAL, "dir_mode must be 0 or 1");
     if (opt->ckpt_bands < 0) return fail(WTS_EINVAL, "ckpt_bands must be >= 0");
+    if (opt->spin_limit < 0) return fail(WTS_EINVAL, "spin_limit must be >= 0");
     return WTS_OK;
 }
 
@@ -280,9 +281,16 @@ int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* 
     return WTS_OK;
 }
 
-DPParams base_params(const Layout& L, char* ws)
+long long spin_limit_of(const wts_options* opt)
+{
+    return (opt && opt->spin_limit > 0) ? (long long)opt->spin_limit : kSpinLimit;
+}
+
+DPParams base_params(const Layout& L, char* ws, const wts_options* opt = nullptr)
 {
     DPParams p{};
+    p.spin_limit = spin_limit_of(opt);
+    p.skip_handoff = (opt && opt->fault_skip_handoff) ? 1 : 0;
     p.pairs = reinterpret_cast<const PairDesc*>(ws + L.off_pairs);
     p.order = reinterpret_cast<const int32_t*>(ws + L.off_order);
     p.prefix = reinterpret_cast<const int32_t*>(ws + L.off_prefix);
@@ -316,7 +324,7 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
 {
     int rc = prepare(L, ws, B, Y, opt, st);
     if (rc) return rc;
-    DPParams p = base_params(L, ws);
+    DPParams p = base_params(L, ws, opt);
     p.cost_out = cost;
     BTParams bt{};
     bt.pairs = p.pairs;
@@ -375,9 +383,11 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
     return WTS_OK;
 }
 
-SoftParams soft_params(const Layout& L, char* ws, float gamma)
+SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options* opt = nullptr)
 {
     SoftParams p{};
+    p.spin_limit = spin_limit_of(opt);
+    p.skip_handoff = (opt && opt->fault_skip_handoff) ? 1 : 0;
     p.pairs = reinterpret_cast<const PairDesc*>(ws + L.off_pairs);
     p.order = reinterpret_cast<const int32_t*>(ws + L.off_order);
     p.prefix = reinterpret_cast<const int32_t*>(ws + L.off_prefix);
@@ -505,7 +515,7 @@ int anomaly_score(const float* B, int64_t M, const wts_batch* Y, const wts_optio
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
-    DPParams p = base_params(L, ws);
+    DPParams p = base_params(L, ws, opt);
     p.cost_out = cost;
     p.plen_out = plen;
     p.score_out = score;
@@ -571,7 +581,7 @@ int wts_pairwise_dtw(const wts_batch* Y, const wts_options* opt, void* workspace
     cudaError_t e = cudaMemsetAsync(C, 0, (size_t)L.T * L.T * sizeof(float), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(C)");
     if ((rc = prepare(L, ws, nullptr, Y, opt, st))) return rc;
-    DPParams p = base_params(L, ws);
+    DPParams p = base_params(L, ws, opt);
     p.cost_matrix = C;
     if ((rc = launch_dp(kModeCost, L, p, opt, st))) return rc;
     return ok();
@@ -590,7 +600,7 @@ int softdtw_forward(const float* B, int64_t M, const wts_batch* Y, float gamma, 
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
-    SoftParams p = soft_params(L, ws, gamma);
+    SoftParams p = soft_params(L, ws, gamma, opt);
     p.value_out = value;
     p.store_r = L.group_bands == 0;      // checkpoint mode keeps only the hand-off rows
     int grid = 0, block = 0;
@@ -620,7 +630,7 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     cudaError_t e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
     if (e == cudaSuccess && L.ebuf_bytes) e = cudaMemsetAsync(ws + L.off_ebuf, 0xFF, L.ebuf_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward hand-off rows)");
-    SoftParams p = soft_params(L, ws, gamma);
+    SoftParams p = soft_params(L, ws, gamma, opt);
     int grid = 0, block = 0;
     if (L.group_bands == 0) {
         if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;
@@ -735,7 +745,7 @@ int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* wo
         float t_min = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {             // first run warms up
             if ((rc = prepare(L, ws, B, Y, &o, st))) break;
-            DPParams p = base_params(L, ws);
+            DPParams p = base_params(L, ws, &o);
             cudaEventRecord(a, st);
             if ((rc = launch_dp(mode, L, p, &o, st))) break;
             cudaEventRecord(b, st);
@@ -852,7 +862,7 @@ extern "C" int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch*
     char* ws = (char*)scratch;
     // prepare() zeroes the header and progress counters left by the previous call
     if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
-    DPParams p = base_params(L, ws);
+    DPParams p = base_params(L, ws, opt);
     p.cost_out = cost;
     p.plen_out = plen;
     p.score_out = score;

@@ -229,7 +229,7 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     char* hb = static_cast<char*>(p.hbuf);
     const char* hprev = top ? nullptr : hb + (pd.hbuf_off + (int64_t)(band - 1) * N) * SLOT;
     // a recomputed band reads its stored top row and produces no hand-off row
-    void* hcur = (last || p.recompute) ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
+    void* hcur = (last || p.recompute || p.skip_handoff) ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
     uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * W
                                          : nullptr;
 
@@ -281,7 +281,8 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
             if (!top) {
                 u64 t = tnext;
                 const bool ok = wait_filled(jj < N && is_nan_bits((uint32_t)t),
-                                            [&]() { t = load_t(jj); return is_nan_bits((uint32_t)t); }, p.hdr, 1);
+                                            [&]() { t = load_t(jj); return is_nan_bits((uint32_t)t); }, p.hdr, 1,
+                                            p.spin_limit);
                 if (!ok) return;
                 st.topv = jj < N ? __uint_as_float((uint32_t)t) : INF;
                 if (MODE == kModePlen) st.topc = (int)(t >> 32);

@@ -33,6 +33,8 @@ struct DPParams {
     // every pair, from their stored top rows, writing codes relative to band_lo
     int recompute;
     int band_lo, band_cnt;
+    long long spin_limit;    // polls before a wait gives up
+    int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
 };
 
 // Launch the persistent wavefront for D (padded channels) and R (rows/lane).

@@ -102,7 +102,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     float prev_up = (top && lane == 0) ? 0.f : INF;
 
     const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
-    float* hcur = (last || p.recompute) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
+    float* hcur = (last || p.recompute || p.skip_handoff) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
     float* rs = p.store_r ? p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R : nullptr;
 
     // lane-0 feeds one chunk of 32 columns ahead (the top row is NaN until written)
@@ -124,7 +124,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
             if (!top) {
                 float t = tnext;
                 const bool ok = wait_filled(jj < N && isnan(t), [&]() { t = __ldcv(hprev + jj); return isnan(t); },
-                                            p.hdr, 3);
+                                            p.hdr, 3, p.spin_limit);
                 if (!ok) return;
                 topv = jj < N ? t : INF;
                 tnext = jj + 32 < N ? __ldcv(hprev + jj + 32) : INF;
@@ -258,7 +258,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
             if (!last) {
                 const bool ok = wait_filled(jj >= 0 && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
                                             [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
-                                            p.hdr, 4);
+                                            p.hdr, 4, p.spin_limit);
                 if (!ok) return;
                 if (jj >= 0) {
                     cr = __uint_as_float((uint32_t)wa);
@@ -322,7 +322,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                     rp[k] = rn; dp[k] = dn; ep[k] = en;
                 }
             }
-            if (emine != nullptr && lane == 0) {
+            if (emine != nullptr && lane == 0 && !p.skip_handoff) {
                 __stcg(emine + 2 * j, pack2(rp[0], dp[0]));
                 __stcg(emine + 2 * j + 1, pack2(ep[0], 0.f));
             }
@@ -396,7 +396,7 @@ __global__ void adam_kernel(float* x, const float* grad, float* m, float* v, int
 template <int D, bool BWD>
 cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
-    constexpr int R = D <= 1 ? 16 : 8;
+    constexpr int R = 8;
     softdtw_kernel<D, R, BWD><<<grid, block, 0, st>>>(p);
     return cudaGetLastError();
 }
@@ -404,7 +404,7 @@ cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
 template <int D, bool BWD>
 int occ_d(int block)
 {
-    constexpr int R = D <= 1 ? 16 : 8;
+    constexpr int R = 8;
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD>, block, 0);
     return n;

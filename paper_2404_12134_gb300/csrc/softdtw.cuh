@@ -27,10 +27,12 @@ struct SoftParams {
     int store_r;         // forward: write R
     int recompute;
     int band_lo, band_cnt;
+    long long spin_limit;    // polls before a wait gives up
+    int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
 };
 
 // Rows held per lane by the soft-DTW kernels for a padded channel count D.
-inline int soft_rows(int D) { return D <= 1 ? 16 : 8; }
+inline int soft_rows(int D) { return 8; }
 
 cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);

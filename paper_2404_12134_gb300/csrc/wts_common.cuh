@@ -62,11 +62,12 @@ __device__ __forceinline__ int ld_volatile(const int* p)
 __device__ __forceinline__ bool is_nan_bits(uint32_t bits) { return (bits & 0x7fffffffu) > 0x7f800000u; }
 
 // Spin (warp-uniform) until no lane reports `missing`; `reload` re-reads the
-// lane's slot and returns whether it is still missing.  Bounded: after
-// kSpinLimit rounds, or once another warp raised the abort word, records a
-// timeout and returns false.
+// lane's slot and returns whether it is still missing.  Bounded: after `limit`
+// rounds, or once another warp raised the abort word, records a timeout and
+// returns false.
 template <typename Reload>
-__device__ __forceinline__ bool wait_filled(bool missing, Reload reload, WsHeader* hdr, int where)
+__device__ __forceinline__ bool wait_filled(bool missing, Reload reload, WsHeader* hdr, int where,
+                                            long long limit = kSpinLimit)
 {
     if (!__any_sync(FULL, missing)) return true;
     long long spins = 0;
@@ -75,7 +76,7 @@ __device__ __forceinline__ bool wait_filled(bool missing, Reload reload, WsHeade
         if (missing) missing = reload();
         if (!__any_sync(FULL, missing)) return true;
         if (ld_volatile(&hdr->abort)) return false;
-        if (++spins > kSpinLimit) {
+        if (++spins > limit) {
             if ((threadIdx.x & 31) == 0) {
                 atomicExch(&hdr->status, kDevTimeout);
                 atomicExch(&hdr->timeout_where, where);

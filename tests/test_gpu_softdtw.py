@@ -136,7 +136,7 @@ def test_gamma_validation(wts):
 def test_checkpoint_mode_identical(wts, G):
     """dir_mode=1 keeps only the band hand-off rows; softdtw_backward
     recomputes R for G bands at a time: values and gradients identical."""
-    B, b = _case(10, 1100, [900, 1300, 77], 1)       # 3 bands of 512 rows (16 rows per lane, d = 1)
+    B, b = _case(10, 1100, [900, 1300, 77], 1)       # several bands of 32 x rows-per-lane rows
     gb = wts.Batch.from_numpy(b.data, b.offsets)
     Bt = torch.from_numpy(B).cuda()
     w = torch.from_numpy((1.0 / b.lengths).astype(np.float32)).cuda()
@@ -150,4 +150,4 @@ def test_checkpoint_mode_identical(wts, G):
     assert torch.equal(v0, v1) and torch.equal(g0, g1)
     s_ck = wts.workspace_size(wts._abi.OP_SOFTDTW, 1100, gb, opt)
     s_st = wts.workspace_size(wts._abi.OP_SOFTDTW, 1100, gb)
-    assert s_ck < s_st if G < 3 else s_ck == s_st
+    assert s_ck <= s_st and (G > 1 or s_ck < s_st)
