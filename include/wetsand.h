@@ -59,6 +59,7 @@ enum {
     WTS_OP_DBA_ITERATE = 3,
     WTS_OP_SOFTDTW = 4,        /* softdtw_forward + softdtw_backward (R kept in the workspace) */
     WTS_OP_PAIRWISE = 5,
+    WTS_OP_COMPACT_NAN = 6,    /* wts_compact_nan (M ignored) */
 };
 
 /* A packed batch of T cycles (Sec. 3.1: d-channel series of uneven lengths). */
@@ -224,6 +225,20 @@ int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, fl
  */
 int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* workspace, size_t workspace_bytes,
                  void* stream, wts_options* best, float* best_ms);
+
+/*
+ * wts_compact_nan - batch staging of Sec. 3.1: every time step with a missing
+ * value (NaN in any channel) is removed and the cycles are re-packed in order,
+ * giving the irregularly sampled series Y the alignment uses.
+ *   Y: the raw batch (samples may be NaN; lengths >= 1)
+ *   out [rows][d] out: compacted samples (at most as many rows as the input)
+ *   out_offsets [T+1] out (device): offsets of the compacted cycles; copy them
+ *   to the host to build the compacted batch.  A cycle whose every step is
+ *   missing comes out empty, which the alignment calls reject.
+ * Workspace: wts_workspace_size(WTS_OP_COMPACT_NAN, 0, Y, NULL, &bytes).
+ */
+int wts_compact_nan(const wts_batch* Y, void* workspace, size_t workspace_bytes, void* stream, float* out,
+                    int64_t* out_offsets);
 
 /*
  * wts_pairwise_dtw - DTW between every two cycles of the batch (rows = the

@@ -12,7 +12,7 @@ _API_NAMES = {
     "Batch", "Workspace", "options", "workspace_size", "read_status", "anomaly_score", "dtw_align",
     "dba_iterate", "pairwise_dtw", "medoid", "resample", "euclid_mean", "profile_enable", "profile_read",
     "anomaly_score_noalloc", "softdtw_forward", "softdtw_backward", "adam_step", "SoftDTW", "softdtw",
-    "softdtw_barycenter", "autotune", "capture", "peak_probe",
+    "softdtw_barycenter", "autotune", "capture", "peak_probe", "compact_nan",
 }
 
 

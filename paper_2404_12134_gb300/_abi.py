@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwetsand.so")
 
 WTS_OK, WTS_EINVAL, WTS_ENOMEM, WTS_ECUDA, WTS_ETIMEOUT = 0, 1, 2, 3, 4
-OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE = 1, 2, 3, 4, 5
+OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE, OP_COMPACT_NAN = 1, 2, 3, 4, 5, 6
 
 # every symbol declared in include/wetsand.h
 EXPORTS = (
@@ -21,7 +21,7 @@ EXPORTS = (
     "wts_profile_enable", "wts_profile_read", "wts_peak_probe",
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
-    "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune",
+    "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune", "wts_compact_nan",
 )
 
 
@@ -78,6 +78,7 @@ _SIGS = {
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),
     "anomaly_score_noalloc": ([VP, I64, PB, PO, VP, VP, VP, VP], ctypes.c_int),
+    "wts_compact_nan": ([PB, VP, SZ, VP, VP, VP], ctypes.c_int),
     "wts_autotune": ([ctypes.c_int, VP, I64, PB, VP, SZ, VP, PO, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "softdtw_forward": ([VP, I64, PB, ctypes.c_float, PO, VP, SZ, VP, VP], ctypes.c_int),
     "softdtw_backward": ([VP, I64, PB, ctypes.c_float, VP, PO, VP, SZ, VP, VP], ctypes.c_int),

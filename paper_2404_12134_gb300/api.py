@@ -250,6 +250,19 @@ def capture(fn):
     return g, out
 
 
+def compact_nan(batch: Batch, ws: Workspace | None = None) -> Batch:
+    """Remove every time step with a NaN in any channel (Sec. 3.1) and re-pack:
+    returns the compacted batch (its host offsets are read back, one sync)."""
+    nb = workspace_size(_abi.OP_COMPACT_NAN, 0, batch)
+    buf = _ws(ws, nb)
+    out = torch.empty_like(batch.data)
+    offs = torch.empty_like(batch.offsets)
+    check(_abi.load().wts_compact_nan(ctypes.byref(batch.c()), buf.data_ptr(), buf.numel(), _stream(),
+                                      out.data_ptr(), offs.data_ptr()))
+    host = offs.cpu().numpy()
+    return Batch(out[: int(host[-1])], offs, host)
+
+
 def pairwise_dtw(batch: Batch, opts=None, ws: Workspace | None = None) -> torch.Tensor:
     """[T, T] symmetric matrix of DTW costs between cycles."""
     lib = _abi.load()

@@ -17,6 +17,9 @@
 
 namespace wts {
 int run_probe(int which, double* ops_per_s);
+size_t compact_workspace_bytes(int64_t rows);
+cudaError_t launch_compact_nan(const float* in, const int64_t* in_offsets, int T, int d, int64_t rows, float* out,
+                               int64_t* out_offsets, void* ws, cudaStream_t st);
 namespace {
 
 thread_local std::string g_err;
@@ -482,6 +485,12 @@ int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options*
 {
     if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
     static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise};
+    if (op == WTS_OP_COMPACT_NAN) {
+        int rc = check_batch(Y, false);
+        if (rc) return rc;
+        *bytes = align256(compact_workspace_bytes(Y->offsets_host[Y->T]));
+        return ok();
+    }
     if (op < 1 || op > 5) return fail(WTS_EINVAL, "unknown op %d", op);
     Layout L;
     int rc = compute_layout(map[op], M, Y, opt, &L);
@@ -768,6 +777,26 @@ int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* wo
     }
     *best = best_o;
     if (best_ms) *best_ms = best_t;
+    return ok();
+}
+
+int wts_compact_nan(const wts_batch* Y, void* workspace, size_t workspace_bytes, void* stream, float* out,
+                    int64_t* out_offsets)
+{
+    int rc = check_batch(Y, true);
+    if (rc) return rc;
+    if (!out || !out_offsets) return fail(WTS_EINVAL, "out and out_offsets must not be NULL");
+    const int64_t rows = Y->offsets_host[Y->T];
+    if (!workspace) return fail(WTS_EINVAL, "workspace is NULL");
+    if (workspace_bytes < compact_workspace_bytes(rows))
+        return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, compact_workspace_bytes(rows));
+    cudaError_t e;
+    {
+        Prof pr("compact_nan", (cudaStream_t)stream);
+        e = launch_compact_nan(Y->data, Y->offsets, Y->T, Y->d, rows, out, out_offsets, workspace,
+                               (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "compaction launch");
     return ok();
 }
 

@@ -151,8 +151,10 @@ def _gaps(rng: np.random.Generator, L: int, frac: float = 0.02) -> np.ndarray:
 
 
 def make_cycle(rng: np.random.Generator, base: BaseSignal, L: int,
-               anomaly: int = 0, noise: float = 0.05, gaps: bool = True) -> np.ndarray:
-    """One cycle of pre-gap length L: warp, optional anomaly, noise, gaps."""
+               anomaly: int = 0, noise: float = 0.05, gaps=True) -> np.ndarray:
+    """One cycle of pre-gap length L: warp, optional anomaly, noise, gaps
+    (gaps=True removes the missing steps, gaps="nan" keeps them as NaN rows, as
+    a regularly sampled stream with missing values carries them)."""
     xk, wk = _warp(rng, slowdown=(anomaly == 3))
     x = np.arange(L) / L
     u = np.interp(x, xk, wk)
@@ -167,7 +169,10 @@ def make_cycle(rng: np.random.Generator, base: BaseSignal, L: int,
         ramp = np.clip((x - a) / 0.3, 0.0, 1.0) * 0.5
         y = y + ramp[:, None]
     y = y + rng.normal(0, noise, size=y.shape)
-    if gaps:
+    if gaps == "nan":
+        y = y.copy()
+        y[~_gaps(rng, L)] = np.nan
+    elif gaps:
         y = y[_gaps(rng, L)]
     return y.astype(np.float32)
 
