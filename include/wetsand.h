@@ -218,8 +218,9 @@ int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, fl
  * wts_autotune - pick the launch options (rows per lane, warps per block) of
  * the wavefront for operation op (WTS_OP_ANOMALY_SCORE, WTS_OP_DTW_ALIGN or
  * WTS_OP_DBA_ITERATE) on this batch by timing each candidate that fits in the
- * given workspace (one warm-up and one timed pass each, CUDA events on
- * `stream`; synchronises it).  Results are cached per (op, d, M, T, total
+ * given workspace (one warm-up and the best of two timed passes each, CUDA
+ * events on `stream`; synchronises it; the default shape is kept unless another
+ * is more than 1 % faster).  Results are cached per (op, d, M, T, total
  * length); a cached answer costs nothing.  best: out (host); best_ms: out
  * (host, may be NULL), the wavefront time of the chosen options.
  */

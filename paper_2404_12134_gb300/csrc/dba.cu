@@ -108,23 +108,22 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             // plane 0 ("not diag") is bit k, plane 1 ("not up") bit R + k of
             // the W words of (step s, lane t)
             const uint32_t* wp = win + ((s - wlo) * 32 + t) * W;
-            const uint32_t nd = (wp[k >> 5] >> (k & 31)) & 1u;
-            const uint32_t nu = (wp[(R + k) >> 5] >> ((R + k) & 31)) & 1u;
-            const int code = nd == 0 ? 0 : (nu == 0 ? 1 : 2);
+            const uint32_t w0 = wp[0];
+            const uint32_t nd = (w0 >> k) & 1u;
+            const uint32_t nu = W == 1 ? (w0 >> (16 + k)) & 1u : (wp[W - 1] >> k) & 1u;
+            // codes: diag (nd = 0) moves up-left, up (nd = 1, nu = 0) moves up,
+            // left (nd = nu = 1) moves left
+            const int di = (nd == 0u || nu == 0u) ? 1 : 0;
+            const int dj = (nd == 0u || nu == 1u) ? 1 : 0;
             // a valid code matrix only moves left on row 0 and only up on
             // column 0; anything else is reported as |pi| = -1
-            if ((i == 0 && code != 2) || (j == 0 && code != 1)) { len = -1; break; }
-            if (code == 0) {
-                if (lane == 0) jlo[i] = j;
-                --i; --j;
-                if (lane == 0) jhi[i] = j;
-            } else if (code == 1) {
-                if (lane == 0) jlo[i] = j;
-                --i;
-                if (lane == 0) jhi[i] = j;
-            } else {
-                --j;
+            if ((i == 0 && di) || (j == 0 && dj)) { len = -1; break; }
+            if (di && lane == 0) {
+                jlo[i] = j;
+                jhi[i - 1] = j - dj;
             }
+            i -= di;
+            j -= dj;
             if (i < i_lo) { left_group = true; break; }    // the rest lies in bands not loaded
         }
         if (left_group) {
@@ -139,40 +138,60 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
     }
 }
 
-// One thread per prototype row i; sums in double, cycles in ascending order,
-// samples in ascending order, then one division and one rounding to float.
-template <int D>
-__global__ void dba_average_kernel(const float* __restrict__ data, const int64_t* __restrict__ offsets, int T, int d,
-                                   int64_t M, const int32_t* __restrict__ jlo, const int32_t* __restrict__ jhi,
-                                   const float* __restrict__ costs, float* __restrict__ B_out,
-                                   int32_t* __restrict__ counts, double* cost_before)
+// One thread per (prototype row i, channel c); the sum of channel c of row i
+// is taken in double, cycles in ascending order, samples in ascending order,
+// then one division and one rounding to float (the thread of channel 0 also
+// writes the count).  The ranges of the next kPre cycles are loaded ahead so
+// that the dependent range -> sample loads of successive cycles overlap.
+constexpr int kPre = 8;
+
+__global__ void __launch_bounds__(256) dba_average_kernel(const float* __restrict__ data,
+                                                          const int64_t* __restrict__ offsets, int T, int d,
+                                                          int64_t M, const int32_t* __restrict__ jlo,
+                                                          const int32_t* __restrict__ jhi,
+                                                          const float* __restrict__ costs, float* __restrict__ B_out,
+                                                          int32_t* __restrict__ counts, double* cost_before)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) {
-        double acc[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < M * d) {
+        const int64_t i = q / d;
+        const int c = (int)(q - i * d);
+        double acc = 0.0;
         int64_t cnt = 0;
-        for (int k = 0; k < T; ++k) {
-            const int64_t o0 = __ldg(offsets + k);
-            const int n = (int)(__ldg(offsets + k + 1) - o0);
-            // ranges come from the backtrack; clamping keeps every read inside
-            // the cycle even if a range were never written
-            const int a = max(__ldg(jlo + (int64_t)k * M + i), 0);
-            const int b = min(__ldg(jhi + (int64_t)k * M + i), n - 1);
-            const float* y = data + o0 * d;
-            for (int j = a; j <= b; ++j)
+        for (int k0 = 0; k0 < T; k0 += kPre) {
+            int a[kPre], b[kPre];
+            int64_t o[kPre];
 #pragma unroll
-                for (int c = 0; c < D; ++c)
-                    if (c < d) acc[c] = __dadd_rn(acc[c], (double)__ldg(y + (int64_t)j * d + c));
-            cnt += b >= a ? b - a + 1 : 0;
+            for (int u = 0; u < kPre; ++u) {
+                const int k = k0 + u;
+                if (k < T) {
+                    o[u] = __ldg(offsets + k);
+                    const int n = (int)(__ldg(offsets + k + 1) - o[u]);
+                    // ranges come from the backtrack; clamping keeps every read
+                    // inside the cycle even if a range were never written
+                    a[u] = max(__ldg(jlo + (int64_t)k * M + i), 0);
+                    b[u] = min(__ldg(jhi + (int64_t)k * M + i), n - 1);
+                } else {
+                    o[u] = 0; a[u] = 0; b[u] = -1;
+                }
+            }
+            float first[kPre];
+#pragma unroll
+            for (int u = 0; u < kPre; ++u)
+                first[u] = b[u] >= a[u] ? __ldg(data + (o[u] + a[u]) * d + c) : 0.f;
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) {
+                if (b[u] < a[u]) continue;
+                acc = __dadd_rn(acc, (double)first[u]);
+                for (int j = a[u] + 1; j <= b[u]; ++j)
+                    acc = __dadd_rn(acc, (double)__ldg(data + (o[u] + j) * d + c));
+                cnt += b[u] - a[u] + 1;
+            }
         }
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            if (c < d) B_out[i * d + c] = __double2float_rn(__ddiv_rn(acc[c], (double)(cnt > 0 ? cnt : 1)));
-        if (counts) counts[i] = (int32_t)cnt;
+        B_out[q] = __double2float_rn(__ddiv_rn(acc, (double)(cnt > 0 ? cnt : 1)));
+        if (counts && c == 0) counts[i] = (int32_t)cnt;
     }
-    if (i == 0 && cost_before) {
+    if (q == 0 && cost_before) {
         double s = 0.0;
         for (int k = 0; k < T; ++k) s = __dadd_rn(s, (double)costs[k]);
         *cost_before = s;
@@ -250,12 +269,10 @@ cudaError_t launch_dba_average(const float* data, const int64_t* offsets, int T,
                                const int32_t* jlo, const int32_t* jhi, const float* costs,
                                float* B_out, int32_t* counts, double* cost_before, cudaStream_t st)
 {
-    const int block = 128;
-    const int grid = (int)((M + block - 1) / block);
-    if (d <= 1) dba_average_kernel<1><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
-    else if (d <= 3) dba_average_kernel<3><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
-    else if (d <= 6) dba_average_kernel<6><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
-    else dba_average_kernel<16><<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
+    const int block = 256;
+    const int64_t n = M * d;
+    const int grid = (int)((n + block - 1) / block);
+    dba_average_kernel<<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
     return cudaGetLastError();
 }
 
