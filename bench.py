@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--T", type=int, default=200, help="cycles (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
+    ap.add_argument("--soft-ckpt", action="store_true",
+                    help="soft leg in checkpoint mode (R recomputed in the backward; for profiling)")
     ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long"],
                     help="soft / score: only that leg (soft: with --T cycles of its workload); for profiling")
     return ap.parse_args()
@@ -179,7 +181,7 @@ def hbm_peak_gbs() -> float:
         return 6800.0
 
 
-def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None):
+def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None, ckpt: bool = False):
     """Soft-DTW forward + backward on the single-channel barycenter workload:
     64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB)."""
     sb = synth.config_batch(2, T=T)
@@ -189,16 +191,17 @@ def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None 
     w = torch.from_numpy((1.0 / sb.lengths).astype(np.float32)).to(dev)
     ws = api.Workspace(dev)
     grad = torch.empty_like(B)
+    opt = api.options(dir_mode=1, ckpt_bands=1 << 20) if ckpt else None
     for _ in range(2):
-        api.softdtw_forward(B, gb, gamma, ws=ws)
-        api.softdtw_backward(B, gb, gamma, w, ws=ws, grad_B=grad)
+        api.softdtw_forward(B, gb, gamma, opt, ws=ws)
+        api.softdtw_backward(B, gb, gamma, w, opt, ws=ws, grad_B=grad)
     barrier()
     api.profile_read("")
     api.profile_enable(True)
     reps = 3
     for _ in range(reps):
-        vals = api.softdtw_forward(B, gb, gamma, ws=ws)
-        api.softdtw_backward(B, gb, gamma, w, ws=ws, grad_B=grad)
+        vals = api.softdtw_forward(B, gb, gamma, opt, ws=ws)
+        api.softdtw_backward(B, gb, gamma, w, opt, ws=ws, grad_B=grad)
     barrier()
     api.profile_enable(False)
     f_ms, _ = api.profile_read("softdtw_fwd")
@@ -384,7 +387,7 @@ def run_gpu(args):
     if args.leg == "soft":
         def sync():
             torch.cuda.synchronize()
-        res = softdtw_leg(api, torch, dev, torch.cuda.current_stream(), sync, T=min(args.T, 64))
+        res = softdtw_leg(api, torch, dev, torch.cuda.current_stream(), sync, T=min(args.T, 64), ckpt=args.soft_ckpt)
         if rank == 0:
             print(json.dumps({"leg": "soft", "softdtw": res}), flush=True)
         return 0

@@ -311,7 +311,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                         const float a = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(nr, r), nd), kk));
                         const float bb = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(rr, r), rd), kk));
                         const float cc = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(xr, r), xd), kk));
-                        float e = __fmaf_rn(cc, xe, __fmaf_rn(bb, re, __fmul_rn(a, ne)));
+                        // the row below's e (ne) is the only input computed in
+                        // this step: it enters last, so the serial chain down the
+                        // rows is one fused multiply-add per row
+                        float e = __fmaf_rn(a, ne, __fmaf_rn(cc, xe, __fmul_rn(bb, re)));
                         if (i0 + k == M - 1 && j == N - 1) e = 1.f;
 #pragma unroll
                         for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(e, t[c], g[k][c]);
