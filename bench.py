@@ -35,6 +35,11 @@ WORKLOAD = ("batched DBA: 200 cycles x 6 ch FP32, pre-gap N ~ U(20k,30k), 2% gap
             "10% anomalous, M=25000, one DBA iteration per step")
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per cell of the code-writing wavefront, from one
+# ncu capture of the same kernel build on 36 cycles of this workload
+# (profiles/wavefront_dirs_36x25k_d6.md): 5.8027e9 bytes / 2.2029e10 cells.
+# Traffic grows in proportion to the cells (codes + hand-off rows).
+WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = 5.8027e9 / 2.2029e10
 
 
 def parse():
@@ -485,7 +490,9 @@ def run_gpu(args):
     peak = sms * FP32_LANES_PER_SM * 2.070e9 / 1e12
     achieved = ops / wf_avg_s / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s (FP32 lane ops)",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak,
+                       "traffic": WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL * cells if d == 6 else None,
+                       "traffic_note": "bytes per launch, ncu dram__bytes_read+write on 36 cycles scaled by cells",
                        "kernel": f"dtw_wavefront_kernel<D=6,R={opts.rows_per_thread},dirs>",
                        "peak_note": f"{sms} SMs x 128 FP32 lanes x 2070 MHz (max SM clock)"}
     out["kernel_ms_per_step"] = {"wavefront": wf_ms / args.steps, "backtrack": bt_ms / args.steps,

@@ -179,7 +179,7 @@ int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, 
  * the recursion Eq. 5 with the soft minimum of Eq. 3, read with the exponent
  * -a_i/gamma).  The soft minimum is evaluated as
  *     m - gamma ln(sum_i exp(-(a_i - m)/gamma)),  m = min_i a_i,
- * with the hardware ex2 / lg2 approximations, in FP32.  Every r(i,j) is kept
+ * with the hardware ex2 / lg2 approximations (flush-to-zero), in FP32.  Every r(i,j) is kept
  * in the workspace for softdtw_backward (4 bytes per cell plus a skew
  * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)); with opt->dir_mode = 1
  * only the band hand-off rows are kept and softdtw_backward recomputes R for

@@ -24,8 +24,8 @@ __global__ void __launch_bounds__(256) probe_kernel(float* out, int iters, float
         for (int c = 0; c < kChains; ++c) {
             if (WHICH == 0) v[c] = __fmaf_rn(v[c], 0.999f, 0.0001f);
             if (WHICH == 1) { v[c] = fminf(v[c], w[c]); w[c] = fmaxf(w[c], v[c]); }
-            if (WHICH == 2) asm volatile("ex2.approx.f32 %0, %0;" : "+f"(v[c]));
-            if (WHICH == 3) asm volatile("lg2.approx.f32 %0, %0;" : "+f"(v[c]));
+            if (WHICH == 2) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(v[c]));
+            if (WHICH == 3) asm volatile("lg2.approx.ftz.f32 %0, %0;" : "+f"(v[c]));
             if (WHICH == 4) {
                 unsigned long long p;
                 asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(v[c]), "f"(w[c]));

@@ -4,7 +4,7 @@
 //   min^gamma(a,b,c) = m - gamma ln(sum exp(-(v - m)/gamma)),  m = min(a,b,c)
 // (the exact rewrite of Eq. 3 with exp(-m/gamma) factored out), evaluated as
 //   m - (gamma ln 2) log2(sum 2^((m - v) log2(e)/gamma))
-// with the hardware ex2 / lg2 approximations.  Every r is stored (FP32) so the
+// with the hardware ex2 / lg2 approximations (flush-to-zero forms).  Every r is stored (FP32) so the
 // backward pass can read it.
 //
 // Backward (Eq. 6 with E from the reverse recursion of Cuturi and Blondel,
@@ -29,10 +29,13 @@ namespace wts {
 
 namespace {
 
+// 2^x and log2(x) by the MUFU approximations, flushing subnormals: a term
+// below 2^-126 next to a sum of at least 1 changes nothing, and log2 is only
+// taken of sums in [1, 3].  (The non-flushing forms cost extra instructions.)
 __device__ __forceinline__ float ex2a(float x)
 {
     float y;
-    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
@@ -48,7 +51,7 @@ __device__ __forceinline__ u64 pack2(float lo, float hi)
 __device__ __forceinline__ float lg2a(float x)
 {
     float y;
-    asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
