@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
     ap.add_argument("--soft-ckpt", action="store_true",
                     help="soft leg in checkpoint mode (R recomputed in the backward; for profiling)")
-    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long"],
+    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long", "bary"],
                     help="soft / score: only that leg (soft: with --T cycles of its workload); for profiling")
     return ap.parse_args()
 
@@ -361,6 +361,45 @@ def long_leg(api, torch, dev, barrier, iters: int = 2):
     return res
 
 
+def bary_leg(api, torch, dev, barrier, gammas=(1.0, 0.1, 0.01), steps: int = 50, dba_iters: int = 10,
+             lr: float = 5e-2):
+    """Barycenters of the single-channel workload (64 cycles, M = 10,000): the
+    Euclidean mean of the resampled cycles (Table I's initialisation), 10 DBA
+    iterations from it, and the Soft-DTW barycenter of Eq. 7 by 50 Adam steps
+    from it; each scored by the intraclass inertia sum_k DTW(B, Y_k) and the
+    mean d_score (Eq. 8), the quantities of the paper's barycenter comparison."""
+    sb = synth.config_batch(2)
+    M = synth.PROTO_LEN[2]
+    gb = api.Batch.from_numpy(sb.data, sb.offsets, device=dev)
+    B0 = api.euclid_mean(gb, M)
+    ws = api.Workspace(dev)
+
+    def quality(B):
+        score, cost, _ = api.anomaly_score(B, gb, ws=ws)
+        return {"inertia": float(cost.double().sum()), "mean_d_score": float(score.double().mean())}
+
+    res = {"workload": "64 cycles x 1 ch FP32, pre-gap N ~ U(8k,12k), 2% gaps, M=10000",
+           "euclidean_mean": quality(B0)}
+    barrier()
+    t0 = time.perf_counter()
+    B = B0.clone()
+    for _ in range(dba_iters):
+        B, _, _, _ = api.dba_iterate(B, gb, ws=ws)
+    barrier()
+    res["dba"] = dict(quality(B), iterations=dba_iters, seconds=time.perf_counter() - t0)
+    for gamma in gammas:
+        t0 = time.perf_counter()
+        Bs, hist, w = api.softdtw_barycenter(gb, M, gamma, steps=steps, lr=lr, init=B0)
+        barrier()
+        el = time.perf_counter() - t0
+        obj = (hist.double() * w.double()).sum(1).cpu().numpy()
+        res[f"softdtw_barycenter_gamma_{gamma:g}"] = dict(quality(Bs), adam_steps=steps, lr=lr, seconds=el,
+                                                          objective_first=float(obj[0]),
+                                                          objective_last=float(obj[-1]))
+    del ws
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -388,6 +427,13 @@ def run_gpu(args):
         res = long_leg(api, torch, dev, sync)
         if rank == 0:
             print(json.dumps({"leg": "long", "long": res}), flush=True)
+        return 0
+    if args.leg == "bary":
+        def sync():
+            torch.cuda.synchronize()
+        res = bary_leg(api, torch, dev, sync)
+        if rank == 0:
+            print(json.dumps({"leg": "bary", "barycenters": res}), flush=True)
         return 0
     if args.leg == "soft":
         def sync():
@@ -544,6 +590,7 @@ def run_gpu(args):
     if not args.no_extras:
         out["scoring"] = scoring_leg(api, torch, dev, barrier)
         out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
+        out["barycenters"] = bary_leg(api, torch, dev, barrier)
         out["measured_peaks_probe"] = {k: api.peak_probe(i) / 1e12 for i, k in
                                        enumerate(("fp32_fma_tops", "fp32_minmax_tops", "mufu_ex2_tops",
                                                   "mufu_lg2_tops", "fp32x2_fma_tops", "fp32_min3_tops"))}
