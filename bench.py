@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
     ap.add_argument("--soft-ckpt", action="store_true",
                     help="soft leg in checkpoint mode (R recomputed in the backward; for profiling)")
-    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long", "bary"],
+    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long", "bary", "table"],
                     help="soft / score: only that leg (soft: with --T cycles of its workload); for profiling")
     return ap.parse_args()
 
@@ -400,6 +400,93 @@ def bary_leg(api, torch, dev, barrier, gammas=(1.0, 0.1, 0.01), steps: int = 50,
     return res
 
 
+def per_pair_align_ms(api, torch, dev, B, b, gb, barrier):
+    """dtw_align launched once per cycle (the plain one-pair-per-launch form)."""
+    singles = []
+    for k in range(b.T):
+        o0, o1 = int(b.offsets[k]), int(b.offsets[k + 1])
+        singles.append(api.Batch(gb.data[o0:o1], torch.tensor([0, o1 - o0], device=dev),
+                                 np.array([0, o1 - o0], dtype=np.int64)))
+    ws = api.Workspace(dev)
+    api.dtw_align(B, singles[0], ws=ws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for one in singles:
+        api.dtw_align(B, one, ws=ws)
+    e1.record()
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def table_leg(api, torch, dev, barrier):
+    """Entries of the results table not covered by the other legs: the small
+    DBA workload end to end (medoid init, 10 DBA iterations, scores), the
+    one-pair-per-launch form of the two DBA workloads, and the CPU oracle on
+    bounded samples of the soft-DTW and uneven-scoring workloads."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    res = {}
+    # workload 0: 16 cycles x 1.0-1.2k, medoid init, 10 DBA iterations + scores
+    b = synth.config_batch(0)
+    gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
+    ws = api.Workspace(dev)
+    barrier()
+    t0 = time.perf_counter()
+    idx, _ = api.medoid(api.pairwise_dtw(gb, ws=ws))
+    k = int(idx)
+    B = gb.data[int(b.offsets[k]):int(b.offsets[k + 1])].clone()
+    M0 = B.shape[0]
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        B, _, _, _ = api.dba_iterate(B, gb, ws=ws)
+    e1.record()
+    score, cost, _ = api.anomaly_score(B, gb, ws=ws)
+    barrier()
+    total = time.perf_counter() - t0
+    cells0 = M0 * int(b.lengths.sum())
+    it_ms = e0.elapsed_time(e1) / 10
+    pp_ms = per_pair_align_ms(api, torch, dev, B, b, gb, barrier)
+    t1 = time.perf_counter()
+    oracle.dba_iterate(B.cpu().numpy().astype(np.float64), b.data, b.offsets, "f64")
+    cpu_s = time.perf_counter() - t1
+    res["small_dba"] = {"M": M0, "cells_per_iter": cells0, "s_per_dba_iter": it_ms * 1e-3,
+                        "gcups": cells0 / (it_ms * 1e-3) / 1e9, "workflow_s": total,
+                        "per_pair_align_s_per_iter": pp_ms * 1e-3,
+                        "cpu_oracle_s_per_iter": cpu_s, "cpu_oracle_gcups": cells0 / cpu_s / 1e9, "cores": ncores}
+    del ws
+    # workload 1: one-pair-per-launch alignment (the dominant part of a DBA iteration)
+    b1, subset = make_workload(200)
+    gb1 = api.Batch.from_numpy(b1.data, b1.offsets, device=dev)
+    B1 = torch.from_numpy(synth.clean_prototype(b1, M_PROTO)).to(dev)
+    pp1 = per_pair_align_ms(api, torch, dev, B1, b1, gb1, barrier)
+    cells1 = M_PROTO * int(b1.lengths.sum())
+    res["batched_dba_per_pair_align"] = {"ms": pp1, "gcups": cells1 / (pp1 * 1e-3) / 1e9}
+    del gb1
+    # CPU oracle: soft-DTW fwd + bwd on 4 cycles of workload 2, scoring on 16 of workload 3
+    b2 = synth.config_batch(2)
+    sub = b2.subset(np.arange(4))
+    B2 = synth.clean_prototype(b2, synth.PROTO_LEN[2])
+    t1 = time.perf_counter()
+    oracle.softdtw_batch(B2, sub.data, sub.offsets, 1.0)
+    s2 = time.perf_counter() - t1
+    cells2 = synth.PROTO_LEN[2] * int(sub.lengths.sum())
+    res["cpu_oracle_softdtw"] = {"sample": "4 of 64 cycles, forward + backward, FP64", "s": s2,
+                                 "gcups": cells2 / s2 / 1e9, "threads": min(4, ncores)}
+    b3 = synth.config_batch(3)
+    sub3 = b3.subset(np.arange(min(ncores, b3.T)))
+    B3 = synth.clean_prototype(b3, synth.PROTO_LEN[3])
+    t1 = time.perf_counter()
+    oracle.score(B3, sub3.data, sub3.offsets, "f64")
+    s3 = time.perf_counter() - t1
+    cells3 = synth.PROTO_LEN[3] * int(sub3.lengths.sum())
+    res["cpu_oracle_scoring"] = {"sample": f"{sub3.T} of 1000 cycles, FP64", "s": s3, "gcups": cells3 / s3 / 1e9,
+                                 "threads": ncores}
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -427,6 +514,13 @@ def run_gpu(args):
         res = long_leg(api, torch, dev, sync)
         if rank == 0:
             print(json.dumps({"leg": "long", "long": res}), flush=True)
+        return 0
+    if args.leg == "table":
+        def sync():
+            torch.cuda.synchronize()
+        res = table_leg(api, torch, dev, sync)
+        if rank == 0:
+            print(json.dumps({"leg": "table", "table": res}), flush=True)
         return 0
     if args.leg == "bary":
         def sync():
