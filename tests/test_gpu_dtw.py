@@ -108,10 +108,10 @@ def test_launch_variants_agree(wts, rows, warps, order):
 
 
 def test_dba_iterations_bit_exact(wts):
-    """Ten DBA iterations from the medoid on workload-0-shaped cycles (scaled
-    to 0.3): every iteration's prototype, counts and cost equal the FP32
-    mirror's; the FP64 oracle's cost stays within 1e-5."""
-    b = synth.config_batch(0, scale=0.3)
+    """Ten DBA iterations from the medoid on the small DBA workload at full
+    size (16 cycles of 1.0-1.2k): every iteration's prototype, counts and cost
+    equal the FP32 mirror's."""
+    b = synth.config_batch(0)
     gb = _gb(wts, b.data, b.offsets)
     C = wts.pairwise_dtw(gb)
     idx, sums = wts.medoid(C)
@@ -201,3 +201,48 @@ def test_checkpoint_dba_identical(wts):
         Bc2, cc, cbc, _ = wts.dba_iterate(Bc, gb, opt)
         assert torch.equal(Bs2, Bc2) and torch.equal(cs, cc) and float(cbs) == float(cbc), it
         Bs, Bc = Bs2, Bc2
+
+
+def test_edge_shapes(wts):
+    """Single-row and single-column pairs, 16 channels (the maximum), and many
+    tiny cycles in one launch (the work list orders thousands of pairs)."""
+    rng = np.random.default_rng(105)
+    cases = []
+    cases.append((rng.normal(size=(1, 4)).astype(np.float32), [rng.normal(size=(n, 4)).astype(np.float32) for n in (1, 5, 300)]))
+    cases.append((rng.normal(size=(900, 2)).astype(np.float32), [rng.normal(size=(1, 2)).astype(np.float32)] * 3))
+    cases.append((rng.normal(size=(530, 16)).astype(np.float32), [rng.normal(size=(n, 16)).astype(np.float32) for n in (7, 640)]))
+    cases.append((rng.normal(size=(40, 1)).astype(np.float32),
+                  [rng.normal(size=(int(n), 1)).astype(np.float32) for n in rng.integers(1, 6, size=3000)]))
+    for B, cyc in cases:
+        data, offs = _pack(cyc)
+        gb = _gb(wts, data, offs)
+        Bt = torch.from_numpy(B).cuda()
+        score, cost, plen = wts.anomaly_score(Bt, gb)
+        s32, c32, L32 = oracle.score(B, data, offs, "f32")
+        assert (cost.cpu().numpy() == c32).all() and (plen.cpu().numpy() == L32).all()
+        c2, p2, jlo, jhi = wts.dtw_align(Bt, gb)
+        for k in (0, len(cyc) - 1):
+            r = oracle.dtw(B, cyc[k], "f32")
+            assert (jlo[k].cpu().numpy() == r["jlo"]).all() and (jhi[k].cpu().numpy() == r["jhi"]).all()
+
+
+def test_full_size_uneven_scoring_sampled(wts):
+    """The full uneven-scoring workload (1,000 cycles, 3 channels, lengths
+    2k-60k, M = 20,000) in the benchmark's launch shape (autotuned, one
+    graph-captured launch): the longest cycle and two others checked against
+    the oracle; every |pi| within [max(M, N), M + N - 1]."""
+    b = synth.config_batch(3)
+    gb = _gb(wts, b.data, b.offsets)
+    B = synth.clean_prototype(b, synth.PROTO_LEN[3])
+    Bt = torch.from_numpy(B).cuda()
+    opts, _ = wts.autotune(wts._abi.OP_ANOMALY_SCORE, Bt, gb)
+    ws = wts.Workspace()
+    g, (score, cost, plen) = wts.capture(lambda: wts.anomaly_score(Bt, gb, opts, ws=ws))
+    g.replay()
+    cost, plen = cost.cpu().numpy(), plen.cpu().numpy()
+    N = b.lengths
+    M = B.shape[0]
+    assert ((plen >= np.maximum(M, N)) & (plen <= M + N - 1)).all()
+    for k in (int(np.argmax(N)), 0, 517):
+        r = oracle.dtw(B, b.cycle(k), "f32", path=False)
+        assert cost[k] == r["cost"] and plen[k] == r["plen"], k

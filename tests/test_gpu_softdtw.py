@@ -151,3 +151,18 @@ def test_checkpoint_mode_identical(wts, G):
     s_ck = wts.workspace_size(wts._abi.OP_SOFTDTW, 1100, gb, opt)
     s_st = wts.workspace_size(wts._abi.OP_SOFTDTW, 1100, gb)
     assert s_ck <= s_st and (G > 1 or s_ck < s_st)
+
+
+def test_full_size_pair_value(wts):
+    """The soft-DTW workload at full size (64 cycles of 8k-12k, M = 10,000,
+    the benchmark's launch): two sampled pairs' values against the FP64
+    oracle."""
+    b = synth.config_batch(2)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M = synth.PROTO_LEN[2]
+    B = wts.euclid_mean(gb, M)
+    v = wts.softdtw_forward(B, gb, 1.0).cpu().numpy()
+    Bh = B.cpu().numpy()
+    for k in (0, 63):
+        ref = oracle.softdtw(Bh, b.cycle(k), 1.0, "f64", want_grad=False)["value"]
+        assert abs(v[k] - ref) <= VALUE_TOL * max(abs(ref), 1.0), (k, v[k], ref)
