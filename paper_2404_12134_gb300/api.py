@@ -226,7 +226,7 @@ def autotune(op: int, B: torch.Tensor, batch: Batch, ws: Workspace | None = None
     B = _check_B(B, batch.d)
     M = B.shape[0]
     need = max(workspace_size(op, M, batch, options(rows_per_thread=r))
-               for r in ((16, 32) if batch.d <= 3 else (16,)))
+               for r in ((8, 16, 32) if batch.d <= 3 else (8, 16)))
     buf = _ws(ws, need)
     best = wts_options()
     ms = ctypes.c_float(0)

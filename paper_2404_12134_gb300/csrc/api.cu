@@ -109,8 +109,8 @@ int check_batch(const wts_batch* Y, bool need_device)
 int check_opt(const wts_options* opt, int D)
 {
     if (!opt) return WTS_OK;
-    if (opt->rows_per_thread && opt->rows_per_thread != 16 && opt->rows_per_thread != 32)
-        return fail(WTS_EINVAL, "rows_per_thread must be 0, 16 or 32");
+    if (opt->rows_per_thread && opt->rows_per_thread != 8 && opt->rows_per_thread != 16 && opt->rows_per_thread != 32)
+        return fail(WTS_EINVAL, "rows_per_thread must be 0, 8, 16 or 32");
     if (opt->rows_per_thread == 32 && D > 3) return fail(WTS_EINVAL, "rows_per_thread=32 needs d <= 3");
     if (opt->warps_per_block < 0 || opt->warps_per_block > 4) return fail(WTS_EINVAL, "warps_per_block must be 0..4");
     if (opt->max_blocks < 0) return fail(WTS_EINVAL, "max_blocks must be >= 0");
@@ -732,7 +732,7 @@ int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* wo
     const int D = pick_D(Y->d);
     std::vector<wts_options> cands;
     // the default shape first: another candidate must beat it by more than 1 %
-    for (int R : {D <= 2 ? 32 : 16, D <= 2 ? 16 : 32}) {
+    for (int R : {D <= 2 ? 32 : 16, D <= 2 ? 16 : 32, 8}) {
         if (R == 32 && D > 3) continue;
         for (int wpb : {4, 2, 1}) {
             wts_options o{};

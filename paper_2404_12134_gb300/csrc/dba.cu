@@ -26,23 +26,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
 }
 
 // Walk the stored predecessor codes back from (M-1, N-1) to (0, 0).
-// Directions of band b live at dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]
-// for the word w of lane t at step s, and a cell (i, j) of the band sits in
-// lane t = (i mod BR) / R at step s = j + t, as bit k = i mod R ("not diag")
-// and bit R + k ("not up") of those W = R / 16 words.  Along the walk s only
-// decreases inside a band, so a window of kBtWords / (32 W) consecutive steps
-// (one contiguous block of global memory) is brought into shared memory by one
-// bulk asynchronous copy (completion on an mbarrier, bounded wait) and the walk
+// A cell (i, j) of band b sits in lane t = (i mod BR) / R at step s = j + t,
+// as bit k = i mod R ("not diag") and bit R + k ("not up") of the lane's 2R
+// code bits of that step.  For R >= 16 those are the W = R / 16 words at
+// dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]; for R = 8 the word
+// dirs[dir_off + b*((N+32)/2)*32 + (s/2)*32 + t] holds steps s and s+1 of the
+// lane (the even step in bits 0..15).  Along the walk s only decreases inside a
+// band, so a window of kBtWords / 32 consecutive word rows (one contiguous
+// block of global memory) is brought into shared memory by one bulk
+// asynchronous copy (completion on an mbarrier, bounded wait) and the walk
 // reads it; every lane walks the same path (broadcast reads), lane 0 writes.
 // Row i's range is [jlo(i), jhi(i)]: jhi when the walk enters the row, jlo
 // when it leaves it (Definition "Alignment path": monotone, so each row's
 // columns are contiguous).
-template <int W>
+template <int R>
 __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
 {
-    constexpr int R = 16 * W;
-    constexpr int LOG_R = W == 1 ? 4 : 5;
-    constexpr int kBtWin = kBtWords / (32 * W);     // steps of one band in the window
+    constexpr int W = R >= 16 ? R / 16 : 1;         // words per (word row, lane)
+    constexpr int SPW = R >= 16 ? 1 : 2;            // steps per word row
+    constexpr int LOG_R = R == 8 ? 3 : (R == 16 ? 4 : 5);
+    constexpr int kBtRows = kBtWords / (32 * W);    // word rows of one band in the window
     __shared__ __align__(128) uint32_t win_all[kBtWarps][kBtWords];
     __shared__ __align__(8) uint64_t bars[kBtWarps];
     const int lane = threadIdx.x & 31;
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             if (i < 0 || len < 0) continue;          // finished, or failed earlier
         }
         const int i_lo = p.band_lo * 32 * R;
-        int band = -1, wlo = 0, whi = -1;
+        int band = -1, wlo = 0, whi = -1;           // word rows in the window
         bool left_group = false;
         for (;;) {
             ++len;
@@ -79,11 +82,12 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             const int t = (i >> LOG_R) & 31;
             const int k = i & (R - 1);
             const int s = j + t;
-            if (b != band || s < wlo || s > whi) {
+            const int row = s / SPW;
+            if (b != band || row < wlo || row > whi) {
                 band = b;
-                whi = s;
-                wlo = max(0, s - kBtWin + 1);
-                const uint32_t* src = p.dirs + pd.dir_off + (int64_t)(b - p.band_lo) * (N + 31) * 32 * W +
+                whi = row;
+                wlo = max(0, row - kBtRows + 1);
+                const uint32_t* src = p.dirs + pd.dir_off + (int64_t)(b - p.band_lo) * band_dir_words(N, R) +
                                       (int64_t)wlo * 32 * W;
                 const uint32_t bytes = (uint32_t)(whi - wlo + 1) * 32 * W * 4;
                 __syncwarp();
@@ -106,11 +110,11 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
                 }
             }
             // plane 0 ("not diag") is bit k, plane 1 ("not up") bit R + k of
-            // the W words of (step s, lane t)
-            const uint32_t* wp = win + ((s - wlo) * 32 + t) * W;
-            const uint32_t w0 = wp[0];
+            // the step's code bits of lane t
+            const uint32_t* wp = win + ((row - wlo) * 32 + t) * W;
+            const uint32_t w0 = R == 8 ? wp[0] >> ((s & 1) * 16) : wp[0];
             const uint32_t nd = (w0 >> k) & 1u;
-            const uint32_t nu = W == 1 ? (w0 >> (16 + k)) & 1u : (wp[W - 1] >> k) & 1u;
+            const uint32_t nu = R <= 16 ? (w0 >> (R + k)) & 1u : (wp[W - 1] >> k) & 1u;
             // codes: diag (nd = 0) moves up-left, up (nd = 1, nu = 0) moves up,
             // left (nd = nu = 1) moves left
             const int di = (nd == 0u || nu == 0u) ? 1 : 0;
@@ -259,8 +263,9 @@ cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int need = (p.P + kBtWarps - 1) / kBtWarps;
     const int grid = need < 4 * sms ? need : 4 * sms;
-    if (p.R == 16) backtrack_kernel<1><<<grid, 32 * kBtWarps, 0, st>>>(p);
-    else if (p.R == 32) backtrack_kernel<2><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    if (p.R == 8) backtrack_kernel<8><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    else if (p.R == 16) backtrack_kernel<16><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    else if (p.R == 32) backtrack_kernel<32><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

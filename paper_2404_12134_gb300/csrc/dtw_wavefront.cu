@@ -28,7 +28,9 @@
 //
 // Predecessor codes (kModeDirs) are two bit-planes per lane and step: bit
 // p*R + k of the lane's W = R/16 words is plane p of row k, plane 0 = "not
-// diag", plane 1 = "not up" (meaningful only when plane 0 is set).
+// diag", plane 1 = "not up" (meaningful only when plane 0 is set).  With R = 8
+// a step has 16 bits and two consecutive steps share one word (the even step
+// in the low half).
 #include "dtw_wavefront.cuh"
 
 namespace wts {
@@ -90,7 +92,7 @@ constexpr int kRing = 128;   // columns of cycle samples staged per warp
 template <int D, int R, int MODE>
 struct Band {
     static constexpr int BR = 32 * R;
-    static constexpr int W = R / 16;        // code words per lane per step
+    static constexpr int W = R / 16;        // code words per lane per step (0: half a word)
     static constexpr int Q = R / 2;         // row pairs
 
     u64 bp[Q][D];                           // prototype rows as pairs
@@ -101,6 +103,7 @@ struct Band {
     int prev_upc;
     float topv;                             // lane l: r(band top - 1, s0 + l)
     int topc;
+    uint32_t half;                          // R = 8: codes of the last even step
 
     // Local costs of column jc for the lane's rows, pair q (two rows at once).
     __device__ __forceinline__ void cost_pair(const u64* yy, int q)
@@ -184,7 +187,12 @@ struct Band {
             for (int q = 0; q < Q; ++q) cost_pair(yy, q);
         }
         if (MODE == kModeDirs) {
-            if (W == 1) {
+            if (W == 0) {
+                if ((s & 1) == 0)
+                    half = word[0];
+                else
+                    __stcs(dout + (int64_t)(s >> 1) * 32 + lane, __byte_perm(half, word[0], 0x5410));
+            } else if (W == 1) {
                 __stcs(dout + (int64_t)s * 32 + lane, word[0]);
             } else {
                 __stcs(reinterpret_cast<uint2*>(dout) + (int64_t)s * 32 + lane,
@@ -223,6 +231,7 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     st.prev_upc = 0;
     st.topv = INF;
     st.topc = 0;
+    st.half = 0u;
 
     // hand-off rows: slot size 4 bytes (r), or 8 bytes ({r, cells}) with |pi|
     constexpr int SLOT = MODE == kModePlen ? 8 : 4;
@@ -230,7 +239,7 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     const char* hprev = top ? nullptr : hb + (pd.hbuf_off + (int64_t)(band - 1) * N) * SLOT;
     // a recomputed band reads its stored top row and produces no hand-off row
     void* hcur = (last || p.recompute || p.skip_handoff) ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
-    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * W
+    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)(band - p.band_lo) * band_dir_words(N, R)
                                          : nullptr;
 
     // Cycle samples go through the ring two chunks of 32 columns ahead of the
@@ -298,6 +307,8 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
         }
     }
 
+    if (MODE == kModeDirs && W == 0 && (steps & 1)) __stcs(dout + (int64_t)(steps >> 1) * 32 + lane, st.half);
+
     if (last && !p.recompute) {
         const int ilast = M - 1 - band * BR;
         if (lane == ilast / R) {
@@ -323,11 +334,13 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     }
 }
 
-// Blocks of at most 4 warps; three resident blocks (12 warps, <= 170 registers)
-// where the prototype rows fit easily, two otherwise (the software-pipelined
-// step keeps enough independent work per warp).
+// Blocks of at most 4 warps.  R = 16: three resident blocks (12 warps, <= 170
+// registers) where the prototype rows fit easily, two otherwise (the
+// software-pipelined step keeps enough independent work per warp).  R = 8
+// halves the prototype registers: four blocks (16 warps, <= 128 registers) up
+// to 6 channels.
 template <int D, int R>
-constexpr int min_blocks() { return (R == 16 && D <= 4) ? 3 : 2; }
+constexpr int min_blocks() { return R == 8 ? (D <= 6 ? 4 : (D <= 8 ? 3 : 2)) : ((R == 16 && D <= 4) ? 3 : 2); }
 
 template <int D, int R, int MODE>
 __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(DPParams p)
@@ -405,7 +418,19 @@ int occ_mode(int mode, int block)
 }  // namespace
 
 #define WTS_DISPATCH_DR(FN, ...)                                              \
-    if (R == 16) {                                                           \
+    if (R == 8) {                                                            \
+        switch (D) {                                                         \
+            case 1: return FN<1, 8>(__VA_ARGS__);                            \
+            case 2: return FN<2, 8>(__VA_ARGS__);                            \
+            case 3: return FN<3, 8>(__VA_ARGS__);                            \
+            case 4: return FN<4, 8>(__VA_ARGS__);                            \
+            case 6: return FN<6, 8>(__VA_ARGS__);                            \
+            case 8: return FN<8, 8>(__VA_ARGS__);                            \
+            case 12: return FN<12, 8>(__VA_ARGS__);                          \
+            case 16: return FN<16, 8>(__VA_ARGS__);                          \
+            default: break;                                                  \
+        }                                                                    \
+    } else if (R == 16) {                                                    \
         switch (D) {                                                         \
             case 1: return FN<1, 16>(__VA_ARGS__);                           \
             case 2: return FN<2, 16>(__VA_ARGS__);                           \

@@ -28,7 +28,14 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Per-pair storage, shared by host sizing and the device setup kernel.
 __host__ __device__ inline int64_t pair_hbuf_slots(int64_t nb, int64_t N) { return (nb - 1) * N; }
-__host__ __device__ inline int64_t pair_dir_words(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * (R / 16); }
+// Predecessor codes of one band: 2R bits per lane and step, R/16 words per
+// (step, lane) for R >= 16; for R = 8 one word holds two consecutive steps
+// (steps 2u and 2u+1 in its low and high halves).
+__host__ __device__ inline int64_t band_dir_words(int64_t N, int R)
+{
+    return R >= 16 ? (N + 31) * 32 * (R / 16) : ((N + 32) / 2) * 32;
+}
+__host__ __device__ inline int64_t pair_dir_words(int64_t nb, int64_t N, int R) { return nb * band_dir_words(N, R); }
 __host__ __device__ inline int64_t pair_rstore_floats(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * R; }
 
 struct Layout {

@@ -2,10 +2,16 @@
 //
 // Forward (Eqs. 3-5): r(i,j) = delta(i,j) + min^gamma(r(i-1,j-1), r(i-1,j), r(i,j-1)),
 //   min^gamma(a,b,c) = m - gamma ln(sum exp(-(v - m)/gamma)),  m = min(a,b,c)
-// (the exact rewrite of Eq. 3 with exp(-m/gamma) factored out), evaluated as
-//   m - (gamma ln 2) log2(sum 2^((m - v) log2(e)/gamma))
-// with the hardware ex2 / lg2 approximations (flush-to-zero forms).  Every r is stored (FP32) so the
-// backward pass can read it.
+// (the exact rewrite of Eq. 3 with exp(-m/gamma) factored out).  The diagonal
+// and left values are known before the row above is, so their part is taken
+// first: with m2 = min(dg, lf), S2 = 1 + 2^(-|dg - lf| k) (k = log2(e)/gamma)
+// and z = 2^(-|up - m2| k),
+//   sum = S2 + z          (up >= m2, m = m2)
+//   sum = S2 z + 1        (up <  m2, m = up)
+// and min^gamma = m - (gamma ln 2) log2(sum), with the hardware ex2 / lg2
+// approximations (flush-to-zero forms): two ex2 and one lg2 per cell, one ex2
+// and the lg2 on the serial path down the rows.  Every r is stored (FP32) so
+// the backward pass can read it.
 //
 // Backward (Eq. 6 with E from the reverse recursion of Cuturi and Blondel,
 // which the paper cites): e(M,N) = 1 and
@@ -54,6 +60,21 @@ __device__ __forceinline__ float lg2a(float x)
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// 16-byte asynchronous global -> shared copies (L2 only), in commit groups
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// Backward steps whose R blocks are in flight at once (shared-memory ring per warp)
+constexpr int kRPre = 8;
+template <int R>
+constexpr size_t rring_bytes(int block) { return (size_t)(block / 32) * kRPre * (R / 4) * 32 * sizeof(float4); }
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -155,12 +176,15 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
                 const float lf = col[k];
                 float t[D];
                 const float delta = local_cost<D>(b[k], y, t);
-                const float m = fminf(dg, fminf(up, lf));
-                const float S = __fadd_rn(__fadd_rn(ex2a(__fmul_rn(__fsub_rn(m, dg), kk)),
-                                                    ex2a(__fmul_rn(__fsub_rn(m, up), kk))),
-                                          ex2a(__fmul_rn(__fsub_rn(m, lf), kk)));
-                const float sm = __fmaf_rn(-gl, lg2a(S), m);
-                const float r = __fadd_rn(delta, sm);
+                // off the serial path (dg, lf known): m2 and S2; dg = lf = +inf
+                // (first column) gives NaN * k, and fminf(NaN, 0) = 0 keeps S2
+                // finite (it is then multiplied by z = 0)
+                const float m2 = fminf(dg, lf);
+                const float S2 = __fadd_rn(1.f, ex2a(fminf(__fmul_rn(__fsub_rn(m2, fmaxf(dg, lf)), kk), 0.f)));
+                const float du = __fsub_rn(up, m2);
+                const float z = ex2a(__fmul_rn(-fabsf(du), kk));
+                const float S = du >= 0.f ? __fadd_rn(S2, z) : __fmaf_rn(S2, z, 1.f);
+                const float r = __fmaf_rn(-gl, lg2a(S), __fadd_rn(delta, fminf(m2, up)));
                 dg = lf;
                 up = r;
                 col[k] = r;
@@ -189,7 +213,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 }
 
 template <int D, int R>
-__device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane)
+__device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring)
 {
     constexpr int BR = 32 * R;
     const int M = pd.M, N = pd.N, d = p.d;
@@ -224,17 +248,22 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     const float* rs = p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R;
 
     // R of this lane's rows at the column of step ss (written by forward step
-    // N+30-ss), loaded one step ahead of its use
-    float4 rnext[R / 4];
-    auto load_r = [&](int ss) {
+    // N+30-ss) is copied into ring slot ss mod kRPre kRPre steps ahead of its
+    // use (one commit group per step, empty past the end), so that a step's
+    // wait covers the copies issued kRPre steps earlier
+    const int steps = N + 31;
+    auto issue_r = [&](int ss) {
         const int jj = N - 1 - ss + (31 - lane);
-        if (jj >= 0 && jj < N) {
+        if (ss < steps && jj >= 0 && jj < N) {
             const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - ss) * 32 * R);
+            float4* dst = ring + (ss & (kRPre - 1)) * (R / 4) * 32;
 #pragma unroll
-            for (int k4 = 0; k4 < R / 4; ++k4) rnext[k4] = __ldcs(src4 + k4 * 32 + lane);
+            for (int k4 = 0; k4 < R / 4; ++k4) cp_async16(dst + k4 * 32 + lane, src4 + k4 * 32 + lane);
         }
+        cp_async_commit();
     };
-    load_r(0);
+#pragma unroll 1
+    for (int ss = 0; ss < kRPre; ++ss) issue_r(ss);
     // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l
     float ynext[D];
     u64 wa = 0, wb = 0;
@@ -248,12 +277,11 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     load_y(N - 1 - lane);
     if (!last) load_e(N - 1 - lane);
 
-    const int steps = N + 31;
     for (int s = 0; s < steps; ++s) {
         float4 rcur[R / 4];
+        cp_async_wait<kRPre - 1>();
 #pragma unroll
-        for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = rnext[k4];
-        if (s + 1 < steps) load_r(s + 1);
+        for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[(s & (kRPre - 1)) * (R / 4) * 32 + k4 * 32 + lane];
         if ((s & 31) == 0 && s < N) {
             const int jj = N - 1 - s - lane;
 #pragma unroll
@@ -262,7 +290,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 const bool ok = wait_filled(jj >= 0 && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
                                             [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
                                             p.hdr, 4, p.spin_limit);
-                if (!ok) return;
+                if (!ok) {
+                    cp_async_wait<0>();
+                    return;
+                }
                 if (jj >= 0) {
                     cr = __uint_as_float((uint32_t)wa);
                     cd = __uint_as_float((uint32_t)(wa >> 32));
@@ -333,7 +364,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 __stcg(emine + 2 * j + 1, pack2(ep[0], 0.f));
             }
         }
+        // the slot just read (its values are consumed) takes step s + kRPre
+        issue_r(s + kRPre);
     }
+    cp_async_wait<0>();
 
     float* gout = p.gpart + (int64_t)pd.out * M * d;
 #pragma unroll
@@ -347,6 +381,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 template <int D, int R, bool BWD>
 __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
 {
+    extern __shared__ float4 rring_all[];
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
@@ -365,7 +400,8 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
         const PairDesc pd = p.pairs[p.order[q]];
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
-            bwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane);
+            bwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane,
+                           rring_all + (threadIdx.x >> 5) * kRPre * (R / 4) * 32);
         } else {
             fwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
         }
@@ -403,7 +439,9 @@ template <int D, bool BWD>
 cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
-    softdtw_kernel<D, R, BWD><<<grid, block, 0, st>>>(p);
+    const size_t smem = BWD ? rring_bytes<R>(block) : 0;
+    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    softdtw_kernel<D, R, BWD><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -411,8 +449,10 @@ template <int D, bool BWD>
 int occ_d(int block)
 {
     constexpr int R = 8;
+    const size_t smem = BWD ? rring_bytes<R>(block) : 0;
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD>, block, 0);
+    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD>, block, smem);
     return n;
 }
 

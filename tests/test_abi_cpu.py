@@ -67,6 +67,13 @@ def test_workspace_sizes(lib):
     assert cells / 4 <= align - score <= cells / 4 * 2.5
     rc, dba = _size(lib, _abi.OP_DBA_ITERATE, 1100, b)
     assert rc == 0 and dba > align
+    # eight rows per lane: two steps' codes per word, the same 2 bits per cell
+    o = _abi.wts_options()
+    o.rows_per_thread = 8
+    rc, score8 = _size(lib, _abi.OP_ANOMALY_SCORE, 1100, b, o)
+    rc2, align8 = _size(lib, _abi.OP_DTW_ALIGN, 1100, b, o)
+    assert rc == 0 and rc2 == 0
+    assert cells / 4 <= align8 - score8 <= cells / 4 * 2.5
 
 
 def test_validation_errors(lib):

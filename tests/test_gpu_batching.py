@@ -34,7 +34,7 @@ def test_autotuned_options_are_exact(wts):
     Bt = torch.from_numpy(B).cuda()
     for op in (wts._abi.OP_ANOMALY_SCORE, wts._abi.OP_DTW_ALIGN):
         opts, ms = wts.autotune(op, Bt, gb)
-        assert opts.rows_per_thread in (16, 32) and 1 <= opts.warps_per_block <= 4 and ms > 0
+        assert opts.rows_per_thread in (8, 16, 32) and 1 <= opts.warps_per_block <= 4 and ms > 0
         again, _ = wts.autotune(op, Bt, gb)          # cached
         assert (again.rows_per_thread, again.warps_per_block) == (opts.rows_per_thread, opts.warps_per_block)
     s, c, L = wts.anomaly_score(Bt, gb, opts)

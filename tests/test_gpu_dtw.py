@@ -89,7 +89,7 @@ def test_dtw_align_paths_bit_exact(wts, case):
         assert (jlo[k] == r["jlo"]).all() and (jhi[k] == r["jhi"]).all(), k
 
 
-@pytest.mark.parametrize("rows,warps,order", [(16, 1, 0), (16, 3, 1), (32, 4, 0), (32, 2, 1)])
+@pytest.mark.parametrize("rows,warps,order", [(8, 4, 0), (8, 1, 1), (16, 1, 0), (16, 3, 1), (32, 4, 0), (32, 2, 1)])
 def test_launch_variants_agree(wts, rows, warps, order):
     rng = np.random.default_rng(102)
     cyc = [rng.normal(size=(n, 2)).astype(np.float32) for n in (3, 700, 1500, 1031)]
@@ -171,8 +171,8 @@ def test_full_size_sampled_pair(wts):
     assert (c.cpu().numpy() == cost).all() and (L.cpu().numpy() == plen).all()
 
 
-@pytest.mark.parametrize("G", [1, 2, 3, 16])
-def test_checkpoint_recompute_paths_identical(wts, G):
+@pytest.mark.parametrize("G,rows", [(1, 16), (2, 16), (3, 16), (16, 16), (3, 8), (5, 8)])
+def test_checkpoint_recompute_paths_identical(wts, G, rows):
     """dir_mode=1 keeps only the band hand-off rows and recomputes G bands of
     codes at a time during the backtrack: same paths, costs and |pi|."""
     rng = np.random.default_rng(104)
@@ -181,8 +181,8 @@ def test_checkpoint_recompute_paths_identical(wts, G):
     data, offs = _pack(cyc)
     gb = _gb(wts, data, offs)
     Bt = torch.from_numpy(B).cuda()
-    ref = [t.cpu().numpy() for t in wts.dtw_align(Bt, gb)]
-    got = [t.cpu().numpy() for t in wts.dtw_align(Bt, gb, wts.options(dir_mode=1, ckpt_bands=G))]
+    ref = [t.cpu().numpy() for t in wts.dtw_align(Bt, gb, wts.options(rows_per_thread=rows))]
+    got = [t.cpu().numpy() for t in wts.dtw_align(Bt, gb, wts.options(rows_per_thread=rows, dir_mode=1, ckpt_bands=G))]
     for a, b in zip(ref, got):
         assert (a == b).all()
     r = oracle.dtw(B, cyc[3], "f32")
@@ -246,3 +246,28 @@ def test_full_size_uneven_scoring_sampled(wts):
     for k in (int(np.argmax(N)), 0, 517):
         r = oracle.dtw(B, b.cycle(k), "f32", path=False)
         assert cost[k] == r["cost"] and plen[k] == r["plen"], k
+
+
+@pytest.mark.parametrize("d", [1, 6, 16])
+def test_half_word_codes(wts, d):
+    """Eight rows per lane: two steps' codes share one word, so an even and an
+    odd number of steps (N + 31) both close their last word; several bands of
+    256 rows with a ragged last band."""
+    rng = np.random.default_rng(106 + d)
+    cyc = [rng.normal(size=(n, d)).astype(np.float32) for n in (1, 2, 257, 600, 601, 1023)]
+    B = rng.normal(size=(1100, d)).astype(np.float32)
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    Bt = torch.from_numpy(B).cuda()
+    o8 = wts.options(rows_per_thread=8)
+    cost, plen, jlo, jhi = (t.cpu().numpy() for t in wts.dtw_align(Bt, gb, o8))
+    score, c2, p2 = wts.anomaly_score(Bt, gb, o8)
+    s32, c32, L32 = oracle.score(B, data, offs, "f32")
+    assert (cost == c32).all() and (plen == L32).all()
+    assert (c2.cpu().numpy() == c32).all() and (p2.cpu().numpy() == L32).all()
+    for k, y in enumerate(cyc):
+        r = oracle.dtw(B, y, "f32")
+        assert (jlo[k] == r["jlo"]).all() and (jhi[k] == r["jhi"]).all(), k
+    Bn, cnt, cb, ck = wts.dba_iterate(Bt, gb, o8)
+    Bo, cnt_o, cb_o, ck_o = oracle.dba_iterate(B, data, offs, "f32")
+    assert (Bn.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all()
