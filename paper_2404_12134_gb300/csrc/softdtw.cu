@@ -31,6 +31,8 @@
 // [(N+31) steps][R/4][32 lanes][4 floats].
 #include "softdtw.cuh"
 
+#include <type_traits>
+
 namespace wts {
 
 namespace {
@@ -110,7 +112,10 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     const int i0 = band * BR + lane * R;
     const bool top = band == 0;
     const bool last = band == pd.nbands - 1;
-    const float INF = inf_f();
+    // r outside the matrix: a large finite value instead of +inf, so that the
+    // difference of two such values is 0, not NaN (every cell of the matrix
+    // has a finite neighbour, and 2^(-(1e30 - r) k) is 0 as 2^(-inf) is)
+    const float INF = 1e30f;
     const float kk = kLog2e / p.gamma;
     const float gl = p.gamma * kLn2;
 
@@ -176,11 +181,9 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
                 const float lf = col[k];
                 float t[D];
                 const float delta = local_cost<D>(b[k], y, t);
-                // off the serial path (dg, lf known): m2 and S2; dg = lf = +inf
-                // (first column) gives NaN * k, and fminf(NaN, 0) = 0 keeps S2
-                // finite (it is then multiplied by z = 0)
+                // off the serial path (dg, lf known): m2 and S2
                 const float m2 = fminf(dg, lf);
-                const float S2 = __fadd_rn(1.f, ex2a(fminf(__fmul_rn(__fsub_rn(m2, fmaxf(dg, lf)), kk), 0.f)));
+                const float S2 = __fadd_rn(1.f, ex2a(__fmul_rn(-fabsf(__fsub_rn(dg, lf)), kk)));
                 const float du = __fsub_rn(up, m2);
                 const float z = ex2a(__fmul_rn(-fabsf(du), kk));
                 const float S = du >= 0.f ? __fadd_rn(S2, z) : __fmaf_rn(S2, z, 1.f);
@@ -225,8 +228,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 
     float b[R][D];
     load_rows<D, R>(b, pd.X, i0, M, d);
-    // state of each row at the column to the right (r, delta, e); beyond the
-    // matrix: (-inf, 0, 0)
+    // lanes whose rows reach the matrix's last row (or pass it)
+    const bool edge = last && i0 + R >= M;
+    // state of each row at the column to the right (r, delta k, e) with
+    // k = log2(e) / gamma; beyond the matrix: (-inf, 0, 0)
     float rp[R], dp[R], ep[R];
     float g[R][D];
 #pragma unroll
@@ -242,7 +247,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     float pbr = NINF, pbd = 0.f, pbe = 0.f;       // row below, one column to the right
 
     // boundary slot b holds the top row of band b+1: per column two 8-byte
-    // words {r, delta} and {e, 0}, each NaN until written
+    // words {r, delta k} and {e, 0}, each NaN until written
     const u64* enext = last ? nullptr : reinterpret_cast<const u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)band * N);
     u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
     const float* rs = p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R;
@@ -327,7 +332,11 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         pbr = br; pbd = bd; pbe = be;
 
         const int j = N - 1 - s + (31 - lane);
-        if (j >= 0 && j < N) {
+        // one column of the lane's rows, bottom to top; CHECKED: rows past the
+        // matrix and the seed e(M-1, N-1) = 1 (only the lanes at the matrix's
+        // last rows, and only at column N-1, take that path)
+        auto column = [&](auto checked) {
+            constexpr bool CHECKED = decltype(checked)::value;
             float nr = br, nd = bd, ne = be;       // below, column j
 #pragma unroll
             for (int k4 = R / 4 - 1; k4 >= 0; --k4) {
@@ -338,27 +347,35 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                     const int k = 4 * k4 + kq;
                     const float rr = rp[k], rd = dp[k], re = ep[k];
                     float rn = NINF, dn = 0.f, en = 0.f;
-                    if (i0 + k < M) {
+                    if (!CHECKED || i0 + k < M) {
                         const float r = rv[kq];
                         float t[D];
                         const float delta = local_cost<D>(b[k], y, t);
-                        const float a = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(nr, r), nd), kk));
-                        const float bb = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(rr, r), rd), kk));
-                        const float cc = ex2a(__fmul_rn(__fsub_rn(__fsub_rn(xr, r), xd), kk));
+                        // successor s: 2^((r(s) - r) k - delta(s) k), the difference
+                        // exact, then one fused multiply-add with delta(s) k kept per cell
+                        const float a = ex2a(__fmaf_rn(__fsub_rn(nr, r), kk, -nd));
+                        const float bb = ex2a(__fmaf_rn(__fsub_rn(rr, r), kk, -rd));
+                        const float cc = ex2a(__fmaf_rn(__fsub_rn(xr, r), kk, -xd));
                         // the row below's e (ne) is the only input computed in
                         // this step: it enters last, so the serial chain down the
                         // rows is one fused multiply-add per row
                         float e = __fmaf_rn(a, ne, __fmaf_rn(cc, xe, __fmul_rn(bb, re)));
-                        if (i0 + k == M - 1 && j == N - 1) e = 1.f;
+                        if (CHECKED && i0 + k == M - 1 && j == N - 1) e = 1.f;
 #pragma unroll
                         for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(e, t[c], g[k][c]);
-                        rn = r; dn = delta; en = e;
+                        rn = r; dn = __fmul_rn(delta, kk); en = e;
                     }
                     xr = rr; xd = rd; xe = re;
                     nr = rn; nd = dn; ne = en;
                     rp[k] = rn; dp[k] = dn; ep[k] = en;
                 }
             }
+        };
+        if (j >= 0 && j < N) {
+            if (edge && (i0 + R > M || j == N - 1))
+                column(std::true_type{});
+            else
+                column(std::false_type{});
             if (emine != nullptr && lane == 0 && !p.skip_handoff) {
                 __stcg(emine + 2 * j, pack2(rp[0], dp[0]));
                 __stcg(emine + 2 * j + 1, pack2(ep[0], 0.f));
