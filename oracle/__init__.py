@@ -17,7 +17,9 @@ What it computes (paper sections; the C body cites the equations):
 * ``softdtw``      - Soft-DTW value, R, E and gradient (Eqs. 3-6);
 * ``softdtw_batch``- barycenter objective Eq. 7 and its gradient;
 * ``medoid``, ``resample``, ``euclid_mean`` - initial barycenters (Table I:
-                     Euclidean-mean init; medoid for DBA).
+                     Euclidean-mean init; medoid for DBA);
+* ``subdtw``, ``segment`` - Sub-DTW and the sliding-window segmentation into
+                     cycles (Sec. 3.2).
 
 ``prec='f64'`` is the reference precision.  ``prec='f32'`` mirrors the CUDA
 kernels' operation order in float so that the warping path, an integer
@@ -91,6 +93,9 @@ def _lib(defines: tuple = ()):
             fn = getattr(lib, f"orc_softdtw_batch_{p}")
             fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, R, VP, VP, VP, VP]
             fn.restype = ctypes.c_int
+            fn = getattr(lib, f"orc_subdtw_{p}")
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, VP, VP, VP, VP, VP, VP]
+            fn.restype = ctypes.c_int
         _libs[key] = lib
         return lib
 
@@ -133,6 +138,48 @@ def dtw(B, Y, prec: str = "f64", path: bool = True, _defines: tuple = ()):
     out = dict(cost=cost[0], plen=L, jlo=jlo, jhi=jhi)
     if path:
         out["path_i"] = pi[:L].copy(); out["path_j"] = pj[:L].copy()
+    return out
+
+
+def subdtw(X, Y, prec: str = "f64", _defines: tuple = ()):
+    """Sub-DTW(X, Y) (Sec. 3.2): min over a <= b of DTW(X, Y[a..b]).
+
+    Returns dict(cost, a, b, plen, jlo, jhi): [a, b] is the matched piece of Y
+    (0-based, inclusive; b the first end column of minimum cost), jlo/jhi the
+    columns of each row of X on the path, plen = |pi|."""
+    X = _as2d(X); Y = _as2d(Y)
+    M, d = X.shape; N = Y.shape[0]
+    assert Y.shape[1] == d and M >= 1 and N >= 1
+    dt = _dt(prec)
+    cost = np.zeros(1, dtype=dt)
+    a = np.zeros(1, dtype=np.int32); b = np.zeros(1, dtype=np.int32); plen = np.zeros(1, dtype=np.int32)
+    jlo = np.zeros(M, dtype=np.int32); jhi = np.zeros(M, dtype=np.int32)
+    rc = getattr(_lib(_defines), f"orc_subdtw_{prec}")(X, M, Y, N, d, _ptr(cost), _ptr(a), _ptr(b), _ptr(plen),
+                                                     _ptr(jlo), _ptr(jhi))
+    if rc:
+        raise RuntimeError(f"oracle subdtw failed (rc={rc})")
+    return dict(cost=cost[0], a=int(a[0]), b=int(b[0]), plen=int(plen[0]), jlo=jlo, jhi=jhi)
+
+
+def segment(X, Y, alpha: int, prec: str = "f32"):
+    """Segmentation of a long series Y into cycles matching X (Sec. 3.2): the
+    window [ws, ws + 2M) (cut at the end of Y) is aligned by Sub-DTW, the piece
+    [ws + a*, ws + b*] is kept, and the next window starts at ws + b* - alpha,
+    while ws < N.  Reading for progress (the paper does not say): when
+    b* - alpha would not move the window forward, it starts one sample later.
+
+    Returns a list of (start, end, cost) with inclusive 0-based bounds."""
+    X = _as2d(X); Y = _as2d(Y)
+    M = X.shape[0]; N = Y.shape[0]
+    out = []
+    ws = 0
+    while ws < N:
+        we = min(ws + 2 * M, N)
+        r = subdtw(X, Y[ws:we], prec)
+        a, b = ws + r["a"], ws + r["b"]
+        out.append((a, b, r["cost"]))
+        nxt = b - alpha
+        ws = nxt if nxt > ws else ws + 1
     return out
 
 

@@ -86,3 +86,28 @@ def softdtw(B, Y, gamma: float):
         for i, j in p:
             E[i, j] += wk / Z
     return value, E
+
+
+def subdtw(X, Y):
+    """Sub-DTW (Sec. 3.2) by enumeration over every piece Y[a..b] and every
+    complete alignment path of X against it: (min cost, b*, the chosen path).
+
+    b* is the smallest end column among the optimal pieces; the chosen path is,
+    among the optimal paths ending at b*, the greatest under the tie order
+    diag > up > left walked back from (M-1, b*), where leaving row 0 (the
+    free start) counts as a diagonal step."""
+    D = cost_matrix(X, Y)
+    M, N = D.shape
+    best = math.inf
+    cands = []                      # (cost, b, path)
+    for a in range(N):
+        for b in range(a, N):
+            for p in paths(M, b - a + 1):
+                q = [(i, j + a) for i, j in p]
+                c = sum(D[i, j] for i, j in q)
+                cands.append((c, b, q))
+                best = min(best, c)
+    b_star = min(b for c, b, q in cands if c == best)
+    opt = [q for c, b, q in cands if c == best and b == b_star]
+    chosen = max(opt, key=lambda q: reversed_steps(q) + (DIAG,))
+    return best, b_star, chosen

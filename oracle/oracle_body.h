@@ -360,3 +360,83 @@ int SFX(orc_softdtw_batch)(const float* B, int64_t M, const float* Y, const int6
     free(g); free(v);
     return bad ? -1 : 0;
 }
+
+/*
+ * Sub-DTW (Sec. 3.2): the minimum over 0 <= a <= b < N of DTW(X, Y[a..b]),
+ * the whole of X (rows, length M) against the best contiguous piece of Y
+ * (columns).  Computed by the recursion of Eq. 5 (gamma = 0) with a free
+ * start: the padded row 0 is r(0,j) = 0 for every j >= 0 (a path may begin in
+ * any column), column 0 keeps r(i,0) = +inf for i >= 1.  Then
+ *   cost = min_j r(M, j),  b* = the smallest such j (reading: the paper does
+ *   not say which end wins a tie),
+ * and walking the recorded choices (tie order diag > up > left, as in DTW)
+ * back from (M, b*) until the walk leaves row 1 gives a*, the first column of
+ * the subsequence.  Outputs are 0-based; jlo/jhi[M] are the columns of each
+ * row of X on the path; plen = |pi| (cells on the path).
+ * Returns 0, -1 on allocation failure, -2 if the walk leaves the grid.
+ */
+int SFX(orc_subdtw)(const float* X, int64_t M, const float* Y, int64_t N, int d,
+                    REAL* cost, int32_t* a_star, int32_t* b_star, int32_t* plen,
+                    int32_t* jlo, int32_t* jhi)
+{
+    REAL* prev = (REAL*)malloc((size_t)(N + 1) * sizeof(REAL));
+    REAL* cur = (REAL*)malloc((size_t)(N + 1) * sizeof(REAL));
+    uint8_t* choice = (uint8_t*)malloc((size_t)M * (size_t)N);
+    if (!prev || !cur || !choice) { free(prev); free(cur); free(choice); return -1; }
+
+    for (int64_t j = 0; j <= N; ++j) prev[j] = 0;      /* free start */
+#ifdef ORACLE_PLANT_SUB_FIXED_START
+    for (int64_t j = 1; j <= N; ++j) prev[j] = (REAL)INFINITY;
+#endif
+    for (int64_t i = 1; i <= M; ++i) {
+        cur[0] = (REAL)INFINITY;
+        const float* xi = X + (i - 1) * d;
+        for (int64_t j = 1; j <= N; ++j) {
+            REAL dg = prev[j - 1], up = prev[j], lf = cur[j - 1];
+            REAL m;
+            uint8_t ch;
+            if (dg <= up && dg <= lf) { ch = 0; m = dg; }
+            else if (up <= lf) { ch = 1; m = up; }
+            else { ch = 2; m = lf; }
+            cur[j] = SFX(local_cost)(xi, Y + (j - 1) * d, d) + m;
+            choice[(i - 1) * N + (j - 1)] = ch;
+        }
+        REAL* t = prev; prev = cur; cur = t;
+    }
+    /* prev holds row M: the cheapest end column, the first one on ties */
+    int64_t jb = 1;
+    for (int64_t j = 2; j <= N; ++j)
+#ifdef ORACLE_PLANT_SUB_LAST_END
+        if (prev[j] <= prev[jb]) jb = j;
+#else
+        if (prev[j] < prev[jb]) jb = j;
+#endif
+    if (cost) *cost = prev[jb];
+    if (b_star) *b_star = (int32_t)(jb - 1);
+
+    int64_t i = M, j = jb, len = 0;
+    if (jhi) jhi[M - 1] = (int32_t)(j - 1);
+    for (;;) {
+        ++len;
+        uint8_t ch = choice[(i - 1) * N + (j - 1)];
+        if (i == 1 && ch != 2) break;           /* the path starts here (row 0 is free) */
+        if ((j == 1 && ch != 1) || len > M + N) { len = -1; break; }
+        if (ch == 0) {
+            if (jlo) jlo[i - 1] = (int32_t)(j - 1);
+            --i; --j;
+            if (jhi) jhi[i - 1] = (int32_t)(j - 1);
+        } else if (ch == 1) {
+            if (jlo) jlo[i - 1] = (int32_t)(j - 1);
+            --i;
+            if (jhi) jhi[i - 1] = (int32_t)(j - 1);
+        } else {
+            --j;
+        }
+    }
+    free(prev); free(cur); free(choice);
+    if (len < 0) return -2;
+    if (jlo) jlo[0] = (int32_t)(j - 1);
+    if (a_star) *a_star = (int32_t)(j - 1);
+    if (plen) *plen = (int32_t)len;
+    return 0;
+}

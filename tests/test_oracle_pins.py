@@ -290,6 +290,100 @@ def test_generator_is_seeded():
     assert a.d == 6 and a.T == 200 and int(a.labels.astype(bool).sum()) == 20
 
 
+# --- Sub-DTW and segmentation (Sec. 3.2) ---------------------------------------
+
+def _path_of(r):
+    """Cells of the oracle's Sub-DTW path from its per-row column ranges."""
+    cells = []
+    for i in range(len(r["jlo"])):
+        cells += [(i, j) for j in range(int(r["jlo"][i]), int(r["jhi"][i]) + 1)]
+    return cells
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_subdtw_matches_brute_force(prec):
+    """Integer samples (exact costs, frequent ties): the minimum over every
+    piece Y[a..b] and every path, the first optimal end column, and the path
+    chosen by the tie order."""
+    rng = np.random.default_rng(40)
+    for M in range(1, 5):
+        for N in range(1, 7):
+            for d in (1, 2):
+                X, Y = synth.integer_pair(rng, M, N, d, -2, 2)
+                best, b_star, chosen = brute.subdtw(X, Y)
+                r = oracle.subdtw(X, Y, prec)
+                assert float(r["cost"]) == best, (M, N, d)
+                assert r["b"] == b_star and r["a"] == chosen[0][1], (M, N, d)
+                assert _path_of(r) == chosen and r["plen"] == len(chosen), (M, N, d)
+
+
+def test_subdtw_real_values_brute_force():
+    rng = np.random.default_rng(41)
+    for M, N in ((3, 6), (4, 5), (2, 6)):
+        X, Y = _real_pair(rng, M, N, 2)
+        best, b_star, chosen = brute.subdtw(X, Y)
+        r = oracle.subdtw(X, Y, "f64")
+        assert abs(r["cost"] - best) <= 1e-12 * max(1.0, best)
+        assert r["b"] == b_star and _path_of(r) == chosen
+
+
+def test_subdtw_embedded_copy_and_bounds():
+    """X copied exactly into Y between samples far from it: cost 0 on the
+    copy, one cell per row.  In general Sub-DTW <= DTW(X, Y), and with one
+    column the cost is sum_i delta(i, 0)."""
+    rng = np.random.default_rng(42)
+    X = rng.normal(size=(37, 3)).astype(np.float32)
+    pre = (rng.normal(size=(23, 3)) + 20).astype(np.float32)
+    post = (rng.normal(size=(41, 3)) - 20).astype(np.float32)
+    Y = np.concatenate([pre, X, post])
+    for prec in ("f64", "f32"):
+        r = oracle.subdtw(X, Y, prec)
+        assert float(r["cost"]) == 0.0 and (r["a"], r["b"]) == (23, 23 + 36) and r["plen"] == 37
+        assert (r["jlo"] == np.arange(23, 60)).all() and (r["jhi"] == r["jlo"]).all()
+    for _ in range(5):
+        X, Y = _real_pair(rng, 17, 29, 2)
+        assert oracle.subdtw(X, Y)["cost"] <= oracle.dtw(X, Y, path=False)["cost"] + 1e-12
+        y = Y[5:6]
+        r = oracle.subdtw(X, y)
+        assert abs(r["cost"] - brute.cost_matrix(X, y)[:, 0].sum()) <= 1e-12 * r["cost"]
+        assert (r["a"], r["b"], r["plen"]) == (0, 0, 17)
+
+
+def test_segmentation_of_repeated_copies():
+    """A series of K exact copies of X: every window holds one whole copy at
+    zero cost, so the first K pieces are the copies themselves; the loop ends
+    once the window start passes the end of the series."""
+    rng = np.random.default_rng(43)
+    M, K = 29, 6
+    X = rng.normal(size=(M, 2)).astype(np.float32)
+    Y = np.concatenate([X] * K)
+    segs = oracle.segment(X, Y, alpha=int(0.15 * M))
+    assert [(a, b) for a, b, c in segs[:K]] == [(k * M, k * M + M - 1) for k in range(K)]
+    assert all(float(c) == 0.0 for a, b, c in segs[:K])
+    assert all(b < len(Y) for a, b, c in segs)
+
+
+def _sub_pins_fail(defines) -> bool:
+    rng = np.random.default_rng(44)
+    try:
+        for M in range(1, 4):
+            for N in range(2, 6):
+                X, Y = synth.integer_pair(rng, M, N, 1, -2, 2)
+                best, b_star, chosen = brute.subdtw(X, Y)
+                r = oracle.subdtw(X, Y, "f64", _defines=defines)
+                if float(r["cost"]) != best or r["b"] != b_star or _path_of(r) != chosen:
+                    return True
+    except Exception:
+        return True
+    return False
+
+
+@pytest.mark.parametrize("plant", ["ORACLE_PLANT_SUB_FIXED_START", "ORACLE_PLANT_SUB_LAST_END"])
+def test_planted_subdtw_mistakes_are_caught(plant):
+    assert not _sub_pins_fail(())
+    assert _sub_pins_fail((plant,))
+
+
 # --- mutation check: each planted mistake trips a pin ----------------------------
 
 def _pins_fail(defines) -> bool:
