@@ -60,6 +60,7 @@ enum {
     WTS_OP_SOFTDTW = 4,        /* softdtw_forward + softdtw_backward (R kept in the workspace) */
     WTS_OP_PAIRWISE = 5,
     WTS_OP_COMPACT_NAN = 6,    /* wts_compact_nan (M ignored) */
+    WTS_OP_SUBDTW = 7,         /* subdtw_align (M = length of X) */
 };
 
 /* A packed batch of T cycles (Sec. 3.1: d-channel series of uneven lengths). */
@@ -152,6 +153,51 @@ int anomaly_score(const float* B, int64_t M, const wts_batch* Y, const wts_optio
 int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
               void* workspace, size_t workspace_bytes, void* stream,
               float* cost, int32_t* plen, int32_t* jlo, int32_t* jhi);
+
+/*
+ * subdtw_align - Sub-DTW (Sec. 3.2): for every cycle ("window") Y_k of the
+ * batch, the minimum over 0 <= a <= b < N_k of DTW(X, Y_k[a..b]), the whole
+ * reference X (length M, rows) against the best contiguous piece of Y_k.  The
+ * recursion of Eq. 5 (gamma = 0) runs with a free start (the row above X is
+ * 0 in every column); b* is the first column of minimum cost in X's last row,
+ * and the walk back from (M-1, b*) under the tie order diag > up > left stops
+ * where it leaves X's first row, at a*.
+ *   X    [M][d]                  in (device)
+ *   cost [T]                     out, min_b r(M-1, b) (may be NULL)
+ *   a_star, b_star [T]           out (int32), 0-based inclusive bounds in Y_k
+ *   plen [T]                     out, |pi| (may be NULL)
+ *   jlo, jhi [T][M]              out (int32), columns of each row of X
+ * rows_per_thread must be 0 or 16; dir_mode 1 (checkpointing) is not offered.
+ * Workspace: wts_workspace_size(WTS_OP_SUBDTW, M, Y, ...).
+ */
+int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_options* opt,
+                 void* workspace, size_t workspace_bytes, void* stream,
+                 float* cost, int32_t* a_star, int32_t* b_star, int32_t* plen, int32_t* jlo, int32_t* jhi);
+
+/*
+ * wts_segment - the segmentation of Sec. 3.2: a long d-channel series Y
+ * (Ydata [N][d], device) is cut into cycles matching the reference X
+ * ([M][d], device).  Window [ws, we) with ws = 0, we = ws + 2M (cut at N);
+ * Sub-DTW of X against the window gives [a*, b*]; the piece
+ * [ws + a*, ws + b*] is recorded and the next window starts at
+ * ws + b* - alpha (the paper takes alpha = 0.15 M), while ws < N.  Two
+ * readings where the paper does not say: the window that reaches the end of
+ * Y is the last one, and when b* - alpha would not move the window forward
+ * the next one starts at ws + b* + 1.
+ *   seg_start, seg_end [max_segments]   out (host, int64, inclusive)
+ *   seg_cost [max_segments]             out (host, may be NULL)
+ *   n_segments                          out (host): pieces found; if more
+ *                                       than max_segments, the first
+ *                                       max_segments are stored and
+ *                                       WTS_ENOMEM is returned
+ * Each window is one subdtw_align call; the window's bounds are read back
+ * before the next (the stream is synchronised once per window).  Workspace:
+ * wts_segment_workspace_size.
+ */
+int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, size_t* bytes);
+int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_t d, int64_t alpha,
+                const wts_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                int32_t max_segments, int64_t* seg_start, int64_t* seg_end, float* seg_cost, int32_t* n_segments);
 
 /*
  * dba_iterate - one iteration of DTW Barycenter Averaging (Petitjean et al.

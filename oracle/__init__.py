@@ -165,8 +165,10 @@ def segment(X, Y, alpha: int, prec: str = "f32"):
     """Segmentation of a long series Y into cycles matching X (Sec. 3.2): the
     window [ws, ws + 2M) (cut at the end of Y) is aligned by Sub-DTW, the piece
     [ws + a*, ws + b*] is kept, and the next window starts at ws + b* - alpha,
-    while ws < N.  Reading for progress (the paper does not say): when
-    b* - alpha would not move the window forward, it starts one sample later.
+    while ws < N.  Readings (the paper does not say): the window that reaches
+    the end of Y is the last one (a later window would only cover its tail
+    again), and when b* - alpha would not move the window forward the next one
+    starts at ws + b* + 1.
 
     Returns a list of (start, end, cost) with inclusive 0-based bounds."""
     X = _as2d(X); Y = _as2d(Y)
@@ -178,8 +180,10 @@ def segment(X, Y, alpha: int, prec: str = "f32"):
         r = subdtw(X, Y[ws:we], prec)
         a, b = ws + r["a"], ws + r["b"]
         out.append((a, b, r["cost"]))
+        if we == N:
+            break
         nxt = b - alpha
-        ws = nxt if nxt > ws else ws + 1
+        ws = nxt if nxt > ws else b + 1
     return out
 
 

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libwetsand.so")
 
 WTS_OK, WTS_EINVAL, WTS_ENOMEM, WTS_ECUDA, WTS_ETIMEOUT = 0, 1, 2, 3, 4
 OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE, OP_COMPACT_NAN = 1, 2, 3, 4, 5, 6
+OP_SUBDTW = 7
 
 # every symbol declared in include/wetsand.h
 EXPORTS = (
@@ -22,6 +23,7 @@ EXPORTS = (
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
     "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune", "wts_compact_nan",
+    "subdtw_align", "wts_segment_workspace_size", "wts_segment",
 )
 
 
@@ -73,6 +75,10 @@ _SIGS = {
     "anomaly_score": ([VP, I64, PB, PO, VP, SZ, VP, VP, VP, VP], ctypes.c_int),
     "dtw_align": ([VP, I64, PB, PO, VP, SZ, VP, VP, VP, VP, VP], ctypes.c_int),
     "dba_iterate": ([VP, VP, I64, PB, PO, VP, SZ, VP, VP, VP, VP], ctypes.c_int),
+    "subdtw_align": ([VP, I64, PB, PO, VP, SZ, VP, VP, VP, VP, VP, VP, VP], ctypes.c_int),
+    "wts_segment_workspace_size": ([I64, I32, PO, ctypes.POINTER(SZ)], ctypes.c_int),
+    "wts_segment": ([VP, I64, VP, I64, I32, I64, PO, VP, SZ, VP, I32, VP, VP, VP, ctypes.POINTER(I32)],
+                    ctypes.c_int),
     "wts_pairwise_dtw": ([PB, PO, VP, SZ, VP, VP], ctypes.c_int),
     "wts_medoid": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),

@@ -200,6 +200,53 @@ def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = N
     return cost, plen, jlo, jhi
 
 
+def subdtw_align(X: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None):
+    """Sub-DTW of X against every cycle (window) of the batch (Sec. 3.2):
+    (cost [T], a_star [T], b_star [T], plen [T], jlo [T, M], jhi [T, M])."""
+    X = _check_B(X, batch.d)
+    M = X.shape[0]
+    lib = _abi.load()
+    nb = workspace_size(_abi.OP_SUBDTW, M, batch, opts)
+    buf = _ws(ws, nb)
+    dev = X.device
+    cost = torch.empty(batch.T, dtype=torch.float32, device=dev)
+    ab = torch.empty((3, batch.T), dtype=torch.int32, device=dev)
+    jlo = torch.empty((batch.T, M), dtype=torch.int32, device=dev)
+    jhi = torch.empty((batch.T, M), dtype=torch.int32, device=dev)
+    check(lib.subdtw_align(X.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts), buf.data_ptr(), buf.numel(),
+                           _stream(), cost.data_ptr(), ab[0].data_ptr(), ab[1].data_ptr(), ab[2].data_ptr(),
+                           jlo.data_ptr(), jhi.data_ptr()))
+    return cost, ab[0], ab[1], ab[2], jlo, jhi
+
+
+def segment(X: torch.Tensor, Y: torch.Tensor, alpha: int | None = None, opts=None, max_segments: int = 4096,
+            ws: Workspace | None = None):
+    """Cut the long series Y [N, d] (device) into cycles matching X [M, d]
+    (Sec. 3.2; alpha defaults to 0.15 M).  Returns a list of
+    (start, end, cost), inclusive bounds."""
+    if Y.dim() == 1:
+        Y = Y[:, None]
+    if not (Y.is_cuda and Y.dtype == torch.float32 and Y.is_contiguous()):
+        raise ValueError("Y must be a contiguous float32 CUDA tensor [N, d]")
+    X = _check_B(X, Y.shape[1])
+    M, d = X.shape
+    N = Y.shape[0]
+    if alpha is None:
+        alpha = int(0.15 * M)
+    lib = _abi.load()
+    nbytes = ctypes.c_size_t(0)
+    check(lib.wts_segment_workspace_size(M, d, _opt(opts), ctypes.byref(nbytes)))
+    buf = _ws(ws, nbytes.value)
+    start = np.zeros(max_segments, dtype=np.int64)
+    end = np.zeros(max_segments, dtype=np.int64)
+    cost = np.zeros(max_segments, dtype=np.float32)
+    n = ctypes.c_int32(0)
+    check(lib.wts_segment(X.data_ptr(), M, Y.data_ptr(), N, d, alpha, _opt(opts), buf.data_ptr(), buf.numel(),
+                          _stream(), max_segments, start.ctypes.data, end.ctypes.data, cost.ctypes.data,
+                          ctypes.byref(n)))
+    return [(int(start[k]), int(end[k]), float(cost[k])) for k in range(n.value)]
+
+
 def dba_iterate(B_in: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None, B_out=None,
                 counts=None, cost_before=None, cost=None):
     """One DBA iteration: (B_out [M, d], counts [M], cost_before (0-d float64), cost [T])."""

@@ -138,6 +138,12 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->d = Y->d;
     L->D = D;
     L->R = pick_R(D, opt);
+    if (op == kOpSubdtw) {
+        if (opt && opt->rows_per_thread && opt->rows_per_thread != 16)
+            return fail(WTS_EINVAL, "Sub-DTW runs with rows_per_thread = 16 (got %d)", opt->rows_per_thread);
+        if (opt && opt->dir_mode == 1) return fail(WTS_EINVAL, "Sub-DTW keeps every code (dir_mode must be 0)");
+        L->R = 16;
+    }
     if (op == kOpSoft) {
         if (D > 8) return fail(WTS_EINVAL, "soft-DTW supports d <= 8 (got %d)", Y->d);
         L->R = soft_rows(D);          // fixed by the channel count (registers)
@@ -161,7 +167,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         const int64_t nb = cdiv(Mp, L->BR);
         items += nb;
         h += pair_hbuf_slots(nb, Np);
-        if (op == kOpAlign || op == kOpDba) {
+        if (op == kOpAlign || op == kOpDba || op == kOpSubdtw) {
             const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
             dw += pair_dir_words(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
         }
@@ -185,7 +191,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->off_order = take((size_t)L->P * sizeof(int32_t));
     L->off_prefix = take((size_t)(L->P + 1) * sizeof(int32_t));
     L->off_hbuf = take(L->hbuf_bytes);
-    if (op == kOpAlign || op == kOpDba) {
+    if (op == kOpAlign || op == kOpDba || op == kOpSubdtw) {
         L->off_dirs = take((size_t)dw * sizeof(uint32_t));
         if (opt && opt->dir_mode == 1) {
             L->group_bands = opt->ckpt_bands ? opt->ckpt_bands : 16;
@@ -484,14 +490,14 @@ int wts_peak_probe(int which, double* ops_per_s)
 int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes)
 {
     if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
-    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise};
+    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise, 0, kOpSubdtw};
     if (op == WTS_OP_COMPACT_NAN) {
         int rc = check_batch(Y, false);
         if (rc) return rc;
         *bytes = align256(compact_workspace_bytes(Y->offsets_host[Y->T]));
         return ok();
     }
-    if (op < 1 || op > 5) return fail(WTS_EINVAL, "unknown op %d", op);
+    if (op < 1 || op > 7 || op == WTS_OP_COMPACT_NAN) return fail(WTS_EINVAL, "unknown op %d", op);
     Layout L;
     int rc = compute_layout(map[op], M, Y, opt, &L);
     if (rc) return rc;
@@ -543,6 +549,149 @@ int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* 
     if (!B || !jlo || !jhi) return fail(WTS_EINVAL, "B, jlo and jhi must not be NULL");
     if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
     if ((rc = align_into(L, (char*)workspace, B, Y, opt, (cudaStream_t)stream, cost, plen, jlo, jhi))) return rc;
+    return ok();
+}
+
+int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_options* opt,
+                 void* workspace, size_t workspace_bytes, void* stream,
+                 float* cost, int32_t* a_star, int32_t* b_star, int32_t* plen, int32_t* jlo, int32_t* jhi)
+{
+    Layout L;
+    int rc = compute_layout(kOpSubdtw, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!X || !a_star || !b_star || !jlo || !jhi) return fail(WTS_EINVAL, "X, a_star, b_star, jlo and jhi must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = prepare(L, ws, X, Y, opt, st))) return rc;
+    DPParams p = base_params(L, ws, opt);
+    p.cost_out = cost;
+    p.bstar_out = b_star;
+    if ((rc = launch_dp(kModeSubDirs, L, p, opt, st))) return rc;
+    BTParams bt{};
+    bt.pairs = p.pairs;
+    bt.P = L.P;
+    bt.R = L.R;
+    bt.dirs = p.dirs;
+    bt.jlo = jlo;
+    bt.jhi = jhi;
+    bt.plen = plen;
+    bt.M = L.M;
+    bt.band_lo = 0;
+    bt.band_hi = (int)cdiv(L.M, L.BR);
+    bt.subseq = 1;
+    bt.bstar = b_star;
+    bt.astar = a_star;
+    cudaError_t e;
+    {
+        Prof pr("backtrack", st);
+        e = launch_backtrack(bt, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+    return ok();
+}
+
+namespace {
+
+// Workspace of wts_segment: the Sub-DTW layout of one full window (2M
+// columns) followed by the window's offsets and outputs.
+struct SegLayout {
+    Layout L;
+    size_t off_offsets, off_cost, off_ab, off_jlo, off_jhi, total;
+};
+
+int segment_layout(int64_t M, int32_t d, const wts_options* opt, SegLayout* S)
+{
+    if (M < 1 || M > ((int64_t)1 << 29)) return fail(WTS_EINVAL, "M=%lld out of range", (long long)M);
+    int64_t offs[2] = {0, 2 * M};
+    wts_batch b{};
+    b.offsets_host = offs;
+    b.T = 1;
+    b.d = d;
+    int rc = compute_layout(kOpSubdtw, M, &b, opt, &S->L);
+    if (rc) return rc;
+    size_t off = align256(S->L.total);
+    auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
+    S->off_offsets = take(2 * sizeof(int64_t));
+    S->off_cost = take(sizeof(float));
+    S->off_ab = take(3 * sizeof(int32_t));          // a*, b*, |pi|
+    S->off_jlo = take((size_t)M * sizeof(int32_t));
+    S->off_jhi = take((size_t)M * sizeof(int32_t));
+    S->total = off;
+    return WTS_OK;
+}
+
+}  // namespace
+
+int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, size_t* bytes)
+{
+    if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
+    SegLayout S;
+    int rc = segment_layout(M, d, opt, &S);
+    if (rc) return rc;
+    *bytes = S.total;
+    return ok();
+}
+
+int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_t d, int64_t alpha,
+                const wts_options* opt, void* workspace, size_t workspace_bytes, void* stream,
+                int32_t max_segments, int64_t* seg_start, int64_t* seg_end, float* seg_cost, int32_t* n_segments)
+{
+    if (!X || !Ydata || !n_segments || (max_segments > 0 && (!seg_start || !seg_end)))
+        return fail(WTS_EINVAL, "X, Ydata, n_segments (and seg_start/seg_end) must not be NULL");
+    if (N < 1) return fail(WTS_EINVAL, "N=%lld (need >= 1)", (long long)N);
+    if (alpha < 0) return fail(WTS_EINVAL, "alpha must be >= 0");
+    if (max_segments < 0) return fail(WTS_EINVAL, "max_segments must be >= 0");
+    SegLayout S;
+    int rc = segment_layout(M, d, opt, &S);
+    if (rc) return rc;
+    if (!workspace || ((uintptr_t)workspace & 255) != 0) return fail(WTS_EINVAL, "workspace must be 256-byte aligned");
+    if (workspace_bytes < S.total) return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, S.total);
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t* d_offs = reinterpret_cast<int64_t*>(ws + S.off_offsets);
+    float* d_cost = reinterpret_cast<float*>(ws + S.off_cost);
+    int32_t* d_ab = reinterpret_cast<int32_t*>(ws + S.off_ab);
+    int32_t found = 0;
+    int64_t pos = 0;
+    while (pos < N) {
+        const int64_t n = (pos + 2 * M < N ? pos + 2 * M : N) - pos;
+        int64_t offs[2] = {0, n};
+        cudaError_t e = cudaMemcpyAsync(d_offs, offs, sizeof(offs), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "window offsets copy");
+        wts_batch b{};
+        b.data = Ydata + pos * d;
+        b.offsets = d_offs;
+        b.offsets_host = offs;
+        b.T = 1;
+        b.d = d;
+        rc = subdtw_align(X, M, &b, opt, ws, S.L.total, stream, d_cost, d_ab, d_ab + 1, d_ab + 2,
+                          reinterpret_cast<int32_t*>(ws + S.off_jlo), reinterpret_cast<int32_t*>(ws + S.off_jhi));
+        if (rc) return rc;
+        int32_t ab[3];
+        float c = 0.f;
+        WsHeader h;
+        e = cudaMemcpyAsync(ab, d_ab, sizeof(ab), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&c, d_cost, sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ws + S.L.off_hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "window result read-back");
+        if (h.status == kDevTimeout) return fail(WTS_ETIMEOUT, "a wait in the window at %lld gave up", (long long)pos);
+        if (ab[0] < 0 || ab[1] < ab[0] || ab[1] >= n)
+            return fail(WTS_ECUDA, "window at %lld gave an invalid piece [%d, %d]", (long long)pos, ab[0], ab[1]);
+        if (found < max_segments) {
+            seg_start[found] = pos + ab[0];
+            seg_end[found] = pos + ab[1];
+            if (seg_cost) seg_cost[found] = c;
+        }
+        ++found;
+        if (pos + n == N) break;                      // this window reached the end of Y
+        const int64_t next = pos + ab[1] - alpha;
+        pos = next > pos ? next : pos + ab[1] + 1;
+    }
+    *n_segments = found;
+    if (found > max_segments) return fail(WTS_ENOMEM, "%d pieces found, room for %d", found, max_segments);
     return ok();
 }
 

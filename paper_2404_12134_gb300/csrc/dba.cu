@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
         int32_t* jhi = p.jhi + (int64_t)pd.out * p.M;
         int i, j, len;
         if (p.state == nullptr || p.first) {
-            i = pd.M - 1; j = N - 1; len = 0;
+            i = pd.M - 1; j = p.subseq ? p.bstar[pd.out] : N - 1; len = 0;
             if (lane == 0) jhi[i] = j;
         } else {
             i = p.state[3 * q]; j = p.state[3 * q + 1]; len = p.state[3 * q + 2];
@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             // left (nd = nu = 1) moves left
             const int di = (nd == 0u || nu == 0u) ? 1 : 0;
             const int dj = (nd == 0u || nu == 1u) ? 1 : 0;
+            // Sub-DTW: a move up from row 0 reaches the free start
+            if (p.subseq && i == 0 && di) break;
             // a valid code matrix only moves left on row 0 and only up on
             // column 0; anything else is reported as |pi| = -1
             if ((i == 0 && di) || (j == 0 && dj)) { len = -1; break; }
@@ -135,7 +137,12 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             continue;
         }
         if (lane == 0) {
-            if (i == 0 && j == 0 && len > 0) jlo[0] = 0;
+            if (p.subseq) {
+                if (len > 0) jlo[0] = j;
+                p.astar[pd.out] = len > 0 ? j : -1;
+            } else if (i == 0 && j == 0 && len > 0) {
+                jlo[0] = 0;
+            }
             if (p.plen) p.plen[pd.out] = len;
             if (p.state) { p.state[3 * q] = -1; p.state[3 * q + 2] = len; }
         }

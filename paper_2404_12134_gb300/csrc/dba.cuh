@@ -22,6 +22,11 @@ struct BTParams {
     int band_lo, band_hi;
     int32_t* state;
     int first;           // 1: start every walk at (M-1, N-1)
+    // Sub-DTW (Sec. 3.2): start at (M-1, bstar[out]) and stop when the walk
+    // leaves row 0 (the free start), writing that column to astar[out]
+    int subseq;
+    const int32_t* bstar;
+    int32_t* astar;
 };
 
 cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st);

@@ -89,6 +89,23 @@ __device__ __forceinline__ uint32_t ne_mask(float a, float b)
 
 constexpr int kRing = 128;   // columns of cycle samples staged per warp
 
+// c[k] for a k known only at run time, by a binary tree of selects on the bits
+// of k (R - 1 selects, no local memory)
+template <int R>
+__device__ __forceinline__ float pick_row(const float (&c)[R], int k)
+{
+    float v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = c[q];
+#pragma unroll
+    for (int w = R / 2; w >= 1; w /= 2) {
+        const bool hi = (k & w) != 0;
+#pragma unroll
+        for (int q = 0; q < w; ++q) v[q] = hi ? v[q + w] : v[q];
+    }
+    return v[0];
+}
+
 template <int D, int R, int MODE>
 struct Band {
     static constexpr int BR = 32 * R;
@@ -104,6 +121,13 @@ struct Band {
     float topv;                             // lane l: r(band top - 1, s0 + l)
     int topc;
     uint32_t half;                          // R = 8: codes of the last even step
+    // kModeSubDirs, matrix's last band: running minimum of r(M-1, j) over the
+    // lane's columns (row kk of the lane), and its first column
+    bool track;
+    int kk;
+    float best;
+    int bestj;
+    static constexpr bool CODES = MODE == kModeDirs || MODE == kModeSubDirs;
 
     // Local costs of column jc for the lane's rows, pair q (two rows at once).
     __device__ __forceinline__ void cost_pair(const u64* yy, int q)
@@ -136,7 +160,9 @@ struct Band {
         const float INF = inf_f();
         const float above = __shfl_up_sync(FULL, col[R - 1], 1);
         const float tv = __shfl_sync(FULL, topv, src);
-        const float up_in = lane == 0 ? (top ? INF : tv) : above;
+        // above the matrix: +inf (DTW), 0 for Sub-DTW (a path may start in any column)
+        const float top_in = MODE == kModeSubDirs ? 0.f : INF;
+        const float up_in = lane == 0 ? (top ? top_in : tv) : above;
         const float dg_in = prev_up;
         prev_up = up_in;
         int upc_in = 0, dgc_in = 0;
@@ -161,7 +187,7 @@ struct Band {
                 const float lf = col[k];
                 const float m = min3f(dg, up, lf);
                 const float r = __fadd_rn(dl[k], m);
-                if (MODE == kModeDirs) {
+                if (CODES) {
                     word[k >> 5] |= ne_mask(dg, m) & (1u << (k & 31));
                     word[(R + k) >> 5] |= ne_mask(up, m) & (1u << ((R + k) & 31));
                 } else if (MODE == kModePlen) {
@@ -176,6 +202,10 @@ struct Band {
                 col[k] = r;
                 if (k & 1) cost_pair(yy, k >> 1);      // rows k-1, k of column j+1
             }
+            if (MODE == kModeSubDirs && track) {
+                const float v = pick_row<R>(col, kk);
+                if (v < best) { best = v; bestj = j; }
+            }
             if (lane == 31 && hcur != nullptr) {
                 if (MODE == kModePlen)
                     __stcg(reinterpret_cast<u64*>(hcur) + j, pack2(col[R - 1], __int_as_float(cnt[R - 1])));
@@ -186,7 +216,7 @@ struct Band {
 #pragma unroll
             for (int q = 0; q < Q; ++q) cost_pair(yy, q);
         }
-        if (MODE == kModeDirs) {
+        if (CODES) {
             if (W == 0) {
                 if ((s & 1) == 0)
                     half = word[0];
@@ -232,6 +262,10 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     st.topv = INF;
     st.topc = 0;
     st.half = 0u;
+    st.track = MODE == kModeSubDirs && last;
+    st.kk = M - 1 - i0;
+    st.best = INF;
+    st.bestj = 0;
 
     // hand-off rows: slot size 4 bytes (r), or 8 bytes ({r, cells}) with |pi|
     constexpr int SLOT = MODE == kModePlen ? 8 : 4;
@@ -239,7 +273,7 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     const char* hprev = top ? nullptr : hb + (pd.hbuf_off + (int64_t)(band - 1) * N) * SLOT;
     // a recomputed band reads its stored top row and produces no hand-off row
     void* hcur = (last || p.recompute || p.skip_handoff) ? nullptr : hb + (pd.hbuf_off + (int64_t)band * N) * SLOT;
-    uint32_t* dout = (MODE == kModeDirs) ? p.dirs + pd.dir_off + (int64_t)(band - p.band_lo) * band_dir_words(N, R)
+    uint32_t* dout = BandT::CODES ? p.dirs + pd.dir_off + (int64_t)(band - p.band_lo) * band_dir_words(N, R)
                                          : nullptr;
 
     // Cycle samples go through the ring two chunks of 32 columns ahead of the
@@ -307,9 +341,14 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
         }
     }
 
-    if (MODE == kModeDirs && W == 0 && (steps & 1)) __stcs(dout + (int64_t)(steps >> 1) * 32 + lane, st.half);
+    if (BandT::CODES && W == 0 && (steps & 1)) __stcs(dout + (int64_t)(steps >> 1) * 32 + lane, st.half);
 
-    if (last && !p.recompute) {
+    if (MODE == kModeSubDirs) {
+        if (last && lane == (M - 1 - band * BR) / R) {
+            if (p.cost_out) p.cost_out[pd.out] = st.best;
+            p.bstar_out[pd.out] = st.bestj;
+        }
+    } else if (last && !p.recompute) {
         const int ilast = M - 1 - band * BR;
         if (lane == ilast / R) {
             const int kk = ilast % R;
@@ -387,6 +426,14 @@ cudaError_t launch_mode(int mode, const DPParams& p, int grid, int block, cudaSt
             cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             dtw_wavefront_kernel<D, R, kModeDirs><<<grid, block, smem, st>>>(p);
             break;
+        case kModeSubDirs:
+            if constexpr (R == 16) {
+                cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeSubDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                dtw_wavefront_kernel<D, R, kModeSubDirs><<<grid, block, smem, st>>>(p);
+                break;
+            } else {
+                return cudaErrorInvalidValue;
+            }
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -409,6 +456,12 @@ int occ_mode(int mode, int block)
         case kModeDirs:
             cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeDirs>, block, smem);
+            break;
+        case kModeSubDirs:
+            if constexpr (R == 16) {
+                cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeSubDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeSubDirs>, block, smem);
+            }
             break;
         default: break;
     }

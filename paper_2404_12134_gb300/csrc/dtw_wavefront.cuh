@@ -10,6 +10,8 @@ enum DPMode : int {
     kModeCost = 0,    // r(M,N) only
     kModePlen = 1,    // r(M,N) and |pi| (cells on the tie-rule path), score = r / |pi|
     kModeDirs = 2,    // r(M,N) and a 2-bit predecessor code per cell
+    kModeSubDirs = 3, // Sub-DTW (Sec. 3.2): free start (the row above the matrix is 0), codes,
+                      // and min_j r(M-1, j) with its first column j (R = 16 only)
 };
 
 struct DPParams {
@@ -26,6 +28,7 @@ struct DPParams {
     float* cost_out;     // [*] indexed by PairDesc::out (may be null)
     int32_t* plen_out;   // [*] (kModePlen, may be null)
     float* score_out;    // [*] (kModePlen, may be null)
+    int32_t* bstar_out;  // [*] (kModeSubDirs): the first column of minimum r in the last row
     float* cost_matrix;  // pairwise mode: [T][T] symmetric, written at (a,b) and (b,a) (may be null)
     int T;               // cycles (pairwise index decode)
     const int32_t* subset;  // pairwise subset (may be null)

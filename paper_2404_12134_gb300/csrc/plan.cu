@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
             pd.nbands = (int32_t)nb;
             pd.out = p;
             h = pair_hbuf_slots(nb, N);
-            if (sp.op == kOpAlign || sp.op == kOpDba)
+            if (sp.op == kOpAlign || sp.op == kOpDba || sp.op == kOpSubdtw)
                 dw = pair_dir_words(sp.group_bands > 0 ? min((int64_t)sp.group_bands, nb) : nb, N, sp.R);
             if (sp.op == kOpSoft)
                 rs = pair_rstore_floats(sp.group_bands > 0 ? min((int64_t)sp.group_bands, nb) : nb, N, sp.R);

@@ -21,6 +21,7 @@ enum Op : int {
     kOpSoft = 4,       // soft-DTW forward (R stored) + backward
     kOpPairwise = 5,   // cost-only DTW between all cycle pairs (medoid init)
     kOpCost = 6,       // cost only
+    kOpSubdtw = 7,     // Sub-DTW: free-start codes, first cheapest end column, backtrack to the start
 };
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -241,6 +241,21 @@ def config_batch(cfg: int, scale: float = 1.0, T: int | None = None) -> Batch:
 PROTO_LEN = {0: None, 1: 25000, 2: 10000, 3: 20000, 4: 110000}
 
 
+def segmentation_stream(K: int, lo: int, hi: int, d: int, ref_len: int, seed: int):
+    """A long series of K back-to-back cycles (pre-gap lengths U{lo..hi}) of one
+    multichannel base, each warped, noisy and with its own gaps removed, and a
+    separately drawn reference cycle of pre-gap length ref_len (an operator's
+    pick: warped, noisy, with gaps).  Returns (X [M, d], Y [N, d], bounds),
+    bounds[k] = (first, last) sample of cycle k in Y (inclusive)."""
+    rng = np.random.default_rng(seed)
+    base = BaseSignal(rng, d, "bumps")
+    X = make_cycle(rng, base, ref_len)
+    cycles = [make_cycle(rng, base, int(rng.integers(lo, hi + 1))) for _ in range(K)]
+    ends = np.cumsum([c.shape[0] for c in cycles])
+    bounds = [(int(e - c.shape[0]), int(e - 1)) for e, c in zip(ends, cycles)]
+    return X, np.ascontiguousarray(np.concatenate(cycles).astype(np.float32)), bounds
+
+
 def clean_prototype(batch: Batch, M: int) -> np.ndarray:
     """The unwarped, noise-free base sampled at M points (fixed scoring prototype)."""
     return batch.base((np.arange(M) + 0.0) / M).astype(np.float32)

@@ -114,3 +114,21 @@ def test_checkpoint_mode_shrinks_workspace(lib):
     assert ckpt < stored / 8
     o.dir_mode = 2
     assert _size(lib, _abi.OP_DBA_ITERATE, 110000, b, o)[0] == _abi.WTS_EINVAL
+
+
+def test_subdtw_workspace_and_validation(lib):
+    b, offs = _batch([1200, 37], d=9)
+    rc, sub = _size(lib, _abi.OP_SUBDTW, 600, b)
+    rc2, align = _size(lib, _abi.OP_DTW_ALIGN, 600, b)
+    assert rc == 0 and rc2 == 0 and sub >= align        # the same codes, plus nothing smaller
+    o = _abi.wts_options()
+    o.rows_per_thread = 8
+    assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == _abi.WTS_EINVAL
+    o.rows_per_thread = 0
+    o.dir_mode = 1
+    assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == _abi.WTS_EINVAL
+    n = ctypes.c_size_t(0)
+    assert lib.wts_segment_workspace_size(16300, 9, None, ctypes.byref(n)) == 0
+    # one window of 2M columns: about M * 2M / 4 bytes of codes
+    assert 16300 * 32600 / 4 <= n.value <= 16300 * 32600 / 4 * 1.2
+    assert lib.wts_segment_workspace_size(0, 9, None, ctypes.byref(n)) == _abi.WTS_EINVAL

@@ -363,6 +363,32 @@ def test_segmentation_of_repeated_copies():
     assert all(b < len(Y) for a, b, c in segs)
 
 
+def pieces_match_cycles(segs, bounds, min_found):
+    """Each piece lies (>= 95 % of its samples) inside one generated cycle and
+    covers >= 90 % of it; pieces come in order, one per cycle; at least
+    min_found cycles are found.  (A cycle may be skipped: the window can hold
+    two cycles and Sub-DTW keeps the cheaper one, leaving the fragment before
+    a* unassigned, as Sec. 3.2 notes.)"""
+    hit = []
+    for a, b, c in segs:
+        best = max(range(len(bounds)), key=lambda k: min(b, bounds[k][1]) - max(a, bounds[k][0]))
+        s0, s1 = bounds[best]
+        ov = min(b, s1) - max(a, s0) + 1
+        assert ov >= 0.95 * (b - a + 1) and ov >= 0.90 * (s1 - s0 + 1), ((a, b), (s0, s1))
+        hit.append(best)
+    assert hit == sorted(set(hit)) and len(hit) >= min_found, hit
+
+
+def test_segmentation_recovers_generated_cycles():
+    """A stream of K warped, noisy, gapped cycles of one base, segmented with a
+    separately drawn reference cycle; the generator's bounds are the ground
+    truth, independent of the oracle."""
+    for d, seed in ((3, 7), (9, 8), (1, 9)):
+        X, Y, bounds = synth.segmentation_stream(6, 550, 650, d, 600, seed)
+        segs = oracle.segment(X, Y, int(0.15 * len(X)), "f32")
+        pieces_match_cycles(segs, bounds, len(bounds) - 1)
+
+
 def _sub_pins_fail(defines) -> bool:
     rng = np.random.default_rng(44)
     try:
