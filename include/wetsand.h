@@ -167,7 +167,8 @@ int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* 
  *   a_star, b_star [T]           out (int32), 0-based inclusive bounds in Y_k
  *   plen [T]                     out, |pi| (may be NULL)
  *   jlo, jhi [T][M]              out (int32), columns of each row of X
- * rows_per_thread must be 0 or 16; dir_mode 1 (checkpointing) is not offered.
+ * rows_per_thread must be 0 (16), 8 or 16; dir_mode 1 (checkpointing) is
+ * not offered.
  * Workspace: wts_workspace_size(WTS_OP_SUBDTW, M, Y, ...).
  */
 int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_options* opt,
@@ -191,8 +192,10 @@ int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_option
  *                                       max_segments are stored and
  *                                       WTS_ENOMEM is returned
  * Each window is one subdtw_align call; the window's bounds are read back
- * before the next (the stream is synchronised once per window).  Workspace:
- * wts_segment_workspace_size.
+ * before the next (the stream is synchronised once per window).  A window is
+ * a single pair, so rows_per_thread = 0 means 8 here (twice the warps of 16,
+ * half the serial chain per step).  Workspace: wts_segment_workspace_size
+ * (with the same options).
  */
 int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, size_t* bytes);
 int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_t d, int64_t alpha,

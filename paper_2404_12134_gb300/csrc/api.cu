@@ -139,10 +139,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->D = D;
     L->R = pick_R(D, opt);
     if (op == kOpSubdtw) {
-        if (opt && opt->rows_per_thread && opt->rows_per_thread != 16)
-            return fail(WTS_EINVAL, "Sub-DTW runs with rows_per_thread = 16 (got %d)", opt->rows_per_thread);
+        if (opt && opt->rows_per_thread && opt->rows_per_thread != 16 && opt->rows_per_thread != 8)
+            return fail(WTS_EINVAL, "Sub-DTW runs with rows_per_thread = 8 or 16 (got %d)", opt->rows_per_thread);
         if (opt && opt->dir_mode == 1) return fail(WTS_EINVAL, "Sub-DTW keeps every code (dir_mode must be 0)");
-        L->R = 16;
+        L->R = (opt && opt->rows_per_thread == 8) ? 8 : 16;
     }
     if (op == kOpSoft) {
         if (D > 8) return fail(WTS_EINVAL, "soft-DTW supports d <= 8 (got %d)", Y->d);
@@ -622,13 +622,23 @@ int segment_layout(int64_t M, int32_t d, const wts_options* opt, SegLayout* S)
     return WTS_OK;
 }
 
+// One window is one pair: the wavefront has only M / (32 R) warps, so the
+// shorter serial chain of 8 rows per lane (twice the warps) is the default.
+wts_options segment_options(const wts_options* opt)
+{
+    wts_options o = opt ? *opt : wts_options{};
+    if (o.rows_per_thread == 0) o.rows_per_thread = 8;
+    return o;
+}
+
 }  // namespace
 
 int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, size_t* bytes)
 {
     if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
     SegLayout S;
-    int rc = segment_layout(M, d, opt, &S);
+    const wts_options o = segment_options(opt);
+    int rc = segment_layout(M, d, &o, &S);
     if (rc) return rc;
     *bytes = S.total;
     return ok();
@@ -644,6 +654,8 @@ int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_
     if (alpha < 0) return fail(WTS_EINVAL, "alpha must be >= 0");
     if (max_segments < 0) return fail(WTS_EINVAL, "max_segments must be >= 0");
     SegLayout S;
+    const wts_options o = segment_options(opt);
+    opt = &o;
     int rc = segment_layout(M, d, opt, &S);
     if (rc) return rc;
     if (!workspace || ((uintptr_t)workspace & 255) != 0) return fail(WTS_EINVAL, "workspace must be 256-byte aligned");

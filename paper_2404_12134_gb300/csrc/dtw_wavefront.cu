@@ -427,7 +427,7 @@ cudaError_t launch_mode(int mode, const DPParams& p, int grid, int block, cudaSt
             dtw_wavefront_kernel<D, R, kModeDirs><<<grid, block, smem, st>>>(p);
             break;
         case kModeSubDirs:
-            if constexpr (R == 16) {
+            if constexpr (R == 16 || R == 8) {
                 cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeSubDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 dtw_wavefront_kernel<D, R, kModeSubDirs><<<grid, block, smem, st>>>(p);
                 break;
@@ -458,7 +458,7 @@ int occ_mode(int mode, int block)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeDirs>, block, smem);
             break;
         case kModeSubDirs:
-            if constexpr (R == 16) {
+            if constexpr (R == 16 || R == 8) {
                 cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeSubDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeSubDirs>, block, smem);
             }

@@ -11,7 +11,7 @@ enum DPMode : int {
     kModePlen = 1,    // r(M,N) and |pi| (cells on the tie-rule path), score = r / |pi|
     kModeDirs = 2,    // r(M,N) and a 2-bit predecessor code per cell
     kModeSubDirs = 3, // Sub-DTW (Sec. 3.2): free start (the row above the matrix is 0), codes,
-                      // and min_j r(M-1, j) with its first column j (R = 16 only)
+                      // and min_j r(M-1, j) with its first column j (R = 8 or 16)
 };
 
 struct DPParams {

@@ -123,6 +123,8 @@ def test_subdtw_workspace_and_validation(lib):
     assert rc == 0 and rc2 == 0 and sub >= align        # the same codes, plus nothing smaller
     o = _abi.wts_options()
     o.rows_per_thread = 8
+    assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == 0
+    o.rows_per_thread = 32
     assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == _abi.WTS_EINVAL
     o.rows_per_thread = 0
     o.dir_mode = 1

@@ -23,10 +23,11 @@ def _pack(cyc):
     return np.ascontiguousarray(np.concatenate(cyc).astype(np.float32)), offs
 
 
-def _check(wts, X, cyc):
+def _check(wts, X, cyc, rows=0):
     data, offs = _pack(cyc)
     gb = wts.Batch.from_numpy(data, offs)
-    cost, a, b, plen, jlo, jhi = (t.cpu().numpy() for t in wts.subdtw_align(torch.from_numpy(X).cuda(), gb))
+    opts = wts.options(rows_per_thread=rows)
+    cost, a, b, plen, jlo, jhi = (t.cpu().numpy() for t in wts.subdtw_align(torch.from_numpy(X).cuda(), gb, opts))
     for k, y in enumerate(cyc):
         r = oracle.subdtw(X, y, "f32")
         assert cost[k] == r["cost"], k
@@ -36,16 +37,17 @@ def _check(wts, X, cyc):
         assert abs(cost[k] - r64["cost"]) <= 1e-5 * max(1.0, r64["cost"]), k
 
 
+@pytest.mark.parametrize("rows", [16, 8])
 @pytest.mark.parametrize("M,lengths,d", [
     (1, [1, 7, 300], 1),
     (37, [1, 2, 40, 95], 3),
-    (513, [600, 1100, 1], 2),          # two bands, the second one row high
-    (1100, [2200, 1733, 900], 9),      # three bands, ragged; windows of 2M and less
+    (513, [600, 1100, 1], 2),          # two bands of 512 (R = 16), the second one row high
+    (1100, [2200, 1733, 900], 9),      # three or five bands, ragged; windows of 2M and less
 ])
-def test_subdtw_bit_exact(wts, M, lengths, d):
+def test_subdtw_bit_exact(wts, M, lengths, d, rows):
     rng = np.random.default_rng(200 + M)
     X = rng.normal(size=(M, d)).astype(np.float32)
-    _check(wts, X, [rng.normal(size=(n, d)).astype(np.float32) for n in lengths])
+    _check(wts, X, [rng.normal(size=(n, d)).astype(np.float32) for n in lengths], rows)
 
 
 def test_subdtw_integer_ties(wts):
@@ -54,7 +56,8 @@ def test_subdtw_integer_ties(wts):
     rng = np.random.default_rng(210)
     for M in (1, 2, 5, 19):
         X = rng.integers(-2, 3, size=(M, 2)).astype(np.float32)
-        _check(wts, X, [rng.integers(-2, 3, size=(n, 2)).astype(np.float32) for n in range(1, 41)])
+        for rows in (16, 8):
+            _check(wts, X, [rng.integers(-2, 3, size=(n, 2)).astype(np.float32) for n in range(1, 41)], rows)
 
 
 def test_subdtw_embedded_copy(wts):
@@ -67,11 +70,11 @@ def test_subdtw_embedded_copy(wts):
     assert float(cost[0]) == 0.0 and (int(a[0]), int(b[0]), int(plen[0])) == (333, 1032, 700)
 
 
-@pytest.mark.parametrize("d,seed", [(3, 7), (9, 8)])
-def test_segment_matches_oracle(wts, d, seed):
+@pytest.mark.parametrize("d,seed,rows", [(3, 7, 16), (9, 8, 16), (9, 8, 8)])
+def test_segment_matches_oracle(wts, d, seed, rows):
     X, Y, bounds = synth.segmentation_stream(6, 550, 650, d, 600, seed)
     alpha = int(0.15 * len(X))
-    got = wts.segment(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), alpha)
+    got = wts.segment(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), alpha, wts.options(rows_per_thread=rows))
     ref = oracle.segment(X, Y, alpha, "f32")
     assert [(a, b) for a, b, c in got] == [(a, b) for a, b, c in ref]
     assert [c for a, b, c in got] == [float(c) for a, b, c in ref]
@@ -98,6 +101,6 @@ def test_subdtw_rejects_unsupported_options(wts):
     X = torch.zeros((10, 1), device="cuda")
     gb = wts.Batch.from_numpy(np.zeros((20, 1), np.float32), np.array([0, 20], np.int64))
     with pytest.raises(Exception):
-        wts.subdtw_align(X, gb, wts.options(rows_per_thread=8))
+        wts.subdtw_align(X, gb, wts.options(rows_per_thread=32))
     with pytest.raises(Exception):
         wts.subdtw_align(X, gb, wts.options(dir_mode=1))
