@@ -79,13 +79,13 @@ def _lib(defines: tuple = ()):
         for p, R, Rp in (("f64", ctypes.c_double, f64p), ("f32", ctypes.c_float, f32p)):
             fn = getattr(lib, f"orc_dtw_{p}")
             fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int,
-                           VP, VP, VP, VP, VP, VP]
+                           VP, VP, VP, VP, VP, VP, ctypes.c_double]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_score_{p}")
-            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP]
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_dba_{p}")
-            fn.argtypes = [Rp, Rp, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP]
+            fn.argtypes = [Rp, Rp, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_softdtw_{p}")
             fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, R, VP, VP, VP, VP]
@@ -117,10 +117,11 @@ def _as2d(x: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(x)
 
 
-def dtw(B, Y, prec: str = "f64", path: bool = True, _defines: tuple = ()):
+def dtw(B, Y, prec: str = "f64", path: bool = True, band: float = 0.0, _defines: tuple = ()):
     """DTW(B, Y) with its optimal path under the tie order diag > up > left.
 
-    Returns dict(cost, plen, jlo, jhi, path_i, path_j); rows index B."""
+    band > 0: Sakoe-Chiba band (Table I), cells with |i N - j M| > floor(band M N)
+    excluded.  Returns dict(cost, plen, jlo, jhi, path_i, path_j); rows index B."""
     B = _as2d(B); Y = _as2d(Y)
     M, d = B.shape; N = Y.shape[0]
     assert Y.shape[1] == d and M >= 1 and N >= 1
@@ -131,9 +132,10 @@ def dtw(B, Y, prec: str = "f64", path: bool = True, _defines: tuple = ()):
     pi = np.zeros(M + N - 1, dtype=np.int32) if path else None
     pj = np.zeros(M + N - 1, dtype=np.int32) if path else None
     rc = getattr(_lib(_defines), f"orc_dtw_{prec}")(B, M, Y, N, d, _ptr(cost), _ptr(plen), _ptr(jlo), _ptr(jhi),
-                                                  _ptr(pi), _ptr(pj))
+                                                  _ptr(pi), _ptr(pj), band)
     if rc:
-        raise RuntimeError(f"oracle dtw failed (rc={rc}: -1 allocation, -2 invalid choice matrix)")
+        raise RuntimeError(f"oracle dtw failed (rc={rc}: -1 allocation, -2 invalid choice matrix, "
+                           f"-3 band narrower than max(M, N))")
     L = int(plen[0])
     out = dict(cost=cost[0], plen=L, jlo=jlo, jhi=jhi)
     if path:
@@ -187,7 +189,7 @@ def segment(X, Y, alpha: int, prec: str = "f32"):
     return out
 
 
-def score(B, data, offsets, prec: str = "f64", _defines: tuple = ()):
+def score(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines: tuple = ()):
     """Similarity score Eq. 8 for each cycle of a packed batch: (score, cost, plen)."""
     B = _as2d(B); data = _as2d(data)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -195,13 +197,13 @@ def score(B, data, offsets, prec: str = "f64", _defines: tuple = ()):
     dt = _dt(prec)
     s = np.zeros(T, dtype=dt); c = np.zeros(T, dtype=dt); L = np.zeros(T, dtype=np.int32)
     rc = getattr(_lib(_defines), f"orc_score_{prec}")(B, B.shape[0], data, offsets, T, B.shape[1],
-                                                    _ptr(s), _ptr(c), _ptr(L))
+                                                    _ptr(s), _ptr(c), _ptr(L), band)
     if rc:
-        raise MemoryError("oracle score allocation failed")
+        raise RuntimeError("oracle score failed (allocation, or a band narrower than max(M, N))")
     return s, c, L
 
 
-def dba_iterate(B, data, offsets, prec: str = "f64", _defines: tuple = ()):
+def dba_iterate(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines: tuple = ()):
     """One DBA iteration: (B_new, counts, cost_before, per-cycle costs)."""
     dt = _dt(prec)
     B = np.ascontiguousarray(np.asarray(B, dtype=dt).reshape(len(B), -1))
@@ -213,9 +215,10 @@ def dba_iterate(B, data, offsets, prec: str = "f64", _defines: tuple = ()):
     cnt = np.zeros(M, dtype=np.int32)
     cb = np.zeros(1, dtype=np.float64)
     ck = np.zeros(T, dtype=dt)
-    rc = getattr(_lib(_defines), f"orc_dba_{prec}")(B, Bo, M, data, offsets, T, d, _ptr(cnt), _ptr(cb), _ptr(ck))
+    rc = getattr(_lib(_defines), f"orc_dba_{prec}")(B, Bo, M, data, offsets, T, d, _ptr(cnt), _ptr(cb), _ptr(ck),
+                                                  band)
     if rc:
-        raise MemoryError("oracle dba allocation failed")
+        raise RuntimeError("oracle dba failed (allocation, or a band narrower than max(M, N))")
     return Bo, cnt, float(cb[0]), ck
 
 

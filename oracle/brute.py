@@ -111,3 +111,21 @@ def subdtw(X, Y):
     opt = [q for c, b, q in cands if c == best and b == b_star]
     chosen = max(opt, key=lambda q: reversed_steps(q) + (DIAG,))
     return best, b_star, chosen
+
+
+def in_band(i: int, j: int, M: int, N: int, band: float) -> bool:
+    """Sakoe-Chiba band membership of 0-based cell (i, j): |i N - j M| <= floor(band M N)."""
+    bound = math.floor(band * M * N)
+    return abs(i * N - j * M) <= bound
+
+
+def dtw_band(B, Y, band: float):
+    """Eq. 1 restricted to the complete paths that stay inside the band:
+    (min cost, the tie-rule path)."""
+    D = cost_matrix(B, Y)
+    M, N = D.shape
+    ps = [p for p in paths(M, N) if all(in_band(i, j, M, N, band) for i, j in p)]
+    costs = [sum(D[i, j] for i, j in p) for p in ps]
+    best = min(costs)
+    chosen = max((p for p, c in zip(ps, costs) if c == best), key=reversed_steps)
+    return best, chosen

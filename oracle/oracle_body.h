@@ -69,8 +69,15 @@ static REAL SFX(local_cost_r)(const REAL* b, const float* y, int d)
  */
 static int SFX(dtw_core)(const REAL* B, int64_t M, const float* Y, int64_t N, int d,
                          REAL* cost, int32_t* plen, int32_t* jlo, int32_t* jhi,
-                         int32_t* pi_i, int32_t* pi_j)
+                         int32_t* pi_i, int32_t* pi_j, double band)
 {
+    /* Sakoe-Chiba band (Table I: a width given as a fraction of the signals'
+     * length; reading for unequal lengths): 0-based cell (i, j) is inside when
+     * |i N - j M| <= floor(band M N), i.e. |i/M - j/N| <= band in normalised
+     * time.  band <= 0: no band.  Outside cells are +inf.  A band narrower
+     * than max(M, N) may hold no path: refused (-3). */
+    const int64_t bound = band > 0 ? (int64_t)floor(band * (double)M * (double)N) : -1;
+    if (band > 0 && bound < (M > N ? M : N)) return -3;
     REAL* prev = (REAL*)malloc((size_t)(N + 1) * sizeof(REAL));
     REAL* cur = (REAL*)malloc((size_t)(N + 1) * sizeof(REAL));
     uint8_t* choice = (uint8_t*)malloc((size_t)M * (size_t)N);
@@ -82,6 +89,18 @@ static int SFX(dtw_core)(const REAL* B, int64_t M, const float* Y, int64_t N, in
         cur[0] = (REAL)INFINITY;
         const REAL* bi = B + (i - 1) * d;
         for (int64_t j = 1; j <= N; ++j) {
+            if (bound >= 0) {
+#ifdef ORACLE_PLANT_BAND_SWAP
+                const int64_t t = (i - 1) * M - (j - 1) * N;
+#else
+                const int64_t t = (i - 1) * N - (j - 1) * M;
+#endif
+                if (t > bound || -t > bound) {
+                    cur[j] = (REAL)INFINITY;
+                    choice[(i - 1) * N + (j - 1)] = 0;
+                    continue;
+                }
+            }
 #ifdef ORACLE_PLANT_DIAG_INDEX
             REAL dg = prev[j], up = prev[j], lf = cur[j - 1];
 #else
@@ -143,12 +162,12 @@ static int SFX(dtw_core)(const REAL* B, int64_t M, const float* Y, int64_t N, in
 /* DTW of one pair with a float prototype (converted exactly to REAL). */
 int SFX(orc_dtw)(const float* B, int64_t M, const float* Y, int64_t N, int d,
                  REAL* cost, int32_t* plen, int32_t* jlo, int32_t* jhi,
-                 int32_t* pi_i, int32_t* pi_j)
+                 int32_t* pi_i, int32_t* pi_j, double band)
 {
     REAL* Br = (REAL*)malloc((size_t)M * d * sizeof(REAL));
     if (!Br) return -1;
     for (int64_t k = 0; k < M * d; ++k) Br[k] = (REAL)B[k];
-    int rc = SFX(dtw_core)(Br, M, Y, N, d, cost, plen, jlo, jhi, pi_i, pi_j);
+    int rc = SFX(dtw_core)(Br, M, Y, N, d, cost, plen, jlo, jhi, pi_i, pi_j, band);
     free(Br);
     return rc;
 }
@@ -159,7 +178,7 @@ int SFX(orc_dtw)(const float* B, int64_t M, const float* Y, int64_t N, int d,
  * Pairs are independent; they are spread over OpenMP threads.
  */
 int SFX(orc_score)(const float* B, int64_t M, const float* Y, const int64_t* offsets, int T, int d,
-                   REAL* score, REAL* cost, int32_t* plen)
+                   REAL* score, REAL* cost, int32_t* plen, double band)
 {
     REAL* Br = (REAL*)malloc((size_t)M * d * sizeof(REAL));
     if (!Br) return -1;
@@ -169,7 +188,7 @@ int SFX(orc_score)(const float* B, int64_t M, const float* Y, const int64_t* off
     for (int k = 0; k < T; ++k) {
         REAL c; int32_t L;
         int64_t N = offsets[k + 1] - offsets[k];
-        bad |= SFX(dtw_core)(Br, M, Y + offsets[k] * d, N, d, &c, &L, NULL, NULL, NULL, NULL);
+        bad |= SFX(dtw_core)(Br, M, Y + offsets[k] * d, N, d, &c, &L, NULL, NULL, NULL, NULL, band) != 0;
         if (cost) cost[k] = c;
         if (plen) plen[k] = L;
         if (score) score[k] = c / (REAL)L;
@@ -190,7 +209,7 @@ int SFX(orc_score)(const float* B, int64_t M, const float* Y, const int64_t* off
  * double and rounded once to REAL.  costs[k] (optional) = DTW(B_in, Y_k).
  */
 int SFX(orc_dba)(const REAL* B_in, REAL* B_out, int64_t M, const float* Y, const int64_t* offsets,
-                 int T, int d, int32_t* counts, double* cost_before, REAL* costs)
+                 int T, int d, int32_t* counts, double* cost_before, REAL* costs, double band)
 {
     int32_t* jlo = (int32_t*)malloc((size_t)T * M * sizeof(int32_t));
     int32_t* jhi = (int32_t*)malloc((size_t)T * M * sizeof(int32_t));
@@ -203,7 +222,7 @@ int SFX(orc_dba)(const REAL* B_in, REAL* B_out, int64_t M, const float* Y, const
     for (int k = 0; k < T; ++k) {
         int64_t N = offsets[k + 1] - offsets[k];
         bad |= SFX(dtw_core)(B_in, M, Y + offsets[k] * d, N, d, &ck[k], NULL,
-                             jlo + (int64_t)k * M, jhi + (int64_t)k * M, NULL, NULL);
+                             jlo + (int64_t)k * M, jhi + (int64_t)k * M, NULL, NULL, band) != 0;
     }
     if (!bad) {
         for (int k = 0; k < T; ++k) {

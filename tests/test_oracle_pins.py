@@ -290,6 +290,72 @@ def test_generator_is_seeded():
     assert a.d == 6 and a.T == 200 and int(a.labels.astype(bool).sum()) == 20
 
 
+# --- Sakoe-Chiba band (Table I) ----------------------------------------------------
+
+def _bands(M, N):
+    """Band widths from the narrowest accepted (floor(w M N) = max(M, N)) up to no restriction."""
+    lo = max(M, N) / (M * N)
+    return [lo * f for f in (1.0, 1.3, 2.0)] + [0.6, 1.0]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_banded_dtw_matches_brute_force(prec):
+    """Integer samples; every band from the narrowest accepted one up: the cost
+    and the tie-rule path over the complete paths that stay in the band."""
+    rng = np.random.default_rng(50)
+    for M in range(1, 7):
+        for N in range(1, 7):
+            B, Y = synth.integer_pair(rng, M, N, 2, -3, 3)
+            for w in _bands(M, N):
+                if math.floor(w * M * N) < max(M, N):
+                    continue
+                best, chosen = brute.dtw_band(B, Y, w)
+                r = oracle.dtw(B, Y, prec, band=w)
+                assert float(r["cost"]) == best, (M, N, w)
+                assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen, (M, N, w)
+
+
+def test_band_limits_and_refusal():
+    """w >= 1 changes nothing; the cost never decreases as the band narrows;
+    M = N with floor(w N^2) = N is the band |i - j| <= 1; a band narrower than
+    max(M, N) is refused."""
+    rng = np.random.default_rng(51)
+    for M, N in ((40, 40), (37, 61), (70, 23)):
+        B, Y = _real_pair(rng, M, N, 2)
+        full = oracle.dtw(B, Y, "f64")
+        assert oracle.dtw(B, Y, "f64", band=1.0)["cost"] == full["cost"]
+        prev = full["cost"]
+        for w in (0.6, 0.3, 0.1, max(M, N) / (M * N)):
+            c = oracle.dtw(B, Y, "f64", band=w)["cost"]
+            assert c >= prev
+            prev = c
+    B, Y = _real_pair(rng, 30, 30, 1)
+    r = oracle.dtw(B, Y, "f64", band=30 / 900)
+    assert all(abs(i - j) <= 1 for i, j in zip(r["path_i"], r["path_j"]))
+    with pytest.raises(RuntimeError):
+        oracle.dtw(B, Y, "f64", band=29 / 900)
+
+
+def test_planted_band_mistake_is_caught():
+    """The band written with the lengths swapped (|i M - j N|) trips the
+    brute-force pin (it differs only when M != N)."""
+    def fails(defines):
+        rng = np.random.default_rng(52)
+        for M, N in ((3, 5), (5, 2), (4, 6)):
+            B, Y = synth.integer_pair(rng, M, N, 1, -3, 3)
+            w = 1.3 * max(M, N) / (M * N)
+            best, chosen = brute.dtw_band(B, Y, w)
+            try:
+                r = oracle.dtw(B, Y, "f64", band=w, _defines=defines)
+            except RuntimeError:
+                return True
+            if float(r["cost"]) != best or list(zip(r["path_i"].tolist(), r["path_j"].tolist())) != chosen:
+                return True
+        return False
+    assert not fails(())
+    assert fails(("ORACLE_PLANT_BAND_SWAP",))
+
+
 # --- Sub-DTW and segmentation (Sec. 3.2) ---------------------------------------
 
 def _path_of(r):
