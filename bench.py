@@ -40,6 +40,11 @@ FP32_LANES_PER_SM = 128
 # (profiles/wavefront_dirs_36x25k_d6.md): 5.8027e9 bytes / 2.2029e10 cells.
 # Traffic grows in proportion to the cells (codes + hand-off rows).
 WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = 5.8027e9 / 2.2029e10
+# DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
+# ncu capture of both kernels on 8 cycles of the soft-DTW workload
+# (profiles/softdtw_fwd_bwd_8x10k_d1.md): (0.0132 + 3.2475 + 3.3412 + 0.0526)e9
+# bytes / 8.0226e8 cells (stored R plus hand-off rows, in proportion to cells).
+SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0132 + 3.2475 + 3.3412 + 0.0526) * 1e9 / 8.0226e8
 
 
 def parse():
@@ -486,6 +491,42 @@ def segment_leg(api, torch, dev, barrier, K: int = 36, cpu_window: bool = True):
     return res
 
 
+def band_cells(M: int, lengths, band: float) -> int:
+    """Cells inside the Sakoe-Chiba band summed over pairs: per row i the
+    columns [ceil((i N - B) / M), floor((i N + B) / M)] clipped to [0, N - 1],
+    B = floor(band M N) (integer arithmetic, the kernels' definition)."""
+    tot = 0
+    i = np.arange(M, dtype=np.int64)
+    for N in lengths:
+        N = int(N)
+        B = M * N if band >= 1 else int(np.floor(band * float(M) * float(N)))
+        lo = np.maximum(0, -((B - i * N) // M))          # ceil((iN - B) / M)
+        hi = np.minimum(N - 1, (i * N + B) // M)
+        tot += int(np.maximum(hi - lo + 1, 0).sum())
+    return tot
+
+
+def banded_dba_leg(api, torch, dev, barrier, gb, b, B0, band: float = 0.6, iters: int = 3):
+    """One DBA iteration with Table I's Sakoe-Chiba band (0.6) on the benchmark
+    batch: time, cells inside the band, and GCUPS over those cells."""
+    opt = api.options(band=band)
+    ws = api.Workspace(dev)
+    B = B0.clone()
+    api.dba_iterate(B, gb, opt, ws=ws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        api.dba_iterate(B, gb, opt, ws=ws)
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1) / iters
+    cells = band_cells(int(B0.shape[0]), b.lengths, band)
+    full = int(B0.shape[0]) * int(b.lengths.sum())
+    return {"band": band, "cells_in_band": cells, "fraction_of_matrix": cells / full, "ms_per_dba_iter": ms,
+            "gcups_in_band": cells / (ms * 1e-3) / 1e9, "device_status": api.read_status(ws.buf)}
+
+
 def table_leg(api, torch, dev, barrier):
     """Entries of the results table not covered by the other legs: the small
     DBA workload end to end (medoid init, 10 DBA iterations, scores), the
@@ -760,6 +801,7 @@ def run_gpu(args):
         out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
         out["barycenters"] = bary_leg(api, torch, dev, barrier)
         out["segmentation"] = segment_leg(api, torch, dev, barrier)
+        out["banded_dba"] = banded_dba_leg(api, torch, dev, barrier, gb, b, B0)
         out["measured_peaks_probe"] = {k: api.peak_probe(i) / 1e12 for i, k in
                                        enumerate(("fp32_fma_tops", "fp32_minmax_tops", "mufu_ex2_tops",
                                                   "mufu_lg2_tops", "fp32x2_fma_tops", "fp32_min3_tops"))}
@@ -776,7 +818,10 @@ def run_gpu(args):
                               "frac": t_mufu / t, "traffic": None}
         else:
             sd["roofline"] = {"bound": "hbm", "achieved": cells_s * 8 / t / 1e9, "peak": hbm_peak_gbs(),
-                              "unit": "GB/s", "frac": t_hbm / t, "traffic": None}
+                              "unit": "GB/s", "frac": t_hbm / t,
+                              "traffic": SOFT_FWD_BWD_DRAM_BYTES_PER_CELL * cells_s,
+                              "traffic_note": "bytes per forward + backward, ncu dram__bytes_read+write on 8 cycles "
+                                              "scaled by cells"}
         sd["hbm_lower_bound_ms"] = t_hbm * 1e3
         sd["mufu_lower_bound_ms"] = t_mufu * 1e3
 

@@ -87,7 +87,13 @@ typedef struct wts_options {
     int32_t fault_skip_handoff;    /* fault injection for tests: 1 = producers skip their hand-off rows, so
                                       consumers wait until spin_limit and the call ends with WTS_ETIMEOUT in
                                       the workspace status; never set it otherwise */
-    int32_t reserved[8];
+    double band;                   /* Sakoe-Chiba band (Table I: a width as a fraction of the signals' length):
+                                      0-based cell (i, j) of an M x N pair is kept when
+                                      |i N - j M| <= floor(band M N) (|i/M - j/N| <= band); cells outside are
+                                      +inf.  0 = no band.  A band narrower than max(M, N) for some pair (it may
+                                      hold no complete path) is WTS_EINVAL.  DTW operations only (anomaly_score,
+                                      dtw_align, dba_iterate). */
+    int32_t reserved[6];
 } wts_options;
 
 /* Library version (major * 100 + minor). */

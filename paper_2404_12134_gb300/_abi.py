@@ -47,7 +47,8 @@ class wts_options(ctypes.Structure):
         ("ckpt_bands", ctypes.c_int32),
         ("spin_limit", ctypes.c_int32),
         ("fault_skip_handoff", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("band", ctypes.c_double),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 

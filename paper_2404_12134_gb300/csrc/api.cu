@@ -117,6 +117,7 @@ int check_opt(const wts_options* opt, int D)
     if (opt->dir_mode < 0 || opt->dir_mode > 1) return fail(WTS_EINVAL, "dir_mode must be 0 or 1");
     if (opt->ckpt_bands < 0) return fail(WTS_EINVAL, "ckpt_bands must be >= 0");
     if (opt->spin_limit < 0) return fail(WTS_EINVAL, "spin_limit must be >= 0");
+    if (!(opt->band >= 0.0) || opt->band > 1e6) return fail(WTS_EINVAL, "band must be a finite value >= 0");
     return WTS_OK;
 }
 
@@ -148,6 +149,12 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         if (D > 8) return fail(WTS_EINVAL, "soft-DTW supports d <= 8 (got %d)", Y->d);
         L->R = soft_rows(D);          // fixed by the channel count (registers)
     }
+    if (opt && opt->band > 0) {
+        if (opt->rows_per_thread && opt->rows_per_thread != 16)
+            return fail(WTS_EINVAL, "with a band, rows_per_thread must be 0 or 16 (got %d)", opt->rows_per_thread);
+        L->R = 16;
+        L->banded = 1;
+    }
     L->BR = 32 * L->R;
     L->M = M;
     const int64_t* o = Y->offsets_host;
@@ -163,6 +170,14 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         } else {
             Mp = M;
             Np = o[p + 1] - o[p];
+        }
+        if (opt && opt->band > 0) {
+            if (op != kOpScore && op != kOpAlign && op != kOpDba)
+                return fail(WTS_EINVAL, "the band applies to anomaly_score, dtw_align and dba_iterate only");
+            const int64_t bb = band_bound_of(opt->band, Mp, Np);
+            if (bb < (Mp > Np ? Mp : Np))
+                return fail(WTS_EINVAL, "band %g too narrow for pair %d (%lld x %lld): floor(band M N) = %lld < "
+                            "max(M, N)", opt->band, p, (long long)Mp, (long long)Np, (long long)bb);
         }
         const int64_t nb = cdiv(Mp, L->BR);
         items += nb;
@@ -263,6 +278,7 @@ int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const
     sp.prefix = reinterpret_cast<int32_t*>(ws + L.off_prefix);
     sp.sort = (opt && opt->keep_batch_order) ? 0 : 1;
     sp.group_bands = L.group_bands;
+    sp.band = opt ? opt->band : 0.0;
     {
         Prof pr("setup", st);
         launch_setup(sp, st);
@@ -280,7 +296,7 @@ int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* 
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    int occ = dtw_wavefront_max_blocks_per_sm(mode, L.D, L.R, *block);
+    int occ = dtw_wavefront_max_blocks_per_sm(mode, L.D, L.R, *block, L.banded);
     if (occ < 1) return fail(WTS_ECUDA, "no resident block for D=%d R=%d block=%d", L.D, L.R, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;
@@ -310,6 +326,7 @@ DPParams base_params(const Layout& L, char* ws, const wts_options* opt = nullptr
     p.hbuf = ws + L.off_hbuf;
     p.dirs = L.off_dirs ? reinterpret_cast<uint32_t*>(ws + L.off_dirs) : nullptr;
     p.T = L.T;
+    p.banded = L.banded;
     return p;
 }
 

@@ -88,6 +88,11 @@ __device__ __forceinline__ uint32_t ne_mask(float a, float b)
 }
 
 constexpr int kRing = 128;   // columns of cycle samples staged per warp
+constexpr int kSlot = 4;     // u64 words after a warp's ring: its band's columns and the band
+
+// floor(a / b) and ceil(a / b) for b > 0 and any sign of a
+__device__ __forceinline__ int64_t floor_div64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return -floor_div64(-a, b); }
 
 // c[k] for a k known only at run time, by a binary tree of selects on the bits
 // of k (R - 1 selects, no local memory)
@@ -106,7 +111,7 @@ __device__ __forceinline__ float pick_row(const float (&c)[R], int k)
     return v[0];
 }
 
-template <int D, int R, int MODE>
+template <int D, int R, int MODE, bool BANDED>
 struct Band {
     static constexpr int BR = 32 * R;
     static constexpr int W = R / 16;        // code words per lane per step (0: half a word)
@@ -153,7 +158,7 @@ struct Band {
     // dl holds the local costs of column j on entry and those of column j+1 on
     // exit: the next column's costs are computed between the links of this
     // column's min-plus chain, which is serial down the rows.
-    template <bool FULLCHUNK>
+    template <bool FULLCHUNK, bool MASK = false>
     __device__ __forceinline__ void step(const u64* ring, int s, int src, int lane, int N, bool top,
                                          void* hcur, uint32_t* dout)
     {
@@ -179,14 +184,35 @@ struct Band {
         uint32_t word[W > 0 ? W : 1];
 #pragma unroll
         for (int w = 0; w < (W > 0 ? W : 1); ++w) word[w] = 0u;
-        if (FULLCHUNK || (j >= 0 && j < N)) {
+        // partial chunks with a band read the band's columns (and the band)
+        // from the warp's slot after the sample ring:
+        // [jlo | jhi << 32, row0 | M << 32, bnd]
+        const u64* slot = ring + D * kRing;
+        bool valid = true;
+        int klo = 0, khi = R - 1;
+        if (!FULLCHUNK && !BANDED) valid = j >= 0 && j < N;
+        if (!FULLCHUNK && BANDED) {
+            const u64 cols = slot[0];
+            valid = j >= (int)(uint32_t)cols && j <= (int)(cols >> 32);
+            if (MASK) {
+                // rows k in [klo, khi] lie in the band at column j
+                const u64 im = slot[1];
+                const int64_t bnd = (int64_t)slot[2];
+                const int i0 = (int)(uint32_t)im + lane * R;
+                const int64_t jm = (int64_t)j * (int64_t)(im >> 32);
+                klo = (int)max((int64_t)-1, ceil_div64(jm - bnd, N) - i0);
+                khi = (int)min((int64_t)R, floor_div64(jm + bnd, N) - i0);
+            }
+        }
+        if (FULLCHUNK || valid) {
             float dg = dg_in, up = up_in;
             int cdg = dgc_in, cup = upc_in;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const float lf = col[k];
                 const float m = min3f(dg, up, lf);
-                const float r = __fadd_rn(dl[k], m);
+                float r = __fadd_rn(dl[k], m);
+                if (MASK && (k < klo || k > khi)) r = INF;     // outside the band
                 if (CODES) {
                     word[k >> 5] |= ne_mask(dg, m) & (1u << (k & 31));
                     word[(R + k) >> 5] |= ne_mask(up, m) & (1u << ((R + k) & 31));
@@ -232,10 +258,10 @@ struct Band {
     }
 };
 
-template <int D, int R, int MODE>
+template <int D, int R, int MODE, bool BANDED>
 __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, int band, int lane, u64* ring)
 {
-    using BandT = Band<D, R, MODE>;
+    using BandT = Band<D, R, MODE, BANDED>;
     constexpr int BR = BandT::BR;
     constexpr int W = BandT::W;
     const int M = pd.M, N = pd.N, d = p.d;
@@ -267,6 +293,35 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
     st.best = INF;
     st.bestj = 0;
 
+    // Sakoe-Chiba band: row i keeps columns [lo(i), hi(i)] with
+    // lo(i) = ceil((i N - bnd) / M), hi(i) = floor((i N + bnd) / M), both
+    // nondecreasing in i.  The band's columns run from lo(first row) to
+    // hi(last row); the row above is +inf outside [lo, hi] of that row; a lane
+    // needs no masking where all its rows are in: [lo(last row), hi(first row)].
+    const int64_t bnd = BANDED ? pd.band_bound : -1;
+    int jlo_b = 0, jhi_b = N - 1, jtop_lo = 0, jtop_hi = N - 1, full_lo = 0, full_hi = N - 1;
+    if (BANDED) {
+        auto lo_of = [&](int64_t i) { return (int)max((int64_t)0, ceil_div64(i * N - bnd, M)); };
+        auto hi_of = [&](int64_t i) { return (int)min((int64_t)N - 1, floor_div64(i * N + bnd, M)); };
+        const int64_t r0 = (int64_t)band * BR, r1 = min(r0 + BR, (int64_t)M) - 1;
+        jlo_b = lo_of(r0);
+        jhi_b = hi_of(r1);
+        if (!top) { jtop_lo = lo_of(r0 - 1); jtop_hi = hi_of(r0 - 1); }
+        if (i0 < M) { full_lo = lo_of(min(i0 + R - 1, M - 1)); full_hi = hi_of(i0); }
+    }
+    if (BANDED) {
+        u64* slot = ring + D * kRing;
+        __syncwarp();
+        if (lane == 0) {
+            slot[0] = (u64)(uint32_t)jlo_b | ((u64)(uint32_t)jhi_b << 32);
+            slot[1] = (u64)(uint32_t)(band * BR) | ((u64)(uint32_t)M << 32);
+            slot[2] = (u64)bnd;
+        }
+        __syncwarp();
+    }
+    const int s_begin = jlo_b & ~31;        // chunks of 32 steps from a multiple of 32
+    const int s_end = jhi_b + 32;           // one past the last step (column jhi_b in lane 31)
+
     // hand-off rows: slot size 4 bytes (r), or 8 bytes ({r, cells}) with |pi|
     constexpr int SLOT = MODE == kModePlen ? 8 : 4;
     char* hb = static_cast<char*>(p.hbuf);
@@ -296,52 +351,61 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
         return (u64)__float_as_uint(__ldcv(reinterpret_cast<const float*>(hprev) + jj));
     };
     __syncwarp();
-    load_y(lane);
-    put_y(lane);
-    load_y(lane + 32);
-    put_y(lane + 32);
-    load_y(lane + 64);
-    if (!top) tnext = load_t(lane);
+    load_y(s_begin + lane);
+    put_y(s_begin + lane);
+    load_y(s_begin + lane + 32);
+    put_y(s_begin + lane + 32);
+    load_y(s_begin + lane + 64);
+    if (!top) tnext = load_t(s_begin + lane);
     __syncwarp();
     {
-        // local costs of the lane's first column (j = -lane: only lane 0's is used)
+        // local costs of the lane's first column (j = s_begin - lane)
         u64 yy[D];
-        st.load_samples(ring, -lane, yy);
+        st.load_samples(ring, s_begin - lane, yy);
 #pragma unroll
         for (int q = 0; q < BandT::Q; ++q) st.cost_pair(yy, q);
     }
 
-    const int steps = N + 31;
-    for (int s0 = 0; s0 < steps; s0 += 32) {
-        if (s0 < N) {
+    for (int s0 = s_begin; s0 < s_end; s0 += 32) {
+        if (s0 <= jhi_b) {
             const int jj = s0 + lane;
-            if (s0 > 0) {
+            if (s0 > s_begin) {
                 __syncwarp();
                 put_y(jj + 32);
                 load_y(jj + 64);
                 __syncwarp();
             }
             if (!top) {
+                // only the row above's columns inside the band are written (and waited for)
+                const bool need = jj >= jtop_lo && jj <= jtop_hi;
                 u64 t = tnext;
-                const bool ok = wait_filled(jj < N && is_nan_bits((uint32_t)t),
+                const bool ok = wait_filled(need && is_nan_bits((uint32_t)t),
                                             [&]() { t = load_t(jj); return is_nan_bits((uint32_t)t); }, p.hdr, 1,
                                             p.spin_limit);
                 if (!ok) return;
-                st.topv = jj < N ? __uint_as_float((uint32_t)t) : INF;
+                st.topv = need ? __uint_as_float((uint32_t)t) : INF;
                 if (MODE == kModePlen) st.topc = (int)(t >> 32);
                 tnext = load_t(jj + 32);
             }
         }
-        if (s0 >= 31 && s0 + 32 <= N) {
+        // every lane in the band's columns and inside the band all chunk long
+        const bool full = BANDED ? (s0 - 31 >= jlo_b && s0 + 31 <= jhi_b &&
+                                    __all_sync(FULL, s0 - lane >= full_lo && s0 + 31 - lane <= full_hi))
+                                 : (s0 >= 31 && s0 + 32 <= N);
+        if (full) {
 #pragma unroll 2
             for (int u = 0; u < 32; ++u) st.template step<true>(ring, s0 + u, u, lane, N, top, hcur, dout);
         } else {
-            const int n = min(32, steps - s0);
-            for (int u = 0; u < n; ++u) st.template step<false>(ring, s0 + u, u, lane, N, top, hcur, dout);
+            const int n = min(32, s_end - s0);
+            if (BANDED) {
+                for (int u = 0; u < n; ++u) st.template step<false, true>(ring, s0 + u, u, lane, N, top, hcur, dout);
+            } else {
+                for (int u = 0; u < n; ++u) st.template step<false>(ring, s0 + u, u, lane, N, top, hcur, dout);
+            }
         }
     }
 
-    if (BandT::CODES && W == 0 && (steps & 1)) __stcs(dout + (int64_t)(steps >> 1) * 32 + lane, st.half);
+    if (BandT::CODES && W == 0 && (s_end & 1)) __stcs(dout + (int64_t)(s_end >> 1) * 32 + lane, st.half);
 
     if (MODE == kModeSubDirs) {
         if (last && lane == (M - 1 - band * BR) / R) {
@@ -381,12 +445,12 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
 template <int D, int R>
 constexpr int min_blocks() { return R == 8 ? (D <= 6 ? 4 : (D <= 8 ? 3 : 2)) : ((R == 16 && D <= 4) ? 3 : 2); }
 
-template <int D, int R, int MODE>
+template <int D, int R, int MODE, bool BANDED>
 __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(DPParams p)
 {
     extern __shared__ u64 ring_all[];
     const int lane = threadIdx.x & 31;
-    u64* ring = ring_all + (threadIdx.x >> 5) * D * kRing;
+    u64* ring = ring_all + (threadIdx.x >> 5) * (D * kRing + kSlot);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&p.hdr->item_counter, 1);
@@ -394,78 +458,104 @@ __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(
         if (item >= p.n_items) break;
         if (ld_volatile(&p.hdr->abort)) break;
         int q, band;
-        if (p.recompute) {
+        if (p.recompute && BANDED) {
+            q = item % p.P;
+            band = p.band_lo + item / p.P;
+        } else if (p.recompute) {
             q = item / p.band_cnt;
             band = p.band_lo + item % p.band_cnt;
+        } else if (BANDED) {
+            // band-major: under a band, row band b of a pair starts only once
+            // the band above has covered the diagonal drift of b's first
+            // column, so a pair has few bands ready at a time; taking every
+            // pair's band b before any band b + 1 keeps warps on ready work.
+            // Band b - 1 of a pair is always earlier in the list (no deadlock).
+            // Every pair has the same number of bands (one prototype).
+            q = item % p.P;
+            band = item / p.P;
         } else {
             q = find_slot(p.prefix, p.P, item);
             band = item - p.prefix[q];
         }
         const PairDesc pd = p.pairs[p.order[q]];
-        run_band<D, R, MODE>(p, pd, band, lane, ring);
+        run_band<D, R, MODE, BANDED>(p, pd, band, lane, ring);
     }
 }
 
 template <int D>
-constexpr size_t ring_bytes(int block) { return (size_t)(block / 32) * D * kRing * sizeof(u64); }
+constexpr size_t ring_bytes(int block) { return (size_t)(block / 32) * (D * kRing + kSlot) * sizeof(u64); }
 
-template <int D, int R>
-cudaError_t launch_mode(int mode, const DPParams& p, int grid, int block, cudaStream_t st)
+template <int D, int R, int MODE, bool BANDED>
+cudaError_t launch_one(const DPParams& p, int grid, int block, cudaStream_t st)
 {
     const size_t smem = ring_bytes<D>(block);
-    switch (mode) {
-        case kModeCost:
-            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeCost>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            dtw_wavefront_kernel<D, R, kModeCost><<<grid, block, smem, st>>>(p);
-            break;
-        case kModePlen:
-            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModePlen>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            dtw_wavefront_kernel<D, R, kModePlen><<<grid, block, smem, st>>>(p);
-            break;
-        case kModeDirs:
-            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            dtw_wavefront_kernel<D, R, kModeDirs><<<grid, block, smem, st>>>(p);
-            break;
-        case kModeSubDirs:
-            if constexpr (R == 16 || R == 8) {
-                cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeSubDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                dtw_wavefront_kernel<D, R, kModeSubDirs><<<grid, block, smem, st>>>(p);
-                break;
-            } else {
-                return cudaErrorInvalidValue;
-            }
-        default: return cudaErrorInvalidValue;
-    }
+    cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, MODE, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dtw_wavefront_kernel<D, R, MODE, BANDED><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int D, int R>
-int occ_mode(int mode, int block)
+template <int D, int R, int MODE, bool BANDED>
+int occ_one(int block)
 {
     int n = 0;
     const size_t smem = ring_bytes<D>(block);
-    switch (mode) {
-        case kModeCost:
-            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeCost>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeCost>, block, smem);
-            break;
-        case kModePlen:
-            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModePlen>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModePlen>, block, smem);
-            break;
-        case kModeDirs:
-            cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeDirs>, block, smem);
-            break;
-        case kModeSubDirs:
-            if constexpr (R == 16 || R == 8) {
-                cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, kModeSubDirs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, kModeSubDirs>, block, smem);
+    cudaFuncSetAttribute(dtw_wavefront_kernel<D, R, MODE, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dtw_wavefront_kernel<D, R, MODE, BANDED>, block, smem);
+    return n;
+}
+
+// Instances: every (D, R) for the three DTW modes; Sub-DTW for R = 8 and 16;
+// the banded DTW modes for R = 16.
+template <int D, int R>
+cudaError_t launch_mode(int mode, const DPParams& p, int grid, int block, cudaStream_t st)
+{
+    if (p.banded) {
+        if constexpr (R == 16) {
+            switch (mode) {
+                case kModeCost: return launch_one<D, R, kModeCost, true>(p, grid, block, st);
+                case kModePlen: return launch_one<D, R, kModePlen, true>(p, grid, block, st);
+                case kModeDirs: return launch_one<D, R, kModeDirs, true>(p, grid, block, st);
+                default: break;
             }
+        }
+        return cudaErrorInvalidValue;
+    }
+    switch (mode) {
+        case kModeCost: return launch_one<D, R, kModeCost, false>(p, grid, block, st);
+        case kModePlen: return launch_one<D, R, kModePlen, false>(p, grid, block, st);
+        case kModeDirs: return launch_one<D, R, kModeDirs, false>(p, grid, block, st);
+        case kModeSubDirs:
+            if constexpr (R == 16 || R == 8) return launch_one<D, R, kModeSubDirs, false>(p, grid, block, st);
             break;
         default: break;
     }
-    return n;
+    return cudaErrorInvalidValue;
+}
+
+template <int D, int R>
+int occ_mode(int mode, int banded, int block)
+{
+    if (banded) {
+        if constexpr (R == 16) {
+            switch (mode) {
+                case kModeCost: return occ_one<D, R, kModeCost, true>(block);
+                case kModePlen: return occ_one<D, R, kModePlen, true>(block);
+                case kModeDirs: return occ_one<D, R, kModeDirs, true>(block);
+                default: break;
+            }
+        }
+        return 0;
+    }
+    switch (mode) {
+        case kModeCost: return occ_one<D, R, kModeCost, false>(block);
+        case kModePlen: return occ_one<D, R, kModePlen, false>(block);
+        case kModeDirs: return occ_one<D, R, kModeDirs, false>(block);
+        case kModeSubDirs:
+            if constexpr (R == 16 || R == 8) return occ_one<D, R, kModeSubDirs, false>(block);
+            break;
+        default: break;
+    }
+    return 0;
 }
 
 }  // namespace
@@ -510,9 +600,9 @@ cudaError_t launch_dtw_wavefront(int mode, int D, int R, const DPParams& p, int 
     return cudaErrorInvalidValue;
 }
 
-int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block)
+int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block, int banded)
 {
-    WTS_DISPATCH_DR(occ_mode, mode, block)
+    WTS_DISPATCH_DR(occ_mode, mode, banded, block)
     return 0;
 }
 

@@ -38,10 +38,12 @@ struct DPParams {
     int band_lo, band_cnt;
     long long spin_limit;    // polls before a wait gives up
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
+    int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); R = 16 only;
+                             // items then run band-major (every pair's band 0, then band 1, ...)
 };
 
 // Launch the persistent wavefront for D (padded channels) and R (rows/lane).
 cudaError_t launch_dtw_wavefront(int mode, int D, int R, const DPParams& p, int grid, int block, cudaStream_t st);
-int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block);
+int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block, int banded = 0);
 
 }  // namespace wts

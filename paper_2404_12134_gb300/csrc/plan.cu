@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
             pd.N = (int32_t)N;
             pd.nbands = (int32_t)nb;
             pd.out = p;
+            pd.band_bound = band_bound_of(sp.band, M, N);
             h = pair_hbuf_slots(nb, N);
             if (sp.op == kOpAlign || sp.op == kOpDba || sp.op == kOpSubdtw)
                 dw = pair_dir_words(sp.group_bands > 0 ? min((int64_t)sp.group_bands, nb) : nb, N, sp.R);

@@ -7,6 +7,7 @@
 // captured in a CUDA graph).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -51,6 +52,8 @@ struct Layout {
     size_t off_hdr = 0, off_pairs = 0, off_order = 0, off_prefix = 0;
     size_t off_hbuf = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0, off_btstate = 0;
     int group_bands = 0;  // checkpoint mode: bands whose codes are recomputed at a time (0 = codes stored)
+    int banded = 0;       // a Sakoe-Chiba band applies (the banded kernels run with R = 16)
+
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
     size_t total = 0;
 };
@@ -68,7 +71,16 @@ struct SetupParams {
     int32_t* prefix;           // [P+1] first item of the q-th pair in order
     int sort;                  // 1: order longest-first, 0: identity
     int group_bands;           // > 0: directions for only this many bands per pair (checkpoint mode)
+    double band;               // Sakoe-Chiba width (0 = none): band_bound = floor(band * M * N)
 };
+
+// floor(band * M * N) in double, as the host validation and the oracle take it
+__host__ __device__ inline int64_t band_bound_of(double band, int64_t M, int64_t N)
+{
+    if (!(band > 0)) return -1;
+    if (band >= 1) return M * N;     // every cell: |i N - j M| < M N
+    return (int64_t)floor(band * (double)M * (double)N);
+}
 
 void launch_setup(const SetupParams& sp, cudaStream_t st);
 

@@ -34,6 +34,7 @@ struct PairDesc {
     int64_t dir_off;     // first direction word of this pair
     int64_t hbuf_off;    // first slot of this pair's hand-off rows ((nbands-1) * N slots)
     int64_t aux_off;     // first element of per-pair auxiliary storage (R store)
+    int64_t band_bound;  // Sakoe-Chiba band: cell (i, j) kept when |i N - j M| <= band_bound; -1 = no band
 };
 
 // Header at the start of every workspace.

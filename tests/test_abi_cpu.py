@@ -134,3 +134,27 @@ def test_subdtw_workspace_and_validation(lib):
     # one window of 2M columns: about M * 2M / 4 bytes of codes
     assert 16300 * 32600 / 4 <= n.value <= 16300 * 32600 / 4 * 1.2
     assert lib.wts_segment_workspace_size(0, 9, None, ctypes.byref(n)) == _abi.WTS_EINVAL
+
+
+def test_band_option_layout_and_validation(lib):
+    """wts_options keeps its 64-byte layout with the double band field; a band
+    narrower than max(M, N) for some pair, a band with 8 rows per lane, and a
+    band on a non-DTW operation are refused on the host."""
+    assert ctypes.sizeof(_abi.wts_options) == 64
+    assert _abi.wts_options.band.offset == 32
+    b, offs = _batch([1200, 800], d=3)
+    o = _abi.wts_options()
+    o.band = 0.6
+    for op in (_abi.OP_ANOMALY_SCORE, _abi.OP_DTW_ALIGN, _abi.OP_DBA_ITERATE):
+        assert _size(lib, op, 1000, b, o)[0] == 0
+    o.band = 1199 / (1000 * 1200)             # floor(w M N) < max(M, N) for the first pair
+    assert _size(lib, _abi.OP_DTW_ALIGN, 1000, b, o)[0] == _abi.WTS_EINVAL
+    assert b"too narrow" in lib.wts_last_error()
+    o.band = 0.6
+    o.rows_per_thread = 8
+    assert _size(lib, _abi.OP_DTW_ALIGN, 1000, b, o)[0] == _abi.WTS_EINVAL
+    o.rows_per_thread = 0
+    for op in (_abi.OP_SOFTDTW, _abi.OP_SUBDTW):
+        assert _size(lib, op, 1000, b, o)[0] == _abi.WTS_EINVAL
+    o.band = -1.0
+    assert _size(lib, _abi.OP_DTW_ALIGN, 1000, b, o)[0] == _abi.WTS_EINVAL
