@@ -209,6 +209,26 @@ int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_
                 int32_t max_segments, int64_t* seg_start, int64_t* seg_end, float* seg_cost, int32_t* n_segments);
 
 /*
+ * wts_thresholds - the two detection thresholds of Sec. 5.3 on a set of
+ * d_score values (host array scores[T], all finite; no CUDA call):
+ *   two_sigma = mean + 2 std   (std with divisor T)
+ *   boxplot   = q3 + 1.5 |q3 - q1|, quartile q taken at position q (T - 1) of
+ *               the sorted scores, linearly between the two neighbouring values
+ * A cycle is flagged abnormal when its score is above the threshold.  Either
+ * output may be NULL (not both).
+ */
+int wts_thresholds(const float* scores, int32_t T, double* two_sigma, double* boxplot);
+
+/*
+ * wts_f2 - confusion counts and the F2 score (Sec. 5.3) of the flags
+ * "score > threshold" against labels[T] (host, nonzero = abnormal):
+ *   F2 = 5 TP / (5 TP + 4 FN + FP), 0 when TP + FN + FP = 0.
+ * tp, fp, fn may be NULL.
+ */
+int wts_f2(const float* scores, const int8_t* labels, int32_t T, double threshold,
+           int32_t* tp, int32_t* fp, int32_t* fn, double* f2);
+
+/*
  * dba_iterate - one iteration of DTW Barycenter Averaging (Petitjean et al.
  * 2011; the paper cites it in Sec. 2 and compares with it in Table II and
  * Fig. 6 without printing a formula):

@@ -19,7 +19,9 @@ What it computes (paper sections; the C body cites the equations):
 * ``medoid``, ``resample``, ``euclid_mean`` - initial barycenters (Table I:
                      Euclidean-mean init; medoid for DBA);
 * ``subdtw``, ``segment`` - Sub-DTW and the sliding-window segmentation into
-                     cycles (Sec. 3.2).
+                     cycles (Sec. 3.2);
+* ``thresholds``, ``f2`` - the 2-sigma and boxplot detection thresholds and
+                     the F2 score (Sec. 5.3).
 
 ``prec='f64'`` is the reference precision.  ``prec='f32'`` mirrors the CUDA
 kernels' operation order in float so that the warping path, an integer
@@ -316,3 +318,22 @@ def euclid_mean(data, offsets, M: int) -> np.ndarray:
     for k in range(T):
         acc += resample(data[offsets[k]:offsets[k + 1]], M).astype(np.float64)
     return (acc / T).astype(np.float32)
+
+
+# --- detection thresholds (Sec. 5.3) ------------------------------------------
+
+def thresholds(scores):
+    """(2-sigma threshold, boxplot threshold) of Sec. 5.3: mean + 2 std (divisor
+    T) and q3 + 1.5 |q3 - q1| with numpy's linear-interpolation quartiles."""
+    x = np.asarray(scores, dtype=np.float64)
+    q1, q3 = np.percentile(x, [25, 75])
+    return float(x.mean() + 2.0 * x.std()), float(q3 + 1.5 * abs(q3 - q1))
+
+
+def f2(scores, labels, threshold):
+    """Confusion counts of score > threshold against labels and F2 = 5 TP / (5 TP + 4 FN + FP)."""
+    flag = np.asarray(scores, dtype=np.float64) > threshold
+    truth = np.asarray(labels) != 0
+    tp = int((flag & truth).sum()); fp = int((flag & ~truth).sum()); fn = int((~flag & truth).sum())
+    den = 5 * tp + 4 * fn + fp
+    return {"tp": tp, "fp": fp, "fn": fn, "f2": 5 * tp / den if den else 0.0}

@@ -23,7 +23,7 @@ EXPORTS = (
     "anomaly_score", "dtw_align", "dba_iterate", "wts_pairwise_dtw", "wts_medoid",
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
     "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune", "wts_compact_nan",
-    "subdtw_align", "wts_segment_workspace_size", "wts_segment",
+    "subdtw_align", "wts_segment_workspace_size", "wts_segment", "wts_thresholds", "wts_f2",
 )
 
 
@@ -81,6 +81,9 @@ _SIGS = {
     "wts_segment": ([VP, I64, VP, I64, I32, I64, PO, VP, SZ, VP, I32, VP, VP, VP, ctypes.POINTER(I32)],
                     ctypes.c_int),
     "wts_pairwise_dtw": ([PB, PO, VP, SZ, VP, VP], ctypes.c_int),
+    "wts_thresholds": ([VP, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "wts_f2": ([VP, VP, I32, ctypes.c_double, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "wts_medoid": ([VP, I32, VP, VP, VP], ctypes.c_int),
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),

@@ -250,6 +250,28 @@ def segment(X: torch.Tensor, Y: torch.Tensor, alpha: int | None = None, opts=Non
     return [(int(start[k]), int(end[k]), float(cost[k])) for k in range(n.value)]
 
 
+def thresholds(scores) -> tuple[float, float]:
+    """The 2-sigma and boxplot detection thresholds of Sec. 5.3 on the scores
+    (host computation in the library): (mean + 2 std, q3 + 1.5 |q3 - q1|)."""
+    sc = np.ascontiguousarray(scores.detach().cpu().numpy() if isinstance(scores, torch.Tensor) else scores,
+                              dtype=np.float32)
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    check(_abi.load().wts_thresholds(sc.ctypes.data, len(sc), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def f2_score(scores, labels, threshold: float) -> dict:
+    """Confusion counts and F2 of "score > threshold" against labels (Sec. 5.3)."""
+    sc = np.ascontiguousarray(scores.detach().cpu().numpy() if isinstance(scores, torch.Tensor) else scores,
+                              dtype=np.float32)
+    lb = np.ascontiguousarray((np.asarray(labels) != 0).astype(np.int8))
+    tp, fp, fn = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    f2 = ctypes.c_double(0)
+    check(_abi.load().wts_f2(sc.ctypes.data, lb.ctypes.data, len(sc), float(threshold), ctypes.byref(tp),
+                             ctypes.byref(fp), ctypes.byref(fn), ctypes.byref(f2)))
+    return {"tp": tp.value, "fp": fp.value, "fn": fn.value, "f2": f2.value}
+
+
 def dba_iterate(B_in: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None, B_out=None,
                 counts=None, cost_before=None, cost=None):
     """One DBA iteration: (B_out [M, d], counts [M], cost_before (0-d float64), cost [T])."""

@@ -2,6 +2,8 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -1075,5 +1077,58 @@ extern "C" int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch*
     p.plen_out = plen;
     p.score_out = score;
     if ((rc = launch_dp(kModePlen, L, p, opt, st))) return rc;
+    return ok();
+}
+
+// Detection thresholds and F2 (Sec. 5.3): host arithmetic on the T scores.
+int wts_thresholds(const float* scores, int32_t T, double* two_sigma, double* boxplot)
+{
+    if (!scores || (!two_sigma && !boxplot)) return fail(WTS_EINVAL, "NULL argument");
+    if (T < 1) return fail(WTS_EINVAL, "T must be >= 1");
+    std::vector<double> v(scores, scores + T);
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(WTS_EINVAL, "scores must be finite");
+    if (two_sigma) {
+        double mean = 0.0;
+        for (double x : v) mean += x;
+        mean /= T;
+        double var = 0.0;
+        for (double x : v) var += (x - mean) * (x - mean);
+        *two_sigma = mean + 2.0 * std::sqrt(var / T);
+    }
+    if (boxplot) {
+        // quartile q at position q (T - 1) of the sorted scores, linear between neighbours
+        std::sort(v.begin(), v.end());
+        auto quartile = [&](double q) {
+            const double pos = q * (T - 1);
+            const int64_t lo = (int64_t)std::floor(pos);
+            const int64_t hi = lo + 1 < T ? lo + 1 : lo;
+            return v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+        };
+        const double q1 = quartile(0.25), q3 = quartile(0.75);
+        *boxplot = q3 + 1.5 * std::fabs(q3 - q1);
+    }
+    return ok();
+}
+
+int wts_f2(const float* scores, const int8_t* labels, int32_t T, double threshold,
+           int32_t* tp, int32_t* fp, int32_t* fn, double* f2)
+{
+    if (!scores || !labels || !f2) return fail(WTS_EINVAL, "NULL argument");
+    if (T < 0) return fail(WTS_EINVAL, "T must be >= 0");
+    int32_t a = 0, b = 0, c = 0;
+    for (int32_t k = 0; k < T; ++k) {
+        const bool flag = (double)scores[k] > threshold;
+        const bool truth = labels[k] != 0;
+        a += flag && truth;
+        b += flag && !truth;
+        c += !flag && truth;
+    }
+    if (tp) *tp = a;
+    if (fp) *fp = b;
+    if (fn) *fn = c;
+    // F_beta with beta = 2: (1 + 4) TP / ((1 + 4) TP + 4 FN + FP); 0 when there is nothing to find or flag
+    const double den = 5.0 * a + 4.0 * c + b;
+    *f2 = den > 0 ? 5.0 * a / den : 0.0;
     return ok();
 }
