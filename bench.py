@@ -367,7 +367,8 @@ def bary_leg(api, torch, dev, barrier, gammas=(1.0, 0.1, 0.01), steps: int = 50,
     """Barycenters of the single-channel workload (64 cycles, M = 10,000): the
     Euclidean mean of the resampled cycles (Table I's initialisation), 10 DBA
     iterations from it, and the Soft-DTW barycenter of Eq. 7 by 50 Adam steps
-    from it; each scored by the intraclass inertia sum_k DTW(B, Y_k) and the
+    and by L-BFGS (Table I's settings) from it; each scored by the intraclass
+    inertia sum_k DTW(B, Y_k) and the
     mean d_score (Eq. 8), the quantities of the paper's barycenter comparison."""
     sb = synth.config_batch(2)
     M = synth.PROTO_LEN[2]
@@ -397,6 +398,13 @@ def bary_leg(api, torch, dev, barrier, gammas=(1.0, 0.1, 0.01), steps: int = 50,
         res[f"softdtw_barycenter_gamma_{gamma:g}"] = dict(quality(Bs), adam_steps=steps, lr=lr, seconds=el,
                                                           objective_first=float(obj[0]),
                                                           objective_last=float(obj[-1]))
+        # the paper's optimiser: L-BFGS with Table I's settings
+        t0 = time.perf_counter()
+        Bl, f, it, ev, why = api.softdtw_barycenter_lbfgs(gb, M, gamma, init=B0)
+        barrier()
+        el = time.perf_counter() - t0
+        res[f"softdtw_barycenter_lbfgs_gamma_{gamma:g}"] = dict(quality(Bl), iterations=it, evaluations=ev,
+                                                                stop=why, objective_last=f, seconds=el)
     del ws
     return res
 

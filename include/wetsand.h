@@ -61,6 +61,7 @@ enum {
     WTS_OP_PAIRWISE = 5,
     WTS_OP_COMPACT_NAN = 6,    /* wts_compact_nan (M ignored) */
     WTS_OP_SUBDTW = 7,         /* subdtw_align (M = length of X) */
+    WTS_OP_SOFTDTW_LBFGS = 8,  /* wts_softdtw_barycenter_lbfgs */
 };
 
 /* A packed batch of T cycles (Sec. 3.1: d-channel series of uneven lengths). */
@@ -227,6 +228,52 @@ int wts_thresholds(const float* scores, int32_t T, double* two_sigma, double* bo
  */
 int wts_f2(const float* scores, const int8_t* labels, int32_t T, double threshold,
            int32_t* tp, int32_t* fp, int32_t* fn, double* f2);
+
+/*
+ * L-BFGS (the optimiser of the paper's barycenters, Table I: "L-BFGS",
+ * max iter 40, max fun 200, G tol 1e-8, tolerance 1e-5), restated from the
+ * standard method (limited-memory BFGS, two-loop recursion):
+ *   direction d = -H g, H from the last `history` pairs (s, y) with s.y > 0,
+ *   initial scaling (s.y)/(y.y) of the newest pair (no pair: d = -g and a
+ *   first step of min(1, 1/||g||_2));
+ *   step by backtracking from 1, halving until f(x + t d) <= f + c1 t g.d;
+ *   stop when max|g| <= gtol (reason 1), when the relative reduction
+ *   (f_k - f_k+1) / max(|f_k|, |f_k+1|, 1) <= ftol (reason 2), after
+ *   max_iter iterations (3) or max_fun evaluations (4).
+ * All vectors in double on the host.  fn(x, f, g, ctx) evaluates the
+ * objective and its gradient and returns 0 (nonzero aborts with
+ * WTS_ECUDA).  x [n] is the start on entry and the last accepted iterate on
+ * return.  prm may be NULL (history 10, max_iter 40, max_fun 200, gtol 1e-8,
+ * ftol 1e-5, c1 1e-4).
+ */
+typedef int (*wts_objective_fn)(const double* x, double* f, double* g, void* ctx);
+typedef struct wts_lbfgs_params {
+    int32_t history;
+    int32_t max_iter;
+    int32_t max_fun;
+    int32_t reserved;
+    double gtol;
+    double ftol;
+    double c1;
+} wts_lbfgs_params;
+int wts_lbfgs_minimize(int64_t n, double* x, wts_objective_fn fn, void* ctx, const wts_lbfgs_params* prm,
+                       double* f_out, int32_t* n_iter, int32_t* n_eval, int32_t* reason);
+
+/*
+ * wts_softdtw_barycenter_lbfgs - the Soft-DTW barycenter of Eq. 7,
+ * argmin_B sum_k w_k Soft-DTW^gamma(B, Y_k) (w_k = lambda_k / m_k, by default
+ * 1 / N_k), by wts_lbfgs_minimize; every evaluation is one softdtw_forward
+ * and one softdtw_backward on the device (the iterate is copied in and the
+ * values and gradient out, the stream synchronised once per evaluation).
+ *   B [M][d]          in: the start (device), out: the last accepted iterate
+ *   weights [T]       device, or NULL for 1 / N_k
+ *   f_out, n_iter, n_eval, reason   host outputs (any may be NULL)
+ * Workspace: wts_workspace_size(WTS_OP_SOFTDTW_LBFGS, M, Y, opt, ...).
+ */
+int wts_softdtw_barycenter_lbfgs(float* B, int64_t M, const wts_batch* Y, float gamma, const float* weights,
+                                 const wts_lbfgs_params* prm, const wts_options* opt, void* workspace,
+                                 size_t workspace_bytes, void* stream, double* f_out, int32_t* n_iter,
+                                 int32_t* n_eval, int32_t* reason);
 
 /*
  * dba_iterate - one iteration of DTW Barycenter Averaging (Petitjean et al.

@@ -337,3 +337,85 @@ def f2(scores, labels, threshold):
     tp = int((flag & truth).sum()); fp = int((flag & ~truth).sum()); fn = int((~flag & truth).sum())
     den = 5 * tp + 4 * fn + fp
     return {"tp": tp, "fp": fp, "fn": fn, "f2": 5 * tp / den if den else 0.0}
+
+
+# --- L-BFGS (Table I's optimiser for the barycenter) ---------------------------
+
+def lbfgs(fn, x0, history=10, max_iter=40, max_fun=200, gtol=1e-8, ftol=1e-5, c1=1e-4):
+    """Limited-memory BFGS (two-loop recursion), restated from the standard
+    method: d = -H g from the last ``history`` pairs with s.y > 0, scaled by
+    (s.y)/(y.y) of the newest; no pair (or no descent): d = -g with a first
+    step min(1, 1/||g||_2); backtracking from 1, halving until
+    f(x + t d) <= f + c1 t g.d; stop at max|g| <= gtol ("gtol"), relative
+    reduction <= ftol ("ftol"), max_iter, max_fun.
+    Returns (x, f, iterations, evaluations, reason)."""
+    x = np.asarray(x0, dtype=np.float64).ravel().copy()
+    f, g = fn(x)
+    g = np.asarray(g, dtype=np.float64).ravel()
+    evals, it = 1, 0
+    S, Y, rho = [], [], []
+    while True:
+        if np.max(np.abs(g)) <= gtol:
+            why = "gtol"; break
+        if it >= max_iter:
+            why = "max_iter"; break
+        q = g.copy()
+        a = [0.0] * len(S)
+        for k in range(len(S) - 1, -1, -1):
+            a[k] = rho[k] * float(S[k] @ q)
+            q -= a[k] * Y[k]
+        if S:
+            q *= float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1])
+        for k in range(len(S)):
+            bk = rho[k] * float(Y[k] @ q)
+            q += S[k] * (a[k] - bk)
+        d = -q
+        gd = float(g @ d)
+        t = 1.0
+        if not S or not gd < 0:
+            S, Y, rho = [], [], []
+            d = -g
+            gd = -float(g @ g)
+            t = min(1.0, 1.0 / np.sqrt(-gd))
+        accepted = False
+        while evals < max_fun:
+            xn = x + t * d
+            fn_new, gn = fn(xn)
+            gn = np.asarray(gn, dtype=np.float64).ravel()
+            evals += 1
+            if fn_new <= f + c1 * t * gd:
+                accepted = True
+                break
+            t *= 0.5
+        if not accepted:
+            why = "max_fun"; break
+        s, y = xn - x, gn - g
+        sy = float(s @ y)
+        if sy > 1e-10 * np.sqrt(float(s @ s) * float(y @ y)):
+            if len(S) == history:
+                S.pop(0); Y.pop(0); rho.pop(0)
+            S.append(s); Y.append(y); rho.append(1.0 / sy)
+        it += 1
+        rel = (f - fn_new) / max(abs(f), abs(fn_new), 1.0)
+        x, f, g = xn, fn_new, gn
+        if rel <= ftol:
+            why = "ftol"; break
+    return x, f, it, evals, why
+
+
+def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, **params):
+    """Eq. 7 barycenter by ``lbfgs``, the objective and gradient from
+    ``softdtw_batch`` in FP64 at the float32 rounding of the iterate (the
+    barycenter is a float32 array), weights 1 / N_k."""
+    B0 = _as2d(B0)
+    M, d = B0.shape
+    lengths = np.diff(np.asarray(offsets, dtype=np.int64))
+    w = (1.0 / lengths).astype(np.float32).astype(np.float64)
+
+    def fn(x):
+        Bf = x.reshape(M, d).astype(np.float32)
+        vals, loss, g = softdtw_batch(Bf, data, offsets, gamma, weights=w, prec="f64")
+        return float(loss), g.ravel()
+
+    x, f, it, ev, why = lbfgs(fn, B0.astype(np.float64).ravel(), **params)
+    return x.reshape(M, d).astype(np.float32), f, it, ev, why

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libwetsand.so")
 WTS_OK, WTS_EINVAL, WTS_ENOMEM, WTS_ECUDA, WTS_ETIMEOUT = 0, 1, 2, 3, 4
 OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE, OP_COMPACT_NAN = 1, 2, 3, 4, 5, 6
 OP_SUBDTW = 7
+OP_SOFTDTW_LBFGS = 8
 
 # every symbol declared in include/wetsand.h
 EXPORTS = (
@@ -24,6 +25,7 @@ EXPORTS = (
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
     "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune", "wts_compact_nan",
     "subdtw_align", "wts_segment_workspace_size", "wts_segment", "wts_thresholds", "wts_f2",
+    "wts_lbfgs_minimize", "wts_softdtw_barycenter_lbfgs",
 )
 
 
@@ -50,6 +52,22 @@ class wts_options(ctypes.Structure):
         ("band", ctypes.c_double),
         ("reserved", ctypes.c_int32 * 6),
     ]
+
+
+class wts_lbfgs_params(ctypes.Structure):
+    _fields_ = [
+        ("history", ctypes.c_int32),
+        ("max_iter", ctypes.c_int32),
+        ("max_fun", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("gtol", ctypes.c_double),
+        ("ftol", ctypes.c_double),
+        ("c1", ctypes.c_double),
+    ]
+
+
+OBJECTIVE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
 class WtsError(RuntimeError):
@@ -81,6 +99,12 @@ _SIGS = {
     "wts_segment": ([VP, I64, VP, I64, I32, I64, PO, VP, SZ, VP, I32, VP, VP, VP, ctypes.POINTER(I32)],
                     ctypes.c_int),
     "wts_pairwise_dtw": ([PB, PO, VP, SZ, VP, VP], ctypes.c_int),
+    "wts_lbfgs_minimize": ([I64, VP, OBJECTIVE_FN, VP, ctypes.POINTER(wts_lbfgs_params),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                            ctypes.POINTER(I32)], ctypes.c_int),
+    "wts_softdtw_barycenter_lbfgs": ([VP, I64, PB, ctypes.c_float, VP, ctypes.POINTER(wts_lbfgs_params), PO, VP, SZ,
+                                      VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32),
+                                      ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
     "wts_thresholds": ([VP, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "wts_f2": ([VP, VP, I32, ctypes.c_double, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),

@@ -250,6 +250,60 @@ def segment(X: torch.Tensor, Y: torch.Tensor, alpha: int | None = None, opts=Non
     return [(int(start[k]), int(end[k]), float(cost[k])) for k in range(n.value)]
 
 
+LBFGS_REASONS = {1: "gtol", 2: "ftol", 3: "max_iter", 4: "max_fun"}
+
+
+def lbfgs_params(history=10, max_iter=40, max_fun=200, gtol=1e-8, ftol=1e-5, c1=1e-4):
+    """L-BFGS settings; the defaults are Table I's (max iter 40, max fun 200,
+    G tol 1e-8, tolerance 1e-5) with a history of 10 pairs."""
+    p = _abi.wts_lbfgs_params()
+    p.history, p.max_iter, p.max_fun = history, max_iter, max_fun
+    p.gtol, p.ftol, p.c1 = gtol, ftol, c1
+    return p
+
+
+def lbfgs_minimize(fn, x0, params=None):
+    """Minimise fn(x) -> (f, grad) from x0 with the library's L-BFGS (host).
+    Returns (x, f, iterations, evaluations, reason)."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64).ravel().copy())
+    n = x.size
+
+    def cb(xp, fp, gp, ctx):
+        xv = np.ctypeslib.as_array(xp, shape=(n,))
+        f, g = fn(xv.copy())
+        fp[0] = float(f)
+        np.ctypeslib.as_array(gp, shape=(n,))[:] = np.asarray(g, dtype=np.float64).ravel()
+        return 0
+
+    cfn = _abi.OBJECTIVE_FN(cb)
+    f = ctypes.c_double(0)
+    it, ev, why = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    check(_abi.load().wts_lbfgs_minimize(n, x.ctypes.data, cfn, None, ctypes.byref(params or lbfgs_params()),
+                                         ctypes.byref(f), ctypes.byref(it), ctypes.byref(ev), ctypes.byref(why)))
+    return x.reshape(np.shape(x0)), f.value, it.value, ev.value, LBFGS_REASONS.get(why.value, why.value)
+
+
+def softdtw_barycenter_lbfgs(batch: Batch, M: int, gamma: float, init: torch.Tensor | None = None,
+                             weights: torch.Tensor | None = None, params=None, opts=None, ws: Workspace | None = None):
+    """Soft-DTW barycenter (Eq. 7) by L-BFGS with Table I's settings: B
+    minimises sum_k w_k Soft-DTW^gamma(B, Y_k), w_k = 1 / N_k unless given;
+    starts from the Euclidean mean resampled to M unless ``init`` is given.
+    Returns (B, objective, iterations, evaluations, stop reason)."""
+    dev = batch.data.device
+    B = euclid_mean(batch, M) if init is None else init.detach().clone().contiguous()
+    lib = _abi.load()
+    nb = workspace_size(_abi.OP_SOFTDTW_LBFGS, M, batch, opts)
+    buf = _ws(ws, nb)
+    f = ctypes.c_double(0)
+    it, ev, why = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    check(lib.wts_softdtw_barycenter_lbfgs(B.data_ptr(), M, ctypes.byref(batch.c()), float(gamma),
+                                           weights.data_ptr() if weights is not None else None,
+                                           ctypes.byref(params or lbfgs_params()), _opt(opts), buf.data_ptr(),
+                                           buf.numel(), _stream(), ctypes.byref(f), ctypes.byref(it),
+                                           ctypes.byref(ev), ctypes.byref(why)))
+    return B, f.value, it.value, ev.value, LBFGS_REASONS.get(why.value, why.value)
+
+
 def thresholds(scores) -> tuple[float, float]:
     """The 2-sigma and boxplot detection thresholds of Sec. 5.3 on the scores
     (host computation in the library): (mean + 2 std, q3 + 1.5 |q3 - q1|)."""

@@ -506,21 +506,32 @@ int wts_peak_probe(int which, double* ops_per_s)
     return ok();
 }
 
+namespace {
+
+// After the soft-DTW workspace: values [T], weights [T], gradient [M][d] (FP32).
+size_t lbfgs_extra_bytes(int64_t M, const wts_batch* Y)
+{
+    return 2 * align256((size_t)Y->T * sizeof(float)) + align256((size_t)M * Y->d * sizeof(float));
+}
+
+}  // namespace
+
 int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes)
 {
     if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
-    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise, 0, kOpSubdtw};
+    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise, 0, kOpSubdtw, kOpSoft};
     if (op == WTS_OP_COMPACT_NAN) {
         int rc = check_batch(Y, false);
         if (rc) return rc;
         *bytes = align256(compact_workspace_bytes(Y->offsets_host[Y->T]));
         return ok();
     }
-    if (op < 1 || op > 7 || op == WTS_OP_COMPACT_NAN) return fail(WTS_EINVAL, "unknown op %d", op);
+    if (op < 1 || op > 8 || op == WTS_OP_COMPACT_NAN) return fail(WTS_EINVAL, "unknown op %d", op);
     Layout L;
     int rc = compute_layout(map[op], M, Y, opt, &L);
     if (rc) return rc;
     *bytes = L.total;
+    if (op == WTS_OP_SOFTDTW_LBFGS) *bytes += lbfgs_extra_bytes(M, Y);
     return ok();
 }
 
@@ -1130,5 +1141,193 @@ int wts_f2(const float* scores, const int8_t* labels, int32_t T, double threshol
     // F_beta with beta = 2: (1 + 4) TP / ((1 + 4) TP + 4 FN + FP); 0 when there is nothing to find or flag
     const double den = 5.0 * a + 4.0 * c + b;
     *f2 = den > 0 ? 5.0 * a / den : 0.0;
+    return ok();
+}
+
+// L-BFGS (see include/wetsand.h for the method and its stopping rules).
+int wts_lbfgs_minimize(int64_t n, double* x, wts_objective_fn fn, void* ctx, const wts_lbfgs_params* prm,
+                       double* f_out, int32_t* n_iter, int32_t* n_eval, int32_t* reason)
+{
+    if (!x || !fn) return fail(WTS_EINVAL, "x and fn must not be NULL");
+    if (n < 1) return fail(WTS_EINVAL, "n must be >= 1");
+    wts_lbfgs_params P{10, 40, 200, 0, 1e-8, 1e-5, 1e-4};
+    if (prm) P = *prm;
+    if (P.history < 1 || P.max_iter < 0 || P.max_fun < 1 || !(P.gtol >= 0) || !(P.ftol >= 0) || !(P.c1 > 0 && P.c1 < 1))
+        return fail(WTS_EINVAL, "bad L-BFGS parameters");
+    auto dot = [n](const double* a, const double* b) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+        return s;
+    };
+    std::vector<double> g(n), d(n), xn(n), gn(n), q(n);
+    std::vector<std::vector<double>> S, Yv;
+    std::vector<double> rho;
+    double f = 0.0;
+    int evals = 0, it = 0, why = 0;
+    if (fn(x, &f, g.data(), ctx)) return fail(WTS_ECUDA, "objective evaluation failed");
+    ++evals;
+    for (;;) {
+        double gmax = 0.0;
+        for (int64_t i = 0; i < n; ++i) gmax = std::max(gmax, std::fabs(g[i]));
+        if (gmax <= P.gtol) { why = 1; break; }
+        if (it >= P.max_iter) { why = 3; break; }
+        // two-loop recursion: d = -H g
+        const int h = (int)S.size();
+        std::vector<double> a(h);
+        for (int64_t i = 0; i < n; ++i) q[i] = g[i];
+        for (int k = h - 1; k >= 0; --k) {
+            a[k] = rho[k] * dot(S[k].data(), q.data());
+            for (int64_t i = 0; i < n; ++i) q[i] -= a[k] * Yv[k][i];
+        }
+        const double scale = h ? dot(S[h - 1].data(), Yv[h - 1].data()) / dot(Yv[h - 1].data(), Yv[h - 1].data()) : 1.0;
+        for (int64_t i = 0; i < n; ++i) q[i] *= scale;
+        for (int k = 0; k < h; ++k) {
+            const double bk = rho[k] * dot(Yv[k].data(), q.data());
+            for (int64_t i = 0; i < n; ++i) q[i] += S[k][i] * (a[k] - bk);
+        }
+        for (int64_t i = 0; i < n; ++i) d[i] = -q[i];
+        double gd = dot(g.data(), d.data());
+        double t = 1.0;
+        if (h == 0 || !(gd < 0)) {
+            // no curvature pairs (or not a descent direction): steepest descent
+            S.clear(); Yv.clear(); rho.clear();
+            for (int64_t i = 0; i < n; ++i) d[i] = -g[i];
+            gd = -dot(g.data(), g.data());
+            t = std::min(1.0, 1.0 / std::sqrt(-gd));
+        }
+        // backtracking (Armijo)
+        double fn_new = 0.0;
+        bool accepted = false;
+        while (evals < P.max_fun) {
+            for (int64_t i = 0; i < n; ++i) xn[i] = x[i] + t * d[i];
+            if (fn(xn.data(), &fn_new, gn.data(), ctx)) return fail(WTS_ECUDA, "objective evaluation failed");
+            ++evals;
+            if (fn_new <= f + P.c1 * t * gd) { accepted = true; break; }
+            t *= 0.5;
+        }
+        if (!accepted) { why = 4; break; }
+        std::vector<double> s(n), y(n);
+        for (int64_t i = 0; i < n; ++i) { s[i] = xn[i] - x[i]; y[i] = gn[i] - g[i]; }
+        const double sy = dot(s.data(), y.data());
+        if (sy > 1e-10 * std::sqrt(dot(s.data(), s.data()) * dot(y.data(), y.data()))) {
+            if ((int)S.size() == P.history) { S.erase(S.begin()); Yv.erase(Yv.begin()); rho.erase(rho.begin()); }
+            S.push_back(std::move(s));
+            Yv.push_back(std::move(y));
+            rho.push_back(1.0 / sy);
+        }
+        ++it;
+        const double rel = (f - fn_new) / std::max(std::max(std::fabs(f), std::fabs(fn_new)), 1.0);
+        for (int64_t i = 0; i < n; ++i) { x[i] = xn[i]; g[i] = gn[i]; }
+        f = fn_new;
+        if (rel <= P.ftol) { why = 2; break; }
+    }
+    if (f_out) *f_out = f;
+    if (n_iter) *n_iter = it;
+    if (n_eval) *n_eval = evals;
+    if (reason) *reason = why;
+    return ok();
+}
+
+namespace {
+
+struct SoftObjective {
+    float* B;
+    int64_t M;
+    const wts_batch* Y;
+    float gamma;
+    const wts_options* opt;
+    char* ws;
+    size_t soft_bytes;
+    cudaStream_t st;
+    float* d_values;
+    const float* d_weights;
+    float* d_grad;
+    std::vector<double> w;        // host weights
+    std::vector<float> xf, vals, gf;
+    int err = WTS_OK;
+};
+
+int soft_objective(const double* x, double* f, double* g, void* ctx)
+{
+    SoftObjective& o = *static_cast<SoftObjective*>(ctx);
+    const int64_t n = o.M * o.Y->d;
+    for (int64_t i = 0; i < n; ++i) o.xf[i] = (float)x[i];
+    cudaError_t e = cudaMemcpyAsync(o.B, o.xf.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice, o.st);
+    if (e != cudaSuccess) { o.err = cuda_fail(e, "barycenter copy"); return 1; }
+    int rc = softdtw_forward(o.B, o.M, o.Y, o.gamma, o.opt, o.ws, o.soft_bytes, o.st, o.d_values);
+    if (rc == WTS_OK)
+        rc = softdtw_backward(o.B, o.M, o.Y, o.gamma, o.d_weights, o.opt, o.ws, o.soft_bytes, o.st, o.d_grad);
+    if (rc != WTS_OK) { o.err = rc; return 1; }
+    e = cudaMemcpyAsync(o.vals.data(), o.d_values, (size_t)o.Y->T * sizeof(float), cudaMemcpyDeviceToHost, o.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(o.gf.data(), o.d_grad, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, o.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(o.st);
+    if (e != cudaSuccess) { o.err = cuda_fail(e, "objective read-back"); return 1; }
+    double s = 0.0;
+    for (int k = 0; k < o.Y->T; ++k) s += o.w[k] * (double)o.vals[k];
+    *f = s;
+    for (int64_t i = 0; i < n; ++i) g[i] = (double)o.gf[i];
+    return 0;
+}
+
+}  // namespace
+
+int wts_softdtw_barycenter_lbfgs(float* B, int64_t M, const wts_batch* Y, float gamma, const float* weights,
+                                 const wts_lbfgs_params* prm, const wts_options* opt, void* workspace,
+                                 size_t workspace_bytes, void* stream, double* f_out, int32_t* n_iter,
+                                 int32_t* n_eval, int32_t* reason)
+{
+    Layout L;
+    int rc = compute_layout(kOpSoft, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if ((rc = check_gamma(gamma))) return rc;
+    if (!B) return fail(WTS_EINVAL, "B must not be NULL");
+    const size_t need = L.total + lbfgs_extra_bytes(M, Y);
+    if (!workspace || ((uintptr_t)workspace & 255) != 0) return fail(WTS_EINVAL, "workspace must be 256-byte aligned");
+    if (workspace_bytes < need) return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
+    SoftObjective o;
+    o.B = B;
+    o.M = M;
+    o.Y = Y;
+    o.gamma = gamma;
+    o.opt = opt;
+    o.ws = (char*)workspace;
+    o.soft_bytes = L.total;
+    o.st = (cudaStream_t)stream;
+    char* extra = o.ws + L.total;
+    o.d_values = reinterpret_cast<float*>(extra);
+    float* d_w = reinterpret_cast<float*>(extra + align256((size_t)Y->T * sizeof(float)));
+    o.d_grad = reinterpret_cast<float*>(extra + 2 * align256((size_t)Y->T * sizeof(float)));
+    const int64_t n = M * Y->d;
+    o.xf.resize(n);
+    o.gf.resize(n);
+    o.vals.resize(Y->T);
+    o.w.resize(Y->T);
+    std::vector<float> wf(Y->T);
+    if (weights) {
+        cudaError_t e = cudaMemcpyAsync(wf.data(), weights, (size_t)Y->T * sizeof(float), cudaMemcpyDeviceToHost, o.st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(o.st);
+        if (e != cudaSuccess) return cuda_fail(e, "weights read");
+    } else {
+        for (int k = 0; k < Y->T; ++k) wf[k] = (float)(1.0 / (double)(Y->offsets_host[k + 1] - Y->offsets_host[k]));
+    }
+    for (int k = 0; k < Y->T; ++k) o.w[k] = (double)wf[k];
+    cudaError_t e = cudaMemcpyAsync(d_w, wf.data(), (size_t)Y->T * sizeof(float), cudaMemcpyHostToDevice, o.st);
+    if (e != cudaSuccess) return cuda_fail(e, "weights copy");
+    o.d_weights = d_w;
+    // start from B
+    std::vector<double> x(n);
+    e = cudaMemcpyAsync(o.xf.data(), B, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, o.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(o.st);
+    if (e != cudaSuccess) return cuda_fail(e, "barycenter read");
+    for (int64_t i = 0; i < n; ++i) x[i] = (double)o.xf[i];
+    rc = wts_lbfgs_minimize(n, x.data(), soft_objective, &o, prm, f_out, n_iter, n_eval, reason);
+    if (rc != WTS_OK) return o.err != WTS_OK ? o.err : rc;
+    // leave the last accepted iterate in B
+    for (int64_t i = 0; i < n; ++i) o.xf[i] = (float)x[i];
+    e = cudaMemcpyAsync(B, o.xf.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice, o.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(o.st);
+    if (e != cudaSuccess) return cuda_fail(e, "barycenter write");
     return ok();
 }

@@ -24,7 +24,7 @@ def lib():
 def _declared():
     src = open(os.path.join(ROOT, "include", "wetsand.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M))
+    return set(re.findall(r"^\s*(?!typedef\b)(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M))
 
 
 def test_every_declared_symbol_is_exported(lib):

@@ -166,3 +166,23 @@ def test_full_size_pair_value(wts):
     for k in (0, 63):
         ref = oracle.softdtw(Bh, b.cycle(k), 1.0, "f64", want_grad=False)["value"]
         assert abs(v[k] - ref) <= VALUE_TOL * max(abs(ref), 1.0), (k, v[k], ref)
+
+
+def test_lbfgs_barycenter_matches_oracle(wts):
+    """Eq. 7 barycenter by L-BFGS with Table I's settings on a small batch: the
+    library (objective and gradient from the GPU kernels, FP32) and the oracle
+    (FP64) reach the same objective to 1e-3 relative; the objective never
+    rises above the start's."""
+    b = synth.config_batch(2, scale=0.008, T=5)          # 5 cycles of 64-96 samples
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M = 60
+    B0 = wts.euclid_mean(gb, M)
+    Bg, f, it, ev, why = wts.softdtw_barycenter_lbfgs(gb, M, 1.0, init=B0)
+    assert why in ("ftol", "gtol", "max_iter", "max_fun") and it <= 40 and ev <= 200
+    B0h = B0.cpu().numpy()
+    w = (1.0 / b.lengths).astype(np.float32)
+    _, f0, _ = oracle.softdtw_batch(B0h, b.data, b.offsets, 1.0, weights=w, prec="f64")
+    Bo, fo, ito, evo, whyo = oracle.softdtw_barycenter_lbfgs(b.data, b.offsets, B0h, 1.0)
+    _, fg, _ = oracle.softdtw_batch(Bg.cpu().numpy(), b.data, b.offsets, 1.0, weights=w, prec="f64")
+    assert fg < f0 and fo < f0
+    assert abs(fg - fo) <= 1e-3 * abs(fo), (fg, fo, it, ito)
