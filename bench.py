@@ -37,9 +37,10 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per cell of the code-writing wavefront, from one
 # ncu capture of the same kernel build on 36 cycles of this workload
-# (profiles/wavefront_dirs_36x25k_d6.md): 5.8027e9 bytes / 2.2029e10 cells.
-# Traffic grows in proportion to the cells (codes + hand-off rows).
-WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = 5.8027e9 / 2.2029e10
+# (profiles/wavefront_dirs_36x25k_d6.md): (0.1582 + 5.6421)e9 bytes /
+# 2.2029e10 cells.  Traffic grows in proportion to the cells (codes +
+# hand-off rows).
+WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1582 + 5.6421) * 1e9 / 2.2029e10
 # DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
 # ncu capture of both kernels on 8 cycles of the soft-DTW workload
 # (profiles/softdtw_fwd_bwd_8x10k_d1.md): (0.0132 + 3.2475 + 3.3412 + 0.0526)e9
