@@ -90,10 +90,11 @@ def _lib(defines: tuple = ()):
             fn.argtypes = [Rp, Rp, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_softdtw_{p}")
-            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, R, VP, VP, VP, VP]
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, R, VP, VP, VP, VP, ctypes.c_double]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_softdtw_batch_{p}")
-            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, R, VP, VP, VP, VP]
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, R, VP, VP, VP, VP,
+                           ctypes.c_double]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_subdtw_{p}")
             fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, VP, VP, VP, VP, VP, VP]
@@ -225,8 +226,9 @@ def dba_iterate(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines
 
 
 def softdtw(B, Y, gamma: float, prec: str = "f64", want_R=False, want_E=False, want_grad=True,
-            _defines: tuple = ()):
-    """Soft-DTW^gamma(B, Y), optionally R, E ((M+2) x (N+2), 1-based) and grad [M, d]."""
+            band: float = 0.0, _defines: tuple = ()):
+    """Soft-DTW^gamma(B, Y), optionally R, E ((M+2) x (N+2), 1-based) and grad [M, d];
+    band > 0: only the complete paths inside the Sakoe-Chiba band (as in ``dtw``)."""
     B = _as2d(B); Y = _as2d(Y)
     M, d = B.shape; N = Y.shape[0]
     dt = _dt(prec)
@@ -234,14 +236,16 @@ def softdtw(B, Y, gamma: float, prec: str = "f64", want_R=False, want_E=False, w
     R = np.zeros((M + 2, N + 2), dtype=dt) if want_R else None
     E = np.zeros((M + 2, N + 2), dtype=dt) if want_E else None
     g = np.zeros((M, d), dtype=dt) if want_grad else None
-    rc = getattr(_lib(_defines), f"orc_softdtw_{prec}")(B, M, Y, N, d, gamma, _ptr(v), _ptr(R), _ptr(E), _ptr(g))
+    rc = getattr(_lib(_defines), f"orc_softdtw_{prec}")(B, M, Y, N, d, gamma, _ptr(v), _ptr(R), _ptr(E), _ptr(g),
+                                                      band)
     if rc:
-        raise ValueError("oracle softdtw failed (allocation, or gamma <= 0 with a gradient requested)")
+        raise ValueError("oracle softdtw failed (allocation, gamma <= 0 with a gradient requested, "
+                         "or a band narrower than max(M, N))")
     return dict(value=v[0], R=R, E=E, grad=g)
 
 
 def softdtw_batch(B, data, offsets, gamma: float, weights=None, prec: str = "f64", want_grad=True,
-                  _defines: tuple = ()):
+                  band: float = 0.0, _defines: tuple = ()):
     """Eq. 7 objective over a packed batch: (values[T], loss, grad[M, d] or None)."""
     B = _as2d(B); data = _as2d(data)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -253,7 +257,7 @@ def softdtw_batch(B, data, offsets, gamma: float, weights=None, prec: str = "f64
     loss = np.zeros(1, dtype=dt)
     g = np.zeros((M, d), dtype=dt) if want_grad else None
     rc = getattr(_lib(_defines), f"orc_softdtw_batch_{prec}")(B, M, data, offsets, T, d, gamma, _ptr(w),
-                                                            _ptr(vals), _ptr(loss), _ptr(g))
+                                                            _ptr(vals), _ptr(loss), _ptr(g), band)
     if rc:
         raise ValueError("oracle softdtw_batch failed")
     return vals, loss[0], g
@@ -403,7 +407,7 @@ def lbfgs(fn, x0, history=10, max_iter=40, max_fun=200, gtol=1e-8, ftol=1e-5, c1
     return x, f, it, evals, why
 
 
-def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, **params):
+def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, band: float = 0.0, **params):
     """Eq. 7 barycenter by ``lbfgs``, the objective and gradient from
     ``softdtw_batch`` in FP64 at the float32 rounding of the iterate (the
     barycenter is a float32 array), weights 1 / N_k."""
@@ -414,7 +418,7 @@ def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, **params):
 
     def fn(x):
         Bf = x.reshape(M, d).astype(np.float32)
-        vals, loss, g = softdtw_batch(Bf, data, offsets, gamma, weights=w, prec="f64")
+        vals, loss, g = softdtw_batch(Bf, data, offsets, gamma, weights=w, prec="f64", band=band)
         return float(loss), g.ravel()
 
     x, f, it, ev, why = lbfgs(fn, B0.astype(np.float64).ravel(), **params)

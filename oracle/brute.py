@@ -129,3 +129,19 @@ def dtw_band(B, Y, band: float):
     best = min(costs)
     chosen = max((p for p, c in zip(ps, costs) if c == best), key=reversed_steps)
     return best, chosen
+
+
+def softdtw_band(B, Y, gamma: float, band: float):
+    """Eq. 4 over the complete paths inside the band: (value, E)."""
+    D = cost_matrix(B, Y)
+    M, N = D.shape
+    ps = [p for p in paths(M, N) if all(in_band(i, j, M, N, band) for i, j in p)]
+    costs = np.array([sum(D[i, j] for i, j in p) for p in ps])
+    m = costs.min()
+    w = np.exp(-(costs - m) / gamma)
+    Z = w.sum()
+    E = np.zeros((M, N))
+    for p, wk in zip(ps, w):
+        for i, j in p:
+            E[i, j] += wk / Z
+    return m - gamma * math.log(Z), E

@@ -280,8 +280,15 @@ static REAL SFX(softmin3)(REAL a, REAL b, REAL c, REAL gamma)
  * gradient.  Returns 0 or -1.
  */
 int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d, REAL gamma,
-                     REAL* value, REAL* R_out, REAL* E_out, REAL* grad)
+                     REAL* value, REAL* R_out, REAL* E_out, REAL* grad, double band)
 {
+    /* Sakoe-Chiba band as in dtw_core: 0-based cell (i, j) kept when
+     * |i N - j M| <= floor(band M N); cells outside are +inf in the forward
+     * and, like the border, -inf with delta = 0 (no successor weight) in the
+     * reverse recursion. */
+    const int64_t bound = band > 0 ? (int64_t)floor(band * (double)M * (double)N) : -1;
+    if (band > 0 && bound < (M > N ? M : N)) return -3;
+#define SOFT_OUT(i, j) (bound >= 0 && (((i) - 1) * N - ((j) - 1) * M > bound || ((j) - 1) * M - ((i) - 1) * N > bound))
     const int64_t W = N + 2;
     size_t cells = (size_t)(M + 2) * (size_t)W;
     REAL* R = R_out ? R_out : (REAL*)malloc(cells * sizeof(REAL));
@@ -291,6 +298,7 @@ int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d
     R[0] = 0;
     for (int64_t i = 1; i <= M; ++i)
         for (int64_t j = 1; j <= N; ++j) {
+            if (SOFT_OUT(i, j)) continue;          /* stays +inf */
             REAL dl = SFX(local_cost)(B + (i - 1) * d, Y + (j - 1) * d, d);
             D[i * W + j] = dl;
             R[i * W + j] = dl + SFX(softmin3)(R[(i - 1) * W + j - 1], R[(i - 1) * W + j],
@@ -308,8 +316,12 @@ int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d
         for (int64_t j = 1; j <= N; ++j) R[(M + 1) * W + j] = (REAL)-INFINITY;
         R[(M + 1) * W + N + 1] = R[M * W + N];
         E[(M + 1) * W + N + 1] = 1;
+        for (int64_t i = 1; i <= M; ++i)
+            for (int64_t j = 1; j <= N; ++j)
+                if (SOFT_OUT(i, j)) R[i * W + j] = (REAL)-INFINITY;
         for (int64_t i = M; i >= 1; --i)
             for (int64_t j = N; j >= 1; --j) {
+                if (SOFT_OUT(i, j)) continue;      /* e stays 0 */
                 REAL r = R[i * W + j];
                 REAL a = EXP((R[(i + 1) * W + j] - r - D[(i + 1) * W + j]) / gamma);
                 REAL b = EXP((R[i * W + j + 1] - r - D[i * W + j + 1]) / gamma);
@@ -332,9 +344,13 @@ int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d
         /* restore the forward border so R_out holds Eq. 5's matrix */
         for (int64_t i = 1; i <= M; ++i) R[i * W + N + 1] = (REAL)INFINITY;
         for (int64_t j = 1; j <= N + 1; ++j) R[(M + 1) * W + j] = (REAL)INFINITY;
+        for (int64_t i = 1; i <= M; ++i)
+            for (int64_t j = 1; j <= N; ++j)
+                if (SOFT_OUT(i, j)) R[i * W + j] = (REAL)INFINITY;
         if (!E_out) free(E);
     }
 done:
+#undef SOFT_OUT
     if (!R_out) free(R);
     free(D);
     return rc;
@@ -348,7 +364,7 @@ done:
  * order.  Pairs run on OpenMP threads.
  */
 int SFX(orc_softdtw_batch)(const float* B, int64_t M, const float* Y, const int64_t* offsets, int T, int d,
-                           REAL gamma, const REAL* weights, REAL* values, REAL* loss, REAL* grad)
+                           REAL gamma, const REAL* weights, REAL* values, REAL* loss, REAL* grad, double band)
 {
     REAL* g = grad ? (REAL*)calloc((size_t)T * M * d, sizeof(REAL)) : NULL;
     REAL* v = (REAL*)malloc((size_t)T * sizeof(REAL));
@@ -358,7 +374,7 @@ int SFX(orc_softdtw_batch)(const float* B, int64_t M, const float* Y, const int6
     for (int k = 0; k < T; ++k) {
         int64_t N = offsets[k + 1] - offsets[k];
         bad |= SFX(orc_softdtw)(B, M, Y + offsets[k] * d, N, d, gamma, &v[k], NULL, NULL,
-                                g ? g + (int64_t)k * M * d : NULL);
+                                g ? g + (int64_t)k * M * d : NULL, band) != 0;
     }
     if (!bad) {
         REAL L = 0;

@@ -315,6 +315,28 @@ def test_banded_dtw_matches_brute_force(prec):
                 assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen, (M, N, w)
 
 
+def test_banded_softdtw_matches_brute_force():
+    """Soft-DTW restricted to the in-band paths: value and E against
+    enumeration, for the narrowest accepted band and a wider one; E is zero
+    outside the band."""
+    rng = np.random.default_rng(53)
+    for M, N in ((4, 6), (6, 3), (5, 5), (3, 3)):
+        B, Y = _real_pair(rng, M, N, 2)
+        for w in (max(M, N) / (M * N), 0.45):
+            if math.floor(w * M * N) < max(M, N):
+                continue
+            for gamma in (1.0, 0.3):
+                v, E = brute.softdtw_band(B, Y, gamma, w)
+                r = oracle.softdtw(B, Y, gamma, "f64", want_E=True, band=w)
+                assert abs(r["value"] - v) <= 1e-10 * max(1.0, abs(v)), (M, N, w, gamma)
+                assert np.allclose(r["E"][1:M + 1, 1:N + 1], E, atol=1e-10), (M, N, w, gamma)
+    # w >= 1 is no band
+    B, Y = _real_pair(rng, 30, 41, 1)
+    a = oracle.softdtw(B, Y, 0.5, "f64")
+    b = oracle.softdtw(B, Y, 0.5, "f64", band=1.0)
+    assert a["value"] == b["value"] and np.array_equal(a["grad"], b["grad"])
+
+
 def test_band_limits_and_refusal():
     """w >= 1 changes nothing; the cost never decreases as the band narrows;
     M = N with floor(w N^2) = N is the band |i - j| <= 1; a band narrower than
