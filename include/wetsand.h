@@ -92,8 +92,10 @@ typedef struct wts_options {
                                       0-based cell (i, j) of an M x N pair is kept when
                                       |i N - j M| <= floor(band M N) (|i/M - j/N| <= band); cells outside are
                                       +inf.  0 = no band.  A band narrower than max(M, N) for some pair (it may
-                                      hold no complete path) is WTS_EINVAL.  DTW operations only (anomaly_score,
-                                      dtw_align, dba_iterate). */
+                                      hold no complete path) is WTS_EINVAL.  DTW and soft-DTW operations
+                                      (anomaly_score, dtw_align, dba_iterate, softdtw_forward / _backward and
+                                      the barycenters); for soft-DTW, cells outside the band take no part in the
+                                      soft minimum (forward) and carry no weight (backward). */
     int32_t reserved[6];
 } wts_options;
 

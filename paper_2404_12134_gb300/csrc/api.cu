@@ -152,9 +152,11 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         L->R = soft_rows(D);          // fixed by the channel count (registers)
     }
     if (opt && opt->band > 0) {
-        if (opt->rows_per_thread && opt->rows_per_thread != 16)
-            return fail(WTS_EINVAL, "with a band, rows_per_thread must be 0 or 16 (got %d)", opt->rows_per_thread);
-        L->R = 16;
+        if (op != kOpSoft) {
+            if (opt->rows_per_thread && opt->rows_per_thread != 16)
+                return fail(WTS_EINVAL, "with a band, rows_per_thread must be 0 or 16 (got %d)", opt->rows_per_thread);
+            L->R = 16;
+        }
         L->banded = 1;
     }
     L->BR = 32 * L->R;
@@ -174,8 +176,8 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             Np = o[p + 1] - o[p];
         }
         if (opt && opt->band > 0) {
-            if (op != kOpScore && op != kOpAlign && op != kOpDba)
-                return fail(WTS_EINVAL, "the band applies to anomaly_score, dtw_align and dba_iterate only");
+            if (op != kOpScore && op != kOpAlign && op != kOpDba && op != kOpSoft)
+                return fail(WTS_EINVAL, "the band applies to the DTW and soft-DTW operations only");
             const int64_t bb = band_bound_of(opt->band, Mp, Np);
             if (bb < (Mp > Np ? Mp : Np))
                 return fail(WTS_EINVAL, "band %g too narrow for pair %d (%lld x %lld): floor(band M N) = %lld < "
@@ -428,6 +430,7 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     p.ebuf = reinterpret_cast<float*>(ws + L.off_ebuf);
     p.rstore = reinterpret_cast<float*>(ws + L.off_rstore);
     p.gpart = reinterpret_cast<float*>(ws + L.off_gpart);
+    p.banded = L.banded;
     return p;
 }
 
@@ -439,7 +442,7 @@ int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, 
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block);
+    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded);
     if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;

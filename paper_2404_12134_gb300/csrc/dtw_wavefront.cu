@@ -90,9 +90,7 @@ __device__ __forceinline__ uint32_t ne_mask(float a, float b)
 constexpr int kRing = 128;   // columns of cycle samples staged per warp
 constexpr int kSlot = 4;     // u64 words after a warp's ring: its band's columns and the band
 
-// floor(a / b) and ceil(a / b) for b > 0 and any sign of a
-__device__ __forceinline__ int64_t floor_div64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-__device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return -floor_div64(-a, b); }
+
 
 // c[k] for a k known only at run time, by a binary tree of selects on the bits
 // of k (R - 1 selects, no local memory)
@@ -319,7 +317,11 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
         }
         __syncwarp();
     }
-    const int s_begin = jlo_b & ~31;        // chunks of 32 steps from a multiple of 32
+    // chunks of 32 steps from a multiple of 32, starting at or before column
+    // jlo_b - 1: lane 0 takes its first diagonal, r(r0 - 1, jlo_b - 1), from
+    // the row above at the step before its first column (that cell may be
+    // inside the band)
+    const int s_begin = max(0, (jlo_b - 1) & ~31);
     const int s_end = jhi_b + 32;           // one past the last step (column jhi_b in lane 31)
 
     // hand-off rows: slot size 4 bytes (r), or 8 bytes ({r, cells}) with |pi|

@@ -104,7 +104,7 @@ __device__ __forceinline__ float local_cost(const float* bk, const float* y, flo
     return acc;
 }
 
-template <int D, int R>
+template <int D, int R, bool BANDED>
 __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane)
 {
     constexpr int BR = 32 * R;
@@ -134,6 +134,23 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     float* hcur = (last || p.recompute || p.skip_handoff) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
     float* rs = p.store_r ? p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R : nullptr;
 
+    // Sakoe-Chiba band (as in the hard-min wavefront): the band's columns
+    // [jlo, jhi], the row above's [jtop_lo, jtop_hi] (the only columns its
+    // producer writes), and the lane's columns with every row inside
+    const int64_t bnd = BANDED ? pd.band_bound : -1;
+    int jlo = 0, jhi = N - 1, jtop_lo = 0, jtop_hi = N - 1, full_lo = 0, full_hi = N - 1;
+    if (BANDED) {
+        const int64_t r0 = (int64_t)band * BR, r1 = min(r0 + BR, (int64_t)M) - 1;
+        jlo = band_lo(r0, bnd, M, N);
+        jhi = band_hi(r1, bnd, M, N);
+        if (!top) { jtop_lo = band_lo(r0 - 1, bnd, M, N); jtop_hi = band_hi(r0 - 1, bnd, M, N); }
+        if (i0 < M) { full_lo = band_lo(min(i0 + R - 1, M - 1), bnd, M, N); full_hi = band_hi(i0, bnd, M, N); }
+    }
+    // from a multiple of 32 at or before jlo - 1 (lane 0's first diagonal is
+    // the row above one column before the band starts)
+    const int s_begin = BANDED ? max(0, (jlo - 1) & ~31) : 0;
+    const int s_end = BANDED ? jhi + 32 : N + 31;
+
     // lane-0 feeds one chunk of 32 columns ahead (the top row is NaN until written)
     float ynext[D];
     float tnext = INF;
@@ -141,21 +158,21 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 #pragma unroll
         for (int c = 0; c < D; ++c) ynext[c] = (jj < N && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
     };
-    load_y(lane);
-    if (!top && lane < N) tnext = __ldcv(hprev + lane);
+    load_y(s_begin + lane);
+    if (!top && s_begin + lane < N) tnext = __ldcv(hprev + s_begin + lane);
 
-    const int steps = N + 31;
-    for (int s = 0; s < steps; ++s) {
-        if ((s & 31) == 0 && s < N) {
+    for (int s = s_begin; s < s_end; ++s) {
+        if ((s & 31) == 0 && s <= jhi) {
             const int jj = s + lane;
 #pragma unroll
             for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
             if (!top) {
+                const bool need = jj >= jtop_lo && jj <= jtop_hi;
                 float t = tnext;
-                const bool ok = wait_filled(jj < N && isnan(t), [&]() { t = __ldcv(hprev + jj); return isnan(t); },
+                const bool ok = wait_filled(need && isnan(t), [&]() { t = __ldcv(hprev + jj); return isnan(t); },
                                             p.hdr, 3, p.spin_limit);
                 if (!ok) return;
-                topv = jj < N ? t : INF;
+                topv = need ? t : INF;
                 tnext = jj + 32 < N ? __ldcv(hprev + jj + 32) : INF;
             }
             load_y(jj + 32);
@@ -174,7 +191,15 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
         prev_up = up_in;
 
         const int j = s - lane;
-        if (j >= 0 && j < N) {
+        // the lane's column; MASK: only rows k in [klo, khi] lie in the band
+        auto column = [&](auto mask) {
+            constexpr bool MASK = decltype(mask)::value;
+            int klo = 0, khi = R - 1;
+            if (MASK) {
+                const int64_t jm = (int64_t)j * M;
+                klo = (int)max((int64_t)-1, ceil_div64(jm - bnd, N) - i0);
+                khi = (int)min((int64_t)R, floor_div64(jm + bnd, N) - i0);
+            }
             float dg = dg_in, up = up_in;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -187,11 +212,18 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
                 const float du = __fsub_rn(up, m2);
                 const float z = ex2a(__fmul_rn(-fabsf(du), kk));
                 const float S = du >= 0.f ? __fadd_rn(S2, z) : __fmaf_rn(S2, z, 1.f);
-                const float r = __fmaf_rn(-gl, lg2a(S), __fadd_rn(delta, fminf(m2, up)));
+                float r = __fmaf_rn(-gl, lg2a(S), __fadd_rn(delta, fminf(m2, up)));
+                if (MASK && (k < klo || k > khi)) r = INF;      // outside the band
                 dg = lf;
                 up = r;
                 col[k] = r;
             }
+        };
+        if (j >= jlo && j <= jhi) {
+            if (BANDED && (j < full_lo || j > full_hi))
+                column(std::true_type{});
+            else
+                column(std::false_type{});
             if (hcur != nullptr && lane == 31) __stcg(hcur + j, col[R - 1]);
         }
         if (rs != nullptr) {
@@ -215,7 +247,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     }
 }
 
-template <int D, int R>
+template <int D, int R, bool BANDED>
 __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring)
 {
     constexpr int BR = 32 * R;
@@ -252,14 +284,31 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
     const float* rs = p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R;
 
+    // Sakoe-Chiba band: the band's columns [jlo, jhi], the row below's
+    // [jbot_lo, jbot_hi] (the only columns its producer waits for here), the
+    // lane's columns with every row inside.  Lane t is at column
+    // N-1-s+(31-t): steps from a multiple of 32 at or before the step where
+    // lane 31 is one column right of jhi (its first below-right value), to the
+    // step where lane 0 reaches jlo.
+    const int64_t bnd = BANDED ? pd.band_bound : -1;
+    int jlo = 0, jhi = N - 1, jbot_lo = 0, jbot_hi = N - 1, full_lo = 0, full_hi = N - 1;
+    if (BANDED) {
+        const int64_t r0 = (int64_t)band * BR, r1 = min(r0 + BR, (int64_t)M) - 1;
+        jlo = band_lo(r0, bnd, M, N);
+        jhi = band_hi(r1, bnd, M, N);
+        if (!last) { jbot_lo = band_lo(r1 + 1, bnd, M, N); jbot_hi = band_hi(r1 + 1, bnd, M, N); }
+        if (i0 < M) { full_lo = band_lo(min(i0 + R - 1, M - 1), bnd, M, N); full_hi = band_hi(i0, bnd, M, N); }
+    }
+    const int s_begin = BANDED ? max(0, (N - 2 - jhi) & ~31) : 0;
+    const int steps = BANDED ? N + 31 - jlo : N + 31;
+
     // R of this lane's rows at the column of step ss (written by forward step
     // N+30-ss) is copied into ring slot ss mod kRPre kRPre steps ahead of its
     // use (one commit group per step, empty past the end), so that a step's
     // wait covers the copies issued kRPre steps earlier
-    const int steps = N + 31;
     auto issue_r = [&](int ss) {
         const int jj = N - 1 - ss + (31 - lane);
-        if (ss < steps && jj >= 0 && jj < N) {
+        if (ss < steps && jj >= jlo && jj <= jhi) {
             const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - ss) * 32 * R);
             float4* dst = ring + (ss & (kRPre - 1)) * (R / 4) * 32;
 #pragma unroll
@@ -268,7 +317,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         cp_async_commit();
     };
 #pragma unroll 1
-    for (int ss = 0; ss < kRPre; ++ss) issue_r(ss);
+    for (int ss = s_begin; ss < s_begin + kRPre; ++ss) issue_r(ss);
     // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l
     float ynext[D];
     u64 wa = 0, wb = 0;
@@ -279,10 +328,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     auto load_e = [&](int jj) {
         if (jj >= 0) { wa = __ldcv(enext + 2 * jj); wb = __ldcv(enext + 2 * jj + 1); }
     };
-    load_y(N - 1 - lane);
-    if (!last) load_e(N - 1 - lane);
+    load_y(N - 1 - s_begin - lane);
+    if (!last) load_e(N - 1 - s_begin - lane);
 
-    for (int s = 0; s < steps; ++s) {
+    for (int s = s_begin; s < steps; ++s) {
         float4 rcur[R / 4];
         cp_async_wait<kRPre - 1>();
 #pragma unroll
@@ -292,14 +341,16 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 #pragma unroll
             for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
             if (!last) {
-                const bool ok = wait_filled(jj >= 0 && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
+                // only the row below's columns inside the band are written (and waited for)
+                const bool need = jj >= jbot_lo && jj <= jbot_hi;
+                const bool ok = wait_filled(need && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
                                             [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
                                             p.hdr, 4, p.spin_limit);
                 if (!ok) {
                     cp_async_wait<0>();
                     return;
                 }
-                if (jj >= 0) {
+                if (need) {
                     cr = __uint_as_float((uint32_t)wa);
                     cd = __uint_as_float((uint32_t)(wa >> 32));
                     ce = __uint_as_float((uint32_t)wb);
@@ -337,6 +388,13 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         // last rows, and only at column N-1, take that path)
         auto column = [&](auto checked) {
             constexpr bool CHECKED = decltype(checked)::value;
+            // checked with a band: only rows k in [klo, khi] lie in the band
+            int klo = 0, khi = R - 1;
+            if (CHECKED && BANDED) {
+                const int64_t jm = (int64_t)j * M;
+                klo = (int)max((int64_t)-1, ceil_div64(jm - bnd, N) - i0);
+                khi = (int)min((int64_t)R, floor_div64(jm + bnd, N) - i0);
+            }
             float nr = br, nd = bd, ne = be;       // below, column j
 #pragma unroll
             for (int k4 = R / 4 - 1; k4 >= 0; --k4) {
@@ -347,7 +405,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                     const int k = 4 * k4 + kq;
                     const float rr = rp[k], rd = dp[k], re = ep[k];
                     float rn = NINF, dn = 0.f, en = 0.f;
-                    if (!CHECKED || i0 + k < M) {
+                    if (!CHECKED || (i0 + k < M && k >= klo && k <= khi)) {
                         const float r = rv[kq];
                         float t[D];
                         const float delta = local_cost<D>(b[k], y, t);
@@ -371,8 +429,8 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 }
             }
         };
-        if (j >= 0 && j < N) {
-            if (edge && (i0 + R > M || j == N - 1))
+        if (j >= jlo && j <= jhi) {
+            if ((edge && (i0 + R > M || j == N - 1)) || (BANDED && (j < full_lo || j > full_hi)))
                 column(std::true_type{});
             else
                 column(std::false_type{});
@@ -395,7 +453,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 if (c < d) gout[(int64_t)(i0 + k) * d + c] = __fmul_rn(2.f, g[k][c]);
 }
 
-template <int D, int R, bool BWD>
+template <int D, int R, bool BWD, bool BANDED>
 __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
 {
     extern __shared__ float4 rring_all[];
@@ -407,7 +465,13 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
         if (item >= p.n_items) break;
         if (ld_volatile(&p.hdr->abort)) break;
         int q, k;
-        if (p.band_cnt > 0) {                 // a band range of every pair
+        if (BANDED) {
+            // band-major (every pair's k-th band, then k + 1): under a band a
+            // pair has few bands ready at a time; band k - 1 of a pair is always
+            // earlier in the list.  Every pair has the same bands (one prototype).
+            q = item % p.P;
+            k = item / p.P;
+        } else if (p.band_cnt > 0) {          // a band range of every pair
             q = item / p.band_cnt;
             k = item % p.band_cnt;
         } else {
@@ -417,10 +481,10 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
         const PairDesc pd = p.pairs[p.order[q]];
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
-            bwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane,
+            bwd_band<D, R, BANDED>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane,
                            rring_all + (threadIdx.x >> 5) * kRPre * (R / 4) * 32);
         } else {
-            fwd_band<D, R>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
+            fwd_band<D, R, BANDED>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
         }
     }
 }
@@ -452,25 +516,37 @@ __global__ void adam_kernel(float* x, const float* grad, float* m, float* v, int
     x[i] = __fsub_rn(x[i], __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(sqrtf(vh), eps)));
 }
 
-template <int D, bool BWD>
-cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
+template <int D, bool BWD, bool BANDED>
+cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
     const size_t smem = BWD ? rring_bytes<R>(block) : 0;
-    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    softdtw_kernel<D, R, BWD><<<grid, block, smem, st>>>(p);
+    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    softdtw_kernel<D, R, BWD, BANDED><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 template <int D, bool BWD>
-int occ_d(int block)
+cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
+{
+    return p.banded ? launch_db<D, BWD, true>(p, grid, block, st) : launch_db<D, BWD, false>(p, grid, block, st);
+}
+
+template <int D, bool BWD, bool BANDED>
+int occ_db(int block)
 {
     constexpr int R = 8;
     const size_t smem = BWD ? rring_bytes<R>(block) : 0;
     int n = 0;
-    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD>, block, smem);
+    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD, BANDED>, block, smem);
     return n;
+}
+
+template <int D, bool BWD>
+int occ_d(int block, int banded)
+{
+    return banded ? occ_db<D, BWD, true>(block) : occ_db<D, BWD, false>(block);
 }
 
 }  // namespace
@@ -498,12 +574,12 @@ cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, 
     return cudaErrorInvalidValue;
 }
 
-int softdtw_max_blocks_per_sm(int D, int backward, int block)
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded)
 {
     if (backward) {
-        WTS_SOFT_DISPATCH(occ_d, true, block)
+        WTS_SOFT_DISPATCH(occ_d, true, block, banded)
     } else {
-        WTS_SOFT_DISPATCH(occ_d, false, block)
+        WTS_SOFT_DISPATCH(occ_d, false, block, banded)
     }
     return 0;
 }

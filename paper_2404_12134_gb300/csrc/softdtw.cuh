@@ -29,6 +29,7 @@ struct SoftParams {
     int band_lo, band_cnt;
     long long spin_limit;    // polls before a wait gives up
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
+    int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
 };
 
 // Rows held per lane by the soft-DTW kernels for a padded channel count D.
@@ -36,7 +37,7 @@ inline int soft_rows(int D) { return 8; }
 
 cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
-int softdtw_max_blocks_per_sm(int D, int backward, int block);
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0);
 
 // grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending)
 cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, int T, int64_t M, int d,

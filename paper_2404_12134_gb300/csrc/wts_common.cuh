@@ -88,6 +88,21 @@ __device__ __forceinline__ bool wait_filled(bool missing, Reload reload, WsHeade
     }
 }
 
+// floor(a / b) and ceil(a / b) for b > 0 and any sign of a
+__device__ __forceinline__ int64_t floor_div64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int64_t ceil_div64(int64_t a, int64_t b) { return -floor_div64(-a, b); }
+
+// Sakoe-Chiba band of an M x N pair with bound bnd: row i keeps the columns
+// [band_lo(i), band_hi(i)] (clipped to the matrix), both nondecreasing in i.
+__device__ __forceinline__ int band_lo(int64_t i, int64_t bnd, int M, int N)
+{
+    return (int)max((int64_t)0, ceil_div64(i * N - bnd, M));
+}
+__device__ __forceinline__ int band_hi(int64_t i, int64_t bnd, int M, int N)
+{
+    return (int)min((int64_t)N - 1, floor_div64(i * N + bnd, M));
+}
+
 // Work list: items are (pair, band) in the order pairs[order[0]], bands 0..,
 // pairs[order[1]], ...; prefix[q] = first item of the q-th pair in that order.
 __device__ __forceinline__ int find_slot(const int32_t* prefix, int n, int item)

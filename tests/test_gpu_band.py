@@ -91,3 +91,26 @@ def test_band_full_size_sampled(wts):
         r = oracle.dtw(Bh, b.cycle(k), "f32", path=False, band=0.6)
         assert cost[k] == r["cost"] and plen[k] == r["plen"], k
         assert (jlo[k] == r["jlo"]).all() and (jhi[k] == r["jhi"]).all(), k
+
+
+def test_band_first_column_on_a_chunk_boundary(wts):
+    """A row band whose first column is a multiple of 32 (M = N = 1100,
+    w = 0.0295: row 512 starts at column 480, row 511 at 479) with a cycle that
+    is the prototype shifted by 32 samples, so the optimal path runs along the
+    band's left edge through (511, 479) -> (512, 480): the band's first cell
+    takes its diagonal from the row above one column before the band starts."""
+    M = N = 1100
+    w = 0.0295
+    assert math.ceil((512 * N - math.floor(w * M * N)) / M) == 480
+    for seed in (5, 6):
+        rng = np.random.default_rng(seed)
+        B = rng.normal(size=(M, 2)).astype(np.float32)
+        y = np.concatenate([B[32:], rng.normal(size=(32, 2)).astype(np.float32)])
+        data, offs = _pack([y])
+        gb = wts.Batch.from_numpy(data, offs)
+        cost, plen, jlo, jhi = (t.cpu().numpy() for t in wts.dtw_align(torch.from_numpy(B).cuda(), gb,
+                                                                         wts.options(band=w)))
+        r = oracle.dtw(B, y, "f32", band=w)
+        assert r["jlo"][512] == 480 and r["jhi"][511] == 479
+        assert cost[0] == r["cost"] and plen[0] == r["plen"]
+        assert (jlo[0] == r["jlo"]).all() and (jhi[0] == r["jhi"]).all()

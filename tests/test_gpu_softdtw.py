@@ -186,3 +186,49 @@ def test_lbfgs_barycenter_matches_oracle(wts):
     _, fg, _ = oracle.softdtw_batch(Bg.cpu().numpy(), b.data, b.offsets, 1.0, weights=w, prec="f64")
     assert fg < f0 and fo < f0
     assert abs(fg - fo) <= 1e-3 * abs(fo), (fg, fo, it, ito)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.1])
+@pytest.mark.parametrize("case,w", [((7, 300, [310, 200, 520], 1), 0.15), ((8, 520, [700, 260], 2), 0.3),
+                                    ((9, 260, [260, 33], 3), 0.6)])
+def test_banded_softdtw_value_and_gradient(wts, case, w, gamma):
+    """Soft-DTW with Table I's Sakoe-Chiba band: values within the value bar
+    of the FP64 oracle (restricted to in-band paths), gradients within the
+    plain-FP32 bar; several row bands, M < N and M > N."""
+    seed, M, lens, d = case
+    B, b = _case(seed, M, lens, d)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    o = wts.options(band=w)
+    ws = wts.Workspace()
+    v = wts.softdtw_forward(Bt, gb, gamma, o, ws=ws)
+    wt = torch.from_numpy((1.0 / np.asarray(lens)).astype(np.float32)).cuda()
+    g = wts.softdtw_backward(Bt, gb, gamma, wt, o, ws=ws)
+    assert wts.read_status(ws.buf) == 0
+    wd = 1.0 / np.asarray(lens, dtype=np.float64)
+    vo, lo, go = oracle.softdtw_batch(B, b.data, b.offsets, gamma, weights=wd, band=w)
+    vg = v.cpu().numpy().astype(np.float64)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(vg - vo) <= VALUE_TOL * np.maximum(np.abs(vo), 1.0)), np.abs(vg - vo).max()
+    g32 = oracle.softdtw_batch(B, b.data, b.offsets, gamma, weights=wd.astype(np.float32), prec="f32", band=w)[2]
+    bar = 2.0 * np.abs(g32.astype(np.float64) - go).max() / np.abs(go).max() + 1e-5
+    assert np.abs(gg - go).max() / np.abs(go).max() <= bar
+    # checkpointed R (recomputed per group of bands): the same gradient
+    oc = wts.options(band=w, dir_mode=1, ckpt_bands=1)
+    wts.softdtw_forward(Bt, gb, gamma, oc, ws=ws)
+    gc = wts.softdtw_backward(Bt, gb, gamma, wt, oc, ws=ws)
+    assert torch.equal(gc, g)
+
+
+def test_banded_lbfgs_barycenter(wts):
+    """Table I's full setting at small size: band 0.6, gamma 1, L-BFGS; the
+    reached objective within 1e-3 of the oracle's (FP64, in-band paths)."""
+    b = synth.config_batch(2, scale=0.008, T=5)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M = 60
+    B0 = wts.euclid_mean(gb, M)
+    Bg, f, it, ev, why = wts.softdtw_barycenter_lbfgs(gb, M, 1.0, init=B0, opts=wts.options(band=0.6))
+    w = (1.0 / b.lengths).astype(np.float32)
+    _, fg, _ = oracle.softdtw_batch(Bg.cpu().numpy(), b.data, b.offsets, 1.0, weights=w, prec="f64", band=0.6)
+    Bo, fo, ito, evo, whyo = oracle.softdtw_barycenter_lbfgs(b.data, b.offsets, B0.cpu().numpy(), 1.0, band=0.6)
+    assert abs(fg - fo) <= 1e-3 * abs(fo), (fg, fo)
