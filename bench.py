@@ -192,9 +192,12 @@ def hbm_peak_gbs() -> float:
         return 6800.0
 
 
-def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None, ckpt: bool = False):
+def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None, ckpt: bool = False,
+                band: float = 0.0):
     """Soft-DTW forward + backward on the single-channel barycenter workload:
-    64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB)."""
+    64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB);
+    band > 0: with the Sakoe-Chiba band (GCUPS then also over the cells in
+    the band)."""
     sb = synth.config_batch(2, T=T)
     M = synth.PROTO_LEN[2]
     gb = api.Batch.from_numpy(sb.data, sb.offsets, device=dev)
@@ -202,7 +205,7 @@ def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None 
     w = torch.from_numpy((1.0 / sb.lengths).astype(np.float32)).to(dev)
     ws = api.Workspace(dev)
     grad = torch.empty_like(B)
-    opt = api.options(dir_mode=1, ckpt_bands=1 << 20) if ckpt else None
+    opt = api.options(dir_mode=1, ckpt_bands=1 << 20, band=band) if ckpt else (api.options(band=band) if band else None)
     for _ in range(2):
         api.softdtw_forward(B, gb, gamma, opt, ws=ws)
         api.softdtw_backward(B, gb, gamma, w, opt, ws=ws, grad_B=grad)
@@ -227,6 +230,9 @@ def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None 
            "fwd_gcups": cells / (fwd * 1e-3) / 1e9, "bwd_gcups": cells / (bwd * 1e-3) / 1e9,
            "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf),
            "loss": float((vals * w).sum())}
+    if band:
+        inb = band_cells(M, sb.lengths, band)
+        res.update(band=band, cells_in_band=inb, fwd_bwd_gcups_in_band=inb / ((fwd + bwd) * 1e-3) / 1e9)
     del ws, gb
     return res
 
@@ -406,6 +412,12 @@ def bary_leg(api, torch, dev, barrier, gammas=(1.0, 0.1, 0.01), steps: int = 50,
         el = time.perf_counter() - t0
         res[f"softdtw_barycenter_lbfgs_gamma_{gamma:g}"] = dict(quality(Bl), iterations=it, evaluations=ev,
                                                                 stop=why, objective_last=f, seconds=el)
+    # Table I's whole setting: gamma 1, Sakoe-Chiba band 0.6, L-BFGS
+    t0 = time.perf_counter()
+    Bl, f, it, ev, why = api.softdtw_barycenter_lbfgs(gb, M, 1.0, init=B0, opts=api.options(band=0.6))
+    barrier()
+    res["softdtw_barycenter_lbfgs_gamma_1_band_0.6"] = dict(quality(Bl), iterations=it, evaluations=ev, stop=why,
+                                                            objective_last=f, seconds=time.perf_counter() - t0)
     del ws
     return res
 
@@ -804,6 +816,7 @@ def run_gpu(args):
     if not args.no_extras:
         out["scoring"] = scoring_leg(api, torch, dev, barrier)
         out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
+        out["softdtw_band_0.6"] = softdtw_leg(api, torch, dev, st, barrier, band=0.6)
         out["barycenters"] = bary_leg(api, torch, dev, barrier)
         out["segmentation"] = segment_leg(api, torch, dev, barrier)
         out["banded_dba"] = banded_dba_leg(api, torch, dev, barrier, gb, b, B0)
