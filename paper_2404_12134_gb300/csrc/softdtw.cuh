@@ -32,8 +32,9 @@ struct SoftParams {
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
 };
 
-// Rows held per lane by the soft-DTW kernels for a padded channel count D.
-inline int soft_rows(int D) { return 8; }
+// Rows held per lane by the soft-DTW kernels (8 for every padded channel
+// count: measured best against 4 and 16).
+inline int soft_rows(int /*D*/) { return 8; }
 
 cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
