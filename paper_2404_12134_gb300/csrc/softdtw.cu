@@ -161,6 +161,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     load_y(s_begin + lane);
     if (!top && s_begin + lane < N) tnext = __ldcv(hprev + s_begin + lane);
 
+#pragma unroll 2
     for (int s = s_begin; s < s_end; ++s) {
         if ((s & 31) == 0 && s <= jhi) {
             const int jj = s + lane;
@@ -331,6 +332,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     load_y(N - 1 - s_begin - lane);
     if (!last) load_e(N - 1 - s_begin - lane);
 
+#pragma unroll 2
     for (int s = s_begin; s < steps; ++s) {
         float4 rcur[R / 4];
         cp_async_wait<kRPre - 1>();
