@@ -43,9 +43,9 @@ FP32_LANES_PER_SM = 128
 WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1582 + 5.6421) * 1e9 / 2.2029e10
 # DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
 # ncu capture of both kernels on 8 cycles of the soft-DTW workload
-# (profiles/softdtw_fwd_bwd_8x10k_d1.md): (0.0132 + 3.2475 + 3.3412 + 0.0526)e9
+# (profiles/softdtw_fwd_bwd_8x10k_d1.md): (0.0120 + 3.2474 + 3.3395 + 0.0522)e9
 # bytes / 8.0226e8 cells (stored R plus hand-off rows, in proportion to cells).
-SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0132 + 3.2475 + 3.3412 + 0.0526) * 1e9 / 8.0226e8
+SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0120 + 3.2474 + 3.3395 + 0.0522) * 1e9 / 8.0226e8
 
 
 def parse():
