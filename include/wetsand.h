@@ -200,8 +200,11 @@ int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_option
  *                                       than max_segments, the first
  *                                       max_segments are stored and
  *                                       WTS_ENOMEM is returned
- * Each window is one subdtw_align call; the window's bounds are read back
- * before the next (the stream is synchronised once per window).  A window is
+ * Each window runs the Sub-DTW wavefront on `stream`; its b* is read back
+ * (the stream is synchronised once per window) and its backtrack (a*) runs on
+ * a second stream of the library's, beside the next window's wavefront; the
+ * workspace holds two window slots.  On return `stream` is ordered after all
+ * of the call's work.  A window is
  * a single pair, so rows_per_thread = 0 means 8 here (twice the warps of 16,
  * half the serial chain per step).  Workspace: wts_segment_workspace_size
  * (with the same options).

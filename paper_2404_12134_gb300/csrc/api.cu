@@ -585,23 +585,26 @@ int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* 
     return ok();
 }
 
-int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_options* opt,
-                 void* workspace, size_t workspace_bytes, void* stream,
-                 float* cost, int32_t* a_star, int32_t* b_star, int32_t* plen, int32_t* jlo, int32_t* jhi)
+namespace {
+
+// Sub-DTW in two halves: the wavefront (cost, b*) and the backtrack (a*, the
+// path), so that the segmentation loop can overlap a window's backtrack with
+// the next window's wavefront.
+int subdtw_dp_part(const Layout& L, char* ws, const float* X, const wts_batch* Y, const wts_options* opt,
+                   cudaStream_t st, float* cost, int32_t* b_star)
 {
-    Layout L;
-    int rc = compute_layout(kOpSubdtw, M, Y, opt, &L);
+    int rc = prepare(L, ws, X, Y, opt, st);
     if (rc) return rc;
-    if ((rc = check_batch(Y, true))) return rc;
-    if (!X || !a_star || !b_star || !jlo || !jhi) return fail(WTS_EINVAL, "X, a_star, b_star, jlo and jhi must not be NULL");
-    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
-    char* ws = (char*)workspace;
-    cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = prepare(L, ws, X, Y, opt, st))) return rc;
     DPParams p = base_params(L, ws, opt);
     p.cost_out = cost;
     p.bstar_out = b_star;
-    if ((rc = launch_dp(kModeSubDirs, L, p, opt, st))) return rc;
+    return launch_dp(kModeSubDirs, L, p, opt, st);
+}
+
+int subdtw_bt_part(const Layout& L, char* ws, const wts_options* opt, cudaStream_t st, const int32_t* b_star,
+                   int32_t* a_star, int32_t* plen, int32_t* jlo, int32_t* jhi)
+{
+    const DPParams p = base_params(L, ws, opt);
     BTParams bt{};
     bt.pairs = p.pairs;
     bt.P = L.P;
@@ -622,6 +625,25 @@ int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_option
         e = launch_backtrack(bt, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
+    return WTS_OK;
+}
+
+}  // namespace
+
+int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_options* opt,
+                 void* workspace, size_t workspace_bytes, void* stream,
+                 float* cost, int32_t* a_star, int32_t* b_star, int32_t* plen, int32_t* jlo, int32_t* jhi)
+{
+    Layout L;
+    int rc = compute_layout(kOpSubdtw, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if (!X || !a_star || !b_star || !jlo || !jhi) return fail(WTS_EINVAL, "X, a_star, b_star, jlo and jhi must not be NULL");
+    if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = subdtw_dp_part(L, ws, X, Y, opt, st, cost, b_star))) return rc;
+    if ((rc = subdtw_bt_part(L, ws, opt, st, b_star, a_star, plen, jlo, jhi))) return rc;
     return ok();
 }
 
@@ -673,10 +695,31 @@ int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, siz
     const wts_options o = segment_options(opt);
     int rc = segment_layout(M, d, &o, &S);
     if (rc) return rc;
-    *bytes = S.total;
+    *bytes = 2 * S.total;                  // two window slots (see wts_segment)
     return ok();
 }
 
+namespace {
+
+struct SegStreams {
+    cudaStream_t bt = nullptr;
+    cudaEvent_t dp_done = nullptr, freed[2] = {nullptr, nullptr};
+    ~SegStreams()
+    {
+        if (bt) cudaStreamSynchronize(bt);
+        if (dp_done) cudaEventDestroy(dp_done);
+        for (cudaEvent_t& e : freed)
+            if (e) cudaEventDestroy(e);
+        if (bt) cudaStreamDestroy(bt);
+    }
+};
+
+}  // namespace
+
+// Windows alternate between two workspace slots.  A window's wavefront runs on
+// the caller's stream; once its b* is read back (it sets the next window), its
+// backtrack runs on a second stream while the next window's wavefront starts
+// on the first; a slot is reused only after its backtrack has finished.
 int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_t d, int64_t alpha,
                 const wts_options* opt, void* workspace, size_t workspace_bytes, void* stream,
                 int32_t max_segments, int64_t* seg_start, int64_t* seg_end, float* seg_cost, int32_t* n_segments)
@@ -692,49 +735,96 @@ int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_
     int rc = segment_layout(M, d, opt, &S);
     if (rc) return rc;
     if (!workspace || ((uintptr_t)workspace & 255) != 0) return fail(WTS_EINVAL, "workspace must be 256-byte aligned");
-    if (workspace_bytes < S.total) return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, S.total);
-    char* ws = (char*)workspace;
+    if (workspace_bytes < 2 * S.total)
+        return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, 2 * S.total);
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t* d_offs = reinterpret_cast<int64_t*>(ws + S.off_offsets);
-    float* d_cost = reinterpret_cast<float*>(ws + S.off_cost);
-    int32_t* d_ab = reinterpret_cast<int32_t*>(ws + S.off_ab);
+    SegStreams ss;
+    cudaError_t e = cudaStreamCreateWithFlags(&ss.bt, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss.dp_done, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ss.freed[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "segmentation stream / events");
+    // the backtrack stream starts after everything already queued on the caller's stream
+    if ((e = cudaEventRecord(ss.dp_done, st)) != cudaSuccess || (e = cudaStreamWaitEvent(ss.bt, ss.dp_done, 0)) != cudaSuccess)
+        return cuda_fail(e, "segmentation stream order");
+
+    int64_t offs[2][2];
     int32_t found = 0;
     int64_t pos = 0;
-    while (pos < N) {
+    // the window whose backtrack is in flight: its slot, start, b*, cost
+    int prev_slot = -1;
+    int64_t prev_pos = 0;
+    int32_t prev_b = 0;
+    float prev_cost = 0.f;
+    auto finish_prev = [&]() -> int {
+        char* base = (char*)workspace + (size_t)prev_slot * S.total;
+        int32_t a = -1;
+        cudaError_t e2 = cudaEventSynchronize(ss.freed[prev_slot]);
+        if (e2 == cudaSuccess) e2 = cudaMemcpy(&a, base + S.off_ab, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "window start read-back");
+        if (a < 0 || a > prev_b) return fail(WTS_ECUDA, "window at %lld gave an invalid piece [%d, %d]",
+                                             (long long)prev_pos, a, prev_b);
+        if (found < max_segments) {
+            seg_start[found] = prev_pos + a;
+            seg_end[found] = prev_pos + prev_b;
+            if (seg_cost) seg_cost[found] = prev_cost;
+        }
+        ++found;
+        return WTS_OK;
+    };
+    for (int64_t k = 0; pos < N; ++k) {
+        const int slot = (int)(k & 1);
+        char* base = (char*)workspace + (size_t)slot * S.total;
         const int64_t n = (pos + 2 * M < N ? pos + 2 * M : N) - pos;
-        int64_t offs[2] = {0, n};
-        cudaError_t e = cudaMemcpyAsync(d_offs, offs, sizeof(offs), cudaMemcpyHostToDevice, st);
+        int64_t* d_offs = reinterpret_cast<int64_t*>(base + S.off_offsets);
+        float* d_cost = reinterpret_cast<float*>(base + S.off_cost);
+        int32_t* d_ab = reinterpret_cast<int32_t*>(base + S.off_ab);
+        if (k >= 2 && (e = cudaStreamWaitEvent(st, ss.freed[slot], 0)) != cudaSuccess)
+            return cuda_fail(e, "slot reuse order");
+        offs[slot][0] = 0;
+        offs[slot][1] = n;
+        e = cudaMemcpyAsync(d_offs, offs[slot], sizeof(offs[slot]), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "window offsets copy");
         wts_batch b{};
         b.data = Ydata + pos * d;
         b.offsets = d_offs;
-        b.offsets_host = offs;
+        b.offsets_host = offs[slot];
         b.T = 1;
         b.d = d;
-        rc = subdtw_align(X, M, &b, opt, ws, S.L.total, stream, d_cost, d_ab, d_ab + 1, d_ab + 2,
-                          reinterpret_cast<int32_t*>(ws + S.off_jlo), reinterpret_cast<int32_t*>(ws + S.off_jhi));
-        if (rc) return rc;
-        int32_t ab[3];
+        Layout L;
+        if ((rc = compute_layout(kOpSubdtw, M, &b, opt, &L))) return rc;
+        if ((rc = check_batch(&b, true))) return rc;
+        if ((rc = subdtw_dp_part(L, base, X, &b, opt, st, d_cost, d_ab + 1))) return rc;
+        int32_t bstar = 0;
         float c = 0.f;
         WsHeader h;
-        e = cudaMemcpyAsync(ab, d_ab, sizeof(ab), cudaMemcpyDeviceToHost, st);
+        e = cudaEventRecord(ss.dp_done, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bstar, d_ab + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&c, d_cost, sizeof(float), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ws + S.L.off_hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, base + L.off_hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "window result read-back");
         if (h.status == kDevTimeout) return fail(WTS_ETIMEOUT, "a wait in the window at %lld gave up", (long long)pos);
-        if (ab[0] < 0 || ab[1] < ab[0] || ab[1] >= n)
-            return fail(WTS_ECUDA, "window at %lld gave an invalid piece [%d, %d]", (long long)pos, ab[0], ab[1]);
-        if (found < max_segments) {
-            seg_start[found] = pos + ab[0];
-            seg_end[found] = pos + ab[1];
-            if (seg_cost) seg_cost[found] = c;
-        }
-        ++found;
+        if (bstar < 0 || bstar >= n) return fail(WTS_ECUDA, "window at %lld gave an invalid end %d", (long long)pos, bstar);
+        // backtrack of this window on the second stream, after its wavefront
+        if ((e = cudaStreamWaitEvent(ss.bt, ss.dp_done, 0)) != cudaSuccess) return cuda_fail(e, "backtrack order");
+        if ((rc = subdtw_bt_part(L, base, opt, ss.bt, d_ab + 1, d_ab, d_ab + 2,
+                                 reinterpret_cast<int32_t*>(base + S.off_jlo),
+                                 reinterpret_cast<int32_t*>(base + S.off_jhi)))) return rc;
+        if ((e = cudaEventRecord(ss.freed[slot], ss.bt)) != cudaSuccess) return cuda_fail(e, "backtrack event");
+        // the previous window's backtrack ran beside this window's wavefront
+        if (prev_slot >= 0 && (rc = finish_prev())) return rc;
+        prev_slot = slot;
+        prev_pos = pos;
+        prev_b = bstar;
+        prev_cost = c;
         if (pos + n == N) break;                      // this window reached the end of Y
-        const int64_t next = pos + ab[1] - alpha;
-        pos = next > pos ? next : pos + ab[1] + 1;
+        const int64_t next = pos + bstar - alpha;
+        pos = next > pos ? next : pos + bstar + 1;
     }
+    if (prev_slot >= 0 && (rc = finish_prev())) return rc;
+    // later work on the caller's stream follows the last backtrack
+    if ((e = cudaEventRecord(ss.dp_done, ss.bt)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ss.dp_done, 0)) != cudaSuccess)
+        return cuda_fail(e, "segmentation stream order");
     *n_segments = found;
     if (found > max_segments) return fail(WTS_ENOMEM, "%d pieces found, room for %d", found, max_segments);
     return ok();

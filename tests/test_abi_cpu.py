@@ -131,8 +131,8 @@ def test_subdtw_workspace_and_validation(lib):
     assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == _abi.WTS_EINVAL
     n = ctypes.c_size_t(0)
     assert lib.wts_segment_workspace_size(16300, 9, None, ctypes.byref(n)) == 0
-    # one window of 2M columns: about M * 2M / 4 bytes of codes
-    assert 16300 * 32600 / 4 <= n.value <= 16300 * 32600 / 4 * 1.2
+    # two window slots of 2M columns: about 2 * M * 2M / 4 bytes of codes
+    assert 2 * 16300 * 32600 / 4 <= n.value <= 2 * 16300 * 32600 / 4 * 1.2
     assert lib.wts_segment_workspace_size(0, 9, None, ctypes.byref(n)) == _abi.WTS_EINVAL
 
 
