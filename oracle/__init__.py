@@ -81,23 +81,26 @@ def _lib(defines: tuple = ()):
         for p, R, Rp in (("f64", ctypes.c_double, f64p), ("f32", ctypes.c_float, f32p)):
             fn = getattr(lib, f"orc_dtw_{p}")
             fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int,
-                           VP, VP, VP, VP, VP, VP, ctypes.c_double]
+                           VP, VP, VP, VP, VP, VP, ctypes.c_double, ctypes.c_int]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_score_{p}")
-            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double]
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double,
+                           ctypes.c_int]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_dba_{p}")
-            fn.argtypes = [Rp, Rp, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double]
+            fn.argtypes = [Rp, Rp, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, VP, VP, VP, ctypes.c_double,
+                           ctypes.c_int]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_softdtw_{p}")
-            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, R, VP, VP, VP, VP, ctypes.c_double]
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, R, VP, VP, VP, VP, ctypes.c_double,
+                           ctypes.c_int]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_softdtw_batch_{p}")
             fn.argtypes = [f32p, ctypes.c_int64, f32p, i64p, ctypes.c_int, ctypes.c_int, R, VP, VP, VP, VP,
-                           ctypes.c_double]
+                           ctypes.c_double, ctypes.c_int]
             fn.restype = ctypes.c_int
             fn = getattr(lib, f"orc_subdtw_{p}")
-            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, VP, VP, VP, VP, VP, VP]
+            fn.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int, VP, VP, VP, VP, VP, VP, ctypes.c_int]
             fn.restype = ctypes.c_int
         _libs[key] = lib
         return lib
@@ -120,11 +123,12 @@ def _as2d(x: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(x)
 
 
-def dtw(B, Y, prec: str = "f64", path: bool = True, band: float = 0.0, _defines: tuple = ()):
+def dtw(B, Y, prec: str = "f64", path: bool = True, band: float = 0.0, cost_kind: int = 0, _defines: tuple = ()):
     """DTW(B, Y) with its optimal path under the tie order diag > up > left.
 
     band > 0: Sakoe-Chiba band (Table I), cells with |i N - j M| > floor(band M N)
-    excluded.  Returns dict(cost, plen, jlo, jhi, path_i, path_j); rows index B."""
+    excluded.  cost_kind 0: squared l2 local cost; 1: the l2 norm (Sec. 3.2).
+    Returns dict(cost, plen, jlo, jhi, path_i, path_j); rows index B."""
     B = _as2d(B); Y = _as2d(Y)
     M, d = B.shape; N = Y.shape[0]
     assert Y.shape[1] == d and M >= 1 and N >= 1
@@ -135,7 +139,7 @@ def dtw(B, Y, prec: str = "f64", path: bool = True, band: float = 0.0, _defines:
     pi = np.zeros(M + N - 1, dtype=np.int32) if path else None
     pj = np.zeros(M + N - 1, dtype=np.int32) if path else None
     rc = getattr(_lib(_defines), f"orc_dtw_{prec}")(B, M, Y, N, d, _ptr(cost), _ptr(plen), _ptr(jlo), _ptr(jhi),
-                                                  _ptr(pi), _ptr(pj), band)
+                                                  _ptr(pi), _ptr(pj), band, cost_kind)
     if rc:
         raise RuntimeError(f"oracle dtw failed (rc={rc}: -1 allocation, -2 invalid choice matrix, "
                            f"-3 band narrower than max(M, N))")
@@ -146,7 +150,7 @@ def dtw(B, Y, prec: str = "f64", path: bool = True, band: float = 0.0, _defines:
     return out
 
 
-def subdtw(X, Y, prec: str = "f64", _defines: tuple = ()):
+def subdtw(X, Y, prec: str = "f64", cost_kind: int = 0, _defines: tuple = ()):
     """Sub-DTW(X, Y) (Sec. 3.2): min over a <= b of DTW(X, Y[a..b]).
 
     Returns dict(cost, a, b, plen, jlo, jhi): [a, b] is the matched piece of Y
@@ -160,13 +164,13 @@ def subdtw(X, Y, prec: str = "f64", _defines: tuple = ()):
     a = np.zeros(1, dtype=np.int32); b = np.zeros(1, dtype=np.int32); plen = np.zeros(1, dtype=np.int32)
     jlo = np.zeros(M, dtype=np.int32); jhi = np.zeros(M, dtype=np.int32)
     rc = getattr(_lib(_defines), f"orc_subdtw_{prec}")(X, M, Y, N, d, _ptr(cost), _ptr(a), _ptr(b), _ptr(plen),
-                                                     _ptr(jlo), _ptr(jhi))
+                                                     _ptr(jlo), _ptr(jhi), cost_kind)
     if rc:
         raise RuntimeError(f"oracle subdtw failed (rc={rc})")
     return dict(cost=cost[0], a=int(a[0]), b=int(b[0]), plen=int(plen[0]), jlo=jlo, jhi=jhi)
 
 
-def segment(X, Y, alpha: int, prec: str = "f32"):
+def segment(X, Y, alpha: int, prec: str = "f32", cost_kind: int = 0):
     """Segmentation of a long series Y into cycles matching X (Sec. 3.2): the
     window [ws, ws + 2M) (cut at the end of Y) is aligned by Sub-DTW, the piece
     [ws + a*, ws + b*] is kept, and the next window starts at ws + b* - alpha,
@@ -182,7 +186,7 @@ def segment(X, Y, alpha: int, prec: str = "f32"):
     ws = 0
     while ws < N:
         we = min(ws + 2 * M, N)
-        r = subdtw(X, Y[ws:we], prec)
+        r = subdtw(X, Y[ws:we], prec, cost_kind=cost_kind)
         a, b = ws + r["a"], ws + r["b"]
         out.append((a, b, r["cost"]))
         if we == N:
@@ -192,7 +196,7 @@ def segment(X, Y, alpha: int, prec: str = "f32"):
     return out
 
 
-def score(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines: tuple = ()):
+def score(B, data, offsets, prec: str = "f64", band: float = 0.0, cost_kind: int = 0, _defines: tuple = ()):
     """Similarity score Eq. 8 for each cycle of a packed batch: (score, cost, plen)."""
     B = _as2d(B); data = _as2d(data)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -200,13 +204,13 @@ def score(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines: tupl
     dt = _dt(prec)
     s = np.zeros(T, dtype=dt); c = np.zeros(T, dtype=dt); L = np.zeros(T, dtype=np.int32)
     rc = getattr(_lib(_defines), f"orc_score_{prec}")(B, B.shape[0], data, offsets, T, B.shape[1],
-                                                    _ptr(s), _ptr(c), _ptr(L), band)
+                                                    _ptr(s), _ptr(c), _ptr(L), band, cost_kind)
     if rc:
         raise RuntimeError("oracle score failed (allocation, or a band narrower than max(M, N))")
     return s, c, L
 
 
-def dba_iterate(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines: tuple = ()):
+def dba_iterate(B, data, offsets, prec: str = "f64", band: float = 0.0, cost_kind: int = 0, _defines: tuple = ()):
     """One DBA iteration: (B_new, counts, cost_before, per-cycle costs)."""
     dt = _dt(prec)
     B = np.ascontiguousarray(np.asarray(B, dtype=dt).reshape(len(B), -1))
@@ -219,16 +223,17 @@ def dba_iterate(B, data, offsets, prec: str = "f64", band: float = 0.0, _defines
     cb = np.zeros(1, dtype=np.float64)
     ck = np.zeros(T, dtype=dt)
     rc = getattr(_lib(_defines), f"orc_dba_{prec}")(B, Bo, M, data, offsets, T, d, _ptr(cnt), _ptr(cb), _ptr(ck),
-                                                  band)
+                                                  band, cost_kind)
     if rc:
         raise RuntimeError("oracle dba failed (allocation, or a band narrower than max(M, N))")
     return Bo, cnt, float(cb[0]), ck
 
 
 def softdtw(B, Y, gamma: float, prec: str = "f64", want_R=False, want_E=False, want_grad=True,
-            band: float = 0.0, _defines: tuple = ()):
+            band: float = 0.0, cost_kind: int = 0, _defines: tuple = ()):
     """Soft-DTW^gamma(B, Y), optionally R, E ((M+2) x (N+2), 1-based) and grad [M, d];
-    band > 0: only the complete paths inside the Sakoe-Chiba band (as in ``dtw``)."""
+    band > 0: only the complete paths inside the Sakoe-Chiba band (as in ``dtw``);
+    cost_kind as in ``dtw`` (1: the l2 norm, its gradient 0 where the norm is 0)."""
     B = _as2d(B); Y = _as2d(Y)
     M, d = B.shape; N = Y.shape[0]
     dt = _dt(prec)
@@ -237,7 +242,7 @@ def softdtw(B, Y, gamma: float, prec: str = "f64", want_R=False, want_E=False, w
     E = np.zeros((M + 2, N + 2), dtype=dt) if want_E else None
     g = np.zeros((M, d), dtype=dt) if want_grad else None
     rc = getattr(_lib(_defines), f"orc_softdtw_{prec}")(B, M, Y, N, d, gamma, _ptr(v), _ptr(R), _ptr(E), _ptr(g),
-                                                      band)
+                                                      band, cost_kind)
     if rc:
         raise ValueError("oracle softdtw failed (allocation, gamma <= 0 with a gradient requested, "
                          "or a band narrower than max(M, N))")
@@ -245,7 +250,7 @@ def softdtw(B, Y, gamma: float, prec: str = "f64", want_R=False, want_E=False, w
 
 
 def softdtw_batch(B, data, offsets, gamma: float, weights=None, prec: str = "f64", want_grad=True,
-                  band: float = 0.0, _defines: tuple = ()):
+                  band: float = 0.0, cost_kind: int = 0, _defines: tuple = ()):
     """Eq. 7 objective over a packed batch: (values[T], loss, grad[M, d] or None)."""
     B = _as2d(B); data = _as2d(data)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -257,7 +262,7 @@ def softdtw_batch(B, data, offsets, gamma: float, weights=None, prec: str = "f64
     loss = np.zeros(1, dtype=dt)
     g = np.zeros((M, d), dtype=dt) if want_grad else None
     rc = getattr(_lib(_defines), f"orc_softdtw_batch_{prec}")(B, M, data, offsets, T, d, gamma, _ptr(w),
-                                                            _ptr(vals), _ptr(loss), _ptr(g), band)
+                                                            _ptr(vals), _ptr(loss), _ptr(g), band, cost_kind)
     if rc:
         raise ValueError("oracle softdtw_batch failed")
     return vals, loss[0], g
@@ -265,7 +270,7 @@ def softdtw_batch(B, data, offsets, gamma: float, weights=None, prec: str = "f64
 
 # --- initial barycenters (Table I: Euclidean-mean init; DBA: medoid) ---------
 
-def medoid(data, offsets, subset=None):
+def medoid(data, offsets, subset=None, cost_kind: int = 0):
     """argmin_k sum_l DTW(Y_k, Y_l) over ``subset`` (default all); ties -> lowest k.
 
     Pairwise costs use the FP32 mirror (the same precision the GPU uses), the
@@ -278,7 +283,8 @@ def medoid(data, offsets, subset=None):
     for a in range(n):
         for b in range(a + 1, n):
             ka, kb = int(idx[a]), int(idx[b])
-            c = dtw(data[offsets[ka]:offsets[ka + 1]], data[offsets[kb]:offsets[kb + 1]], "f32", path=False)["cost"]
+            c = dtw(data[offsets[ka]:offsets[ka + 1]], data[offsets[kb]:offsets[kb + 1]], "f32", path=False,
+                    cost_kind=cost_kind)["cost"]
             C[a, b] = C[b, a] = c
     sums = np.zeros(n, dtype=np.float64)
     for a in range(n):
@@ -407,7 +413,7 @@ def lbfgs(fn, x0, history=10, max_iter=40, max_fun=200, gtol=1e-8, ftol=1e-5, c1
     return x, f, it, evals, why
 
 
-def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, band: float = 0.0, **params):
+def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, band: float = 0.0, cost_kind: int = 0, **params):
     """Eq. 7 barycenter by ``lbfgs``, the objective and gradient from
     ``softdtw_batch`` in FP64 at the float32 rounding of the iterate (the
     barycenter is a float32 array), weights 1 / N_k."""
@@ -418,7 +424,8 @@ def softdtw_barycenter_lbfgs(data, offsets, B0, gamma: float, band: float = 0.0,
 
     def fn(x):
         Bf = x.reshape(M, d).astype(np.float32)
-        vals, loss, g = softdtw_batch(Bf, data, offsets, gamma, weights=w, prec="f64", band=band)
+        vals, loss, g = softdtw_batch(Bf, data, offsets, gamma, weights=w, prec="f64", band=band,
+                                      cost_kind=cost_kind)
         return float(loss), g.ravel()
 
     x, f, it, ev, why = lbfgs(fn, B0.astype(np.float64).ravel(), **params)

@@ -41,10 +41,13 @@ def paths(M: int, N: int):
     return out
 
 
-def cost_matrix(B, Y) -> np.ndarray:
-    """Delta[i, j] = sum_c (b_ic - y_jc)^2 in double (exact for small integers)."""
+def cost_matrix(B, Y, cost_kind: int = 0) -> np.ndarray:
+    """Delta[i, j] = sum_c (b_ic - y_jc)^2 in double (exact for small integers);
+    cost_kind 1: the Euclidean norm, numpy's ``linalg.norm`` of b_i - y_j."""
     B = np.asarray(B, dtype=np.float64).reshape(len(B), -1)
     Y = np.asarray(Y, dtype=np.float64).reshape(len(Y), -1)
+    if cost_kind:
+        return np.linalg.norm(B[:, None, :] - Y[None, :, :], axis=-1)
     return ((B[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
 
 
@@ -58,9 +61,9 @@ def reversed_steps(p):
     return tuple(codes)
 
 
-def dtw(B, Y):
+def dtw(B, Y, cost_kind: int = 0):
     """Eq. 1 by enumeration: (min cost, the tie-rule path, all optimal paths)."""
-    D = cost_matrix(B, Y)
+    D = cost_matrix(B, Y, cost_kind)
     M, N = D.shape
     ps = paths(M, N)
     costs = [sum(D[i, j] for i, j in p) for p in ps]
@@ -70,10 +73,10 @@ def dtw(B, Y):
     return best, chosen, opt
 
 
-def softdtw(B, Y, gamma: float):
+def softdtw(B, Y, gamma: float, cost_kind: int = 0):
     """Eq. 4 by enumeration: value -gamma log sum_A exp(-<A,Delta>/gamma) and the
     expected alignment matrix E = sum_A p(A) A, p(A) proportional to exp(-<A,Delta>/gamma)."""
-    D = cost_matrix(B, Y)
+    D = cost_matrix(B, Y, cost_kind)
     M, N = D.shape
     ps = paths(M, N)
     costs = np.array([sum(D[i, j] for i, j in p) for p in ps])
@@ -88,7 +91,7 @@ def softdtw(B, Y, gamma: float):
     return value, E
 
 
-def subdtw(X, Y):
+def subdtw(X, Y, cost_kind: int = 0):
     """Sub-DTW (Sec. 3.2) by enumeration over every piece Y[a..b] and every
     complete alignment path of X against it: (min cost, b*, the chosen path).
 
@@ -96,7 +99,7 @@ def subdtw(X, Y):
     among the optimal paths ending at b*, the greatest under the tie order
     diag > up > left walked back from (M-1, b*), where leaving row 0 (the
     free start) counts as a diagonal step."""
-    D = cost_matrix(X, Y)
+    D = cost_matrix(X, Y, cost_kind)
     M, N = D.shape
     best = math.inf
     cands = []                      # (cost, b, path)

@@ -13,7 +13,7 @@
  * paper's 1-based indices with a padded row 0 and column 0 (Eq. 5); outputs
  * are 0-based.
  *
- * Required macros: REAL, FMA(a,b,c), EXP(x), LOG(x), SFX(name).
+ * Required macros: REAL, FMA(a,b,c), EXP(x), LOG(x), SQRT(x), SFX(name).
  *
  * The ORACLE_PLANT_* switches are mutation hooks, off in every normal build:
  * the pin tests compile the oracle once per switch, each planting one
@@ -22,10 +22,22 @@
  * fails for each.
  */
 
-/* delta(b_i, y_j): squared Euclidean local cost (Definition "Distance
- * Matrix", Sec. 3.2, read as the squared l2 norm).  Accumulated channel by
- * channel from 0 with one fused multiply-add per channel. */
-static REAL SFX(local_cost)(const float* b, const float* y, int d)
+/* delta(b_i, y_j) (Definition "Distance Matrix", Sec. 3.2).  The sum
+ * s = sum_c (b_c - y_c)^2 is accumulated channel by channel from 0 with one
+ * fused multiply-add per channel.  cost_kind 0: delta = s, the squared l2 norm
+ * (the default reading); cost_kind 1: delta = sqrt(s), the l2 norm itself (the
+ * paper's wording), rounded once in the working precision. */
+static REAL SFX(finish_cost)(REAL acc, int cost_kind)
+{
+#ifdef ORACLE_PLANT_L2_NO_SQRT
+    (void)cost_kind;
+    return acc;
+#else
+    return cost_kind ? SQRT(acc) : acc;
+#endif
+}
+
+static REAL SFX(local_cost)(const float* b, const float* y, int d, int cost_kind)
 {
     REAL acc = 0;
     for (int c = 0; c < d; ++c) {
@@ -35,11 +47,11 @@ static REAL SFX(local_cost)(const float* b, const float* y, int d)
 #endif
         acc = FMA(t, t, acc);
     }
-    return acc;
+    return SFX(finish_cost)(acc, cost_kind);
 }
 
 /* Same cost with a REAL-typed prototype row (DBA keeps B in REAL). */
-static REAL SFX(local_cost_r)(const REAL* b, const float* y, int d)
+static REAL SFX(local_cost_r)(const REAL* b, const float* y, int d, int cost_kind)
 {
     REAL acc = 0;
     for (int c = 0; c < d; ++c) {
@@ -49,7 +61,7 @@ static REAL SFX(local_cost_r)(const REAL* b, const float* y, int d)
 #endif
         acc = FMA(t, t, acc);
     }
-    return acc;
+    return SFX(finish_cost)(acc, cost_kind);
 }
 
 /*
@@ -69,7 +81,7 @@ static REAL SFX(local_cost_r)(const REAL* b, const float* y, int d)
  */
 static int SFX(dtw_core)(const REAL* B, int64_t M, const float* Y, int64_t N, int d,
                          REAL* cost, int32_t* plen, int32_t* jlo, int32_t* jhi,
-                         int32_t* pi_i, int32_t* pi_j, double band)
+                         int32_t* pi_i, int32_t* pi_j, double band, int cost_kind)
 {
     /* Sakoe-Chiba band (Table I: a width given as a fraction of the signals'
      * length; reading for unequal lengths): 0-based cell (i, j) is inside when
@@ -116,7 +128,7 @@ static int SFX(dtw_core)(const REAL* B, int64_t M, const float* Y, int64_t N, in
             else if (up <= lf) { ch = 1; m = up; }
 #endif
             else { ch = 2; m = lf; }
-            cur[j] = SFX(local_cost_r)(bi, Y + (j - 1) * d, d) + m;
+            cur[j] = SFX(local_cost_r)(bi, Y + (j - 1) * d, d, cost_kind) + m;
             choice[(i - 1) * N + (j - 1)] = ch;
         }
         REAL* t = prev; prev = cur; cur = t;
@@ -162,12 +174,12 @@ static int SFX(dtw_core)(const REAL* B, int64_t M, const float* Y, int64_t N, in
 /* DTW of one pair with a float prototype (converted exactly to REAL). */
 int SFX(orc_dtw)(const float* B, int64_t M, const float* Y, int64_t N, int d,
                  REAL* cost, int32_t* plen, int32_t* jlo, int32_t* jhi,
-                 int32_t* pi_i, int32_t* pi_j, double band)
+                 int32_t* pi_i, int32_t* pi_j, double band, int cost_kind)
 {
     REAL* Br = (REAL*)malloc((size_t)M * d * sizeof(REAL));
     if (!Br) return -1;
     for (int64_t k = 0; k < M * d; ++k) Br[k] = (REAL)B[k];
-    int rc = SFX(dtw_core)(Br, M, Y, N, d, cost, plen, jlo, jhi, pi_i, pi_j, band);
+    int rc = SFX(dtw_core)(Br, M, Y, N, d, cost, plen, jlo, jhi, pi_i, pi_j, band, cost_kind);
     free(Br);
     return rc;
 }
@@ -178,7 +190,7 @@ int SFX(orc_dtw)(const float* B, int64_t M, const float* Y, int64_t N, int d,
  * Pairs are independent; they are spread over OpenMP threads.
  */
 int SFX(orc_score)(const float* B, int64_t M, const float* Y, const int64_t* offsets, int T, int d,
-                   REAL* score, REAL* cost, int32_t* plen, double band)
+                   REAL* score, REAL* cost, int32_t* plen, double band, int cost_kind)
 {
     REAL* Br = (REAL*)malloc((size_t)M * d * sizeof(REAL));
     if (!Br) return -1;
@@ -188,7 +200,7 @@ int SFX(orc_score)(const float* B, int64_t M, const float* Y, const int64_t* off
     for (int k = 0; k < T; ++k) {
         REAL c; int32_t L;
         int64_t N = offsets[k + 1] - offsets[k];
-        bad |= SFX(dtw_core)(Br, M, Y + offsets[k] * d, N, d, &c, &L, NULL, NULL, NULL, NULL, band) != 0;
+        bad |= SFX(dtw_core)(Br, M, Y + offsets[k] * d, N, d, &c, &L, NULL, NULL, NULL, NULL, band, cost_kind) != 0;
         if (cost) cost[k] = c;
         if (plen) plen[k] = L;
         if (score) score[k] = c / (REAL)L;
@@ -209,7 +221,8 @@ int SFX(orc_score)(const float* B, int64_t M, const float* Y, const int64_t* off
  * double and rounded once to REAL.  costs[k] (optional) = DTW(B_in, Y_k).
  */
 int SFX(orc_dba)(const REAL* B_in, REAL* B_out, int64_t M, const float* Y, const int64_t* offsets,
-                 int T, int d, int32_t* counts, double* cost_before, REAL* costs, double band)
+                 int T, int d, int32_t* counts, double* cost_before, REAL* costs, double band,
+                 int cost_kind)
 {
     int32_t* jlo = (int32_t*)malloc((size_t)T * M * sizeof(int32_t));
     int32_t* jhi = (int32_t*)malloc((size_t)T * M * sizeof(int32_t));
@@ -222,7 +235,7 @@ int SFX(orc_dba)(const REAL* B_in, REAL* B_out, int64_t M, const float* Y, const
     for (int k = 0; k < T; ++k) {
         int64_t N = offsets[k + 1] - offsets[k];
         bad |= SFX(dtw_core)(B_in, M, Y + offsets[k] * d, N, d, &ck[k], NULL,
-                             jlo + (int64_t)k * M, jhi + (int64_t)k * M, NULL, NULL, band) != 0;
+                             jlo + (int64_t)k * M, jhi + (int64_t)k * M, NULL, NULL, band, cost_kind) != 0;
     }
     if (!bad) {
         for (int k = 0; k < T; ++k) {
@@ -273,14 +286,15 @@ static REAL SFX(softmin3)(REAL a, REAL b, REAL c, REAL gamma)
  *   e(i,j) = sum over successors s in {(i+1,j), (i,j+1), (i+1,j+1)} of
  *            exp((r(s) - r(i,j) - delta(s)) / gamma) * e(s),
  * i.e. e(i,j) = d r(M,N) / d r(i,j), the expected alignment matrix.  Then
- *   grad[i][c] = sum_j e(i,j) * d delta(i,j) / d b_ic = sum_j e(i,j) * 2 (b_ic - y_jc).
+ *   grad[i][c] = sum_j e(i,j) * d delta(i,j) / d b_ic, which is
+ *   sum_j e(i,j) * 2 (b_ic - y_jc) for the squared norm.
  *
  * R and E (optional, may be NULL) receive the (M+2) x (N+2) matrices in
  * 1-based layout.  grad (optional) is [M][d].  gamma must be > 0 for the
  * gradient.  Returns 0 or -1.
  */
 int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d, REAL gamma,
-                     REAL* value, REAL* R_out, REAL* E_out, REAL* grad, double band)
+                     REAL* value, REAL* R_out, REAL* E_out, REAL* grad, double band, int cost_kind)
 {
     /* Sakoe-Chiba band as in dtw_core: 0-based cell (i, j) kept when
      * |i N - j M| <= floor(band M N); cells outside are +inf in the forward
@@ -299,7 +313,7 @@ int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d
     for (int64_t i = 1; i <= M; ++i)
         for (int64_t j = 1; j <= N; ++j) {
             if (SOFT_OUT(i, j)) continue;          /* stays +inf */
-            REAL dl = SFX(local_cost)(B + (i - 1) * d, Y + (j - 1) * d, d);
+            REAL dl = SFX(local_cost)(B + (i - 1) * d, Y + (j - 1) * d, d, cost_kind);
             D[i * W + j] = dl;
             R[i * W + j] = dl + SFX(softmin3)(R[(i - 1) * W + j - 1], R[(i - 1) * W + j],
                                               R[i * W + j - 1], gamma);
@@ -333,11 +347,25 @@ int SFX(orc_softdtw)(const float* B, int64_t M, const float* Y, int64_t N, int d
 #endif
             }
         if (grad) {
+            /* d delta / d b_ic: 2 (b_ic - y_jc) for the squared norm;
+             * (b_ic - y_jc) / delta for the norm itself, 0 where delta = 0 (the
+             * norm has no derivative there; 0 is the minimum-norm subgradient) */
             for (int64_t i = 1; i <= M; ++i)
                 for (int c = 0; c < d; ++c) {
                     REAL g = 0;
-                    for (int64_t j = 1; j <= N; ++j)
-                        g += E[i * W + j] * 2 * ((REAL)B[(i - 1) * d + c] - (REAL)Y[(j - 1) * d + c]);
+                    for (int64_t j = 1; j <= N; ++j) {
+                        const REAL t = (REAL)B[(i - 1) * d + c] - (REAL)Y[(j - 1) * d + c];
+                        const REAL dl = D[i * W + j];
+                        if (!cost_kind)
+                            g += E[i * W + j] * 2 * t;
+#ifdef ORACLE_PLANT_L2_GRAD_TWO
+                        else if (dl > 0)
+                            g += E[i * W + j] * 2 * t / dl;
+#else
+                        else if (dl > 0)
+                            g += E[i * W + j] * t / dl;
+#endif
+                    }
                     grad[(i - 1) * d + c] = g;
                 }
         }
@@ -364,7 +392,8 @@ done:
  * order.  Pairs run on OpenMP threads.
  */
 int SFX(orc_softdtw_batch)(const float* B, int64_t M, const float* Y, const int64_t* offsets, int T, int d,
-                           REAL gamma, const REAL* weights, REAL* values, REAL* loss, REAL* grad, double band)
+                           REAL gamma, const REAL* weights, REAL* values, REAL* loss, REAL* grad, double band,
+                           int cost_kind)
 {
     REAL* g = grad ? (REAL*)calloc((size_t)T * M * d, sizeof(REAL)) : NULL;
     REAL* v = (REAL*)malloc((size_t)T * sizeof(REAL));
@@ -374,7 +403,7 @@ int SFX(orc_softdtw_batch)(const float* B, int64_t M, const float* Y, const int6
     for (int k = 0; k < T; ++k) {
         int64_t N = offsets[k + 1] - offsets[k];
         bad |= SFX(orc_softdtw)(B, M, Y + offsets[k] * d, N, d, gamma, &v[k], NULL, NULL,
-                                g ? g + (int64_t)k * M * d : NULL, band) != 0;
+                                g ? g + (int64_t)k * M * d : NULL, band, cost_kind) != 0;
     }
     if (!bad) {
         REAL L = 0;
@@ -412,7 +441,7 @@ int SFX(orc_softdtw_batch)(const float* B, int64_t M, const float* Y, const int6
  */
 int SFX(orc_subdtw)(const float* X, int64_t M, const float* Y, int64_t N, int d,
                     REAL* cost, int32_t* a_star, int32_t* b_star, int32_t* plen,
-                    int32_t* jlo, int32_t* jhi)
+                    int32_t* jlo, int32_t* jhi, int cost_kind)
 {
     REAL* prev = (REAL*)malloc((size_t)(N + 1) * sizeof(REAL));
     REAL* cur = (REAL*)malloc((size_t)(N + 1) * sizeof(REAL));
@@ -433,7 +462,7 @@ int SFX(orc_subdtw)(const float* X, int64_t M, const float* Y, int64_t N, int d,
             if (dg <= up && dg <= lf) { ch = 0; m = dg; }
             else if (up <= lf) { ch = 1; m = up; }
             else { ch = 2; m = lf; }
-            cur[j] = SFX(local_cost)(xi, Y + (j - 1) * d, d) + m;
+            cur[j] = SFX(local_cost)(xi, Y + (j - 1) * d, d, cost_kind) + m;
             choice[(i - 1) * N + (j - 1)] = ch;
         }
         REAL* t = prev; prev = cur; cur = t;

@@ -22,24 +22,28 @@
 #define FMA(a, b, c) fma((a), (b), (c))
 #define EXP(x) exp(x)
 #define LOG(x) log(x)
+#define SQRT(x) sqrt(x)
 #define SFX(name) name##_f64
 #include "oracle_body.h"
 #undef REAL
 #undef FMA
 #undef EXP
 #undef LOG
+#undef SQRT
 #undef SFX
 
 #define REAL float
 #define FMA(a, b, c) fmaf((a), (b), (c))
 #define EXP(x) expf(x)
 #define LOG(x) logf(x)
+#define SQRT(x) sqrtf(x)
 #define SFX(name) name##_f32
 #include "oracle_body.h"
 #undef REAL
 #undef FMA
 #undef EXP
 #undef LOG
+#undef SQRT
 #undef SFX
 
-int orc_abi_version(void) { return 1; }
+int orc_abi_version(void) { return 2; }

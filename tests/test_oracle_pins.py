@@ -528,3 +528,154 @@ def _pins_fail(defines) -> bool:
 def test_planted_mistakes_are_caught(plant):
     assert not _pins_fail(())
     assert _pins_fail((plant,))
+
+
+# --- the l2-norm local cost (cost_kind 1, Sec. 3.2's "Euclidean distance") -----
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_l2_dtw_matches_brute_force_integer_ties(prec):
+    """d = 1 integer samples: the l2 norm is |b - y|, an exact integer, so every
+    path cost is exact and ties are frequent; cost and tie-rule path equal to
+    the enumeration's (numpy's norm)."""
+    rng = np.random.default_rng(61)
+    for M in range(1, 7):
+        for N in range(1, 7):
+            B, Y = synth.integer_pair(rng, M, N, 1, -3, 3)
+            best, chosen, _ = brute.dtw(B, Y, cost_kind=1)
+            r = oracle.dtw(B, Y, prec, cost_kind=1)
+            assert float(r["cost"]) == best, (M, N)
+            assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen, (M, N)
+            assert r["plen"] == len(chosen)
+
+
+def test_l2_dtw_matches_brute_force_real():
+    """d = 2, 3 real samples: cost within rounding; the path equal wherever the
+    optimum is unique by a margin."""
+    rng = np.random.default_rng(62)
+    for M in range(1, 7):
+        for N in range(1, 7):
+            for d in (2, 3):
+                B, Y = _real_pair(rng, M, N, d)
+                best, chosen, _ = brute.dtw(B, Y, cost_kind=1)
+                r = oracle.dtw(B, Y, "f64", cost_kind=1)
+                assert abs(r["cost"] - best) <= 1e-12 * max(1.0, best), (M, N, d)
+                D = brute.cost_matrix(B, Y, 1)
+                costs = sorted(sum(D[i, j] for i, j in p) for p in brute.paths(M, N))
+                if len(costs) == 1 or costs[1] - costs[0] > 1e-9:
+                    assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen, (M, N, d)
+
+
+def test_l2_closed_forms():
+    """One row: DTW = sum_j ||b - y_j||.  DTW(x, x) = 0.  Equal lengths: DTW <=
+    sum_i ||x_i - y_i|| (the diagonal path).  Samples in {0, 1} with d = 1:
+    |b - y| = (b - y)^2, so both costs agree, paths included."""
+    rng = np.random.default_rng(63)
+    b = rng.normal(size=(1, 3)).astype(np.float32)
+    Y = rng.normal(size=(17, 3)).astype(np.float32)
+    want = float(np.linalg.norm(b.astype(np.float64) - Y.astype(np.float64), axis=1).sum())
+    assert abs(oracle.dtw(b, Y, "f64", cost_kind=1)["cost"] - want) <= 1e-12 * want
+    X = rng.normal(size=(40, 2)).astype(np.float32)
+    assert oracle.dtw(X, X, "f64", cost_kind=1)["cost"] == 0.0
+    Z = rng.normal(size=(40, 2)).astype(np.float32)
+    diag = float(np.linalg.norm(X.astype(np.float64) - Z.astype(np.float64), axis=1).sum())
+    assert oracle.dtw(X, Z, "f64", cost_kind=1)["cost"] <= diag + 1e-12
+    for _ in range(10):
+        B = rng.integers(0, 2, size=(9, 1)).astype(np.float32)
+        Y = rng.integers(0, 2, size=(12, 1)).astype(np.float32)
+        a, s = oracle.dtw(B, Y, "f32", cost_kind=1), oracle.dtw(B, Y, "f32")
+        assert a["cost"] == s["cost"] and (a["jlo"] == s["jlo"]).all() and (a["jhi"] == s["jhi"]).all()
+
+
+def test_l2_subdtw_matches_brute_force():
+    rng = np.random.default_rng(64)
+    for M in range(1, 4):
+        for N in range(1, 6):
+            X, Y = synth.integer_pair(rng, M, N, 1, -3, 3)
+            best, b_star, chosen = brute.subdtw(X, Y, cost_kind=1)
+            r = oracle.subdtw(X, Y, "f32", cost_kind=1)
+            assert float(r["cost"]) == best and r["b"] == b_star and _path_of(r) == chosen, (M, N)
+
+
+def test_l2_dba_against_brute_force_paths():
+    """The DBA update under the l2 alignment: each row's mean of the samples
+    that the brute-force tie-rule paths associate with it."""
+    rng = np.random.default_rng(65)
+    B = rng.integers(-3, 4, size=(5, 1)).astype(np.float32)
+    cyc = [rng.integers(-3, 4, size=(n, 1)).astype(np.float32) for n in (6, 4, 5)]
+    data = np.concatenate(cyc); offs = np.array([0, 6, 10, 15])
+    sums = np.zeros((5, 1)); cnt = np.zeros(5, dtype=np.int64); total = 0.0
+    for y in cyc:
+        best, chosen, _ = brute.dtw(B, y, cost_kind=1)
+        total += best
+        for i, j in chosen:
+            sums[i] += y[j]; cnt[i] += 1
+    Bo, counts, cb, _ = oracle.dba_iterate(B, data, offs, "f64", cost_kind=1)
+    assert (counts == cnt).all() and cb == total
+    assert np.allclose(Bo, sums / cnt[:, None], rtol=0, atol=1e-15)
+
+
+def test_l2_softdtw_matches_brute_force():
+    rng = np.random.default_rng(66)
+    for M in range(1, 6):
+        for N in range(1, 6):
+            B, Y = _real_pair(rng, M, N, 2)
+            for g in (0.1, 1.0):
+                v, E = brute.softdtw(B, Y, g, cost_kind=1)
+                r = oracle.softdtw(B, Y, g, "f64", want_E=True, cost_kind=1)
+                assert abs(r["value"] - v) <= 1e-10 * max(1.0, abs(v)), (M, N, g)
+                assert np.allclose(r["E"][1:M + 1, 1:N + 1], E, rtol=1e-9, atol=1e-12), (M, N, g)
+
+
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_l2_softdtw_gradient_finite_differences(gamma):
+    """Central differences of the l2 objective (every distance > 0 for normal
+    samples): d ||b - y|| / d b = (b - y) / ||b - y||, no factor 2."""
+    rng = np.random.default_rng(67)
+    B, Y = _real_pair(rng, 20, 48, 3)
+    g = oracle.softdtw(B, Y, gamma, "f64", cost_kind=1)["grad"]
+    h = 1e-3
+    for (i, c) in ((0, 0), (7, 2), (19, 1), (11, 0)):
+        Bp = B.astype(np.float64).copy(); Bm = Bp.copy()
+        Bp[i, c] += h; Bm[i, c] -= h
+        vp = oracle.softdtw(Bp.astype(np.float32), Y, gamma, "f64", want_grad=False, cost_kind=1)["value"]
+        vm = oracle.softdtw(Bm.astype(np.float32), Y, gamma, "f64", want_grad=False, cost_kind=1)["value"]
+        hp = float(np.float32(Bp[i, c])) - float(np.float32(Bm[i, c]))
+        fd = (vp - vm) / hp
+        assert abs(fd - g[i, c]) <= 1e-4 * max(1.0, abs(g[i, c])), (i, c, fd, g[i, c])
+    # B = Y: every diagonal distance is 0, where the norm has no derivative;
+    # the gradient takes 0 there and stays finite
+    X = rng.normal(size=(10, 2)).astype(np.float32)
+    assert np.isfinite(oracle.softdtw(X, X, gamma, "f64", cost_kind=1)["grad"]).all()
+
+
+def _l2_pins_fail(defines) -> bool:
+    rng = np.random.default_rng(68)
+    try:
+        for M in range(2, 6):
+            for N in range(2, 6):
+                B, Y = synth.integer_pair(rng, M, N, 1, -3, 3)
+                best, chosen, _ = brute.dtw(B, Y, cost_kind=1)
+                r = oracle.dtw(B, Y, "f64", cost_kind=1, _defines=defines)
+                if float(r["cost"]) != best:
+                    return True
+        B, Y = _real_pair(rng, 12, 20, 2)
+        g = oracle.softdtw(B, Y, 0.5, "f64", cost_kind=1, _defines=defines)["grad"]
+        h = 1e-3
+        Bp = B.astype(np.float64).copy(); Bm = Bp.copy()
+        Bp[3, 1] += h; Bm[3, 1] -= h
+        vp = oracle.softdtw(Bp.astype(np.float32), Y, 0.5, "f64", want_grad=False, cost_kind=1,
+                            _defines=defines)["value"]
+        vm = oracle.softdtw(Bm.astype(np.float32), Y, 0.5, "f64", want_grad=False, cost_kind=1,
+                            _defines=defines)["value"]
+        fd = (vp - vm) / (float(np.float32(Bp[3, 1])) - float(np.float32(Bm[3, 1])))
+        if abs(fd - g[3, 1]) > 1e-4 * max(1.0, abs(g[3, 1])):
+            return True
+    except Exception:
+        return True
+    return False
+
+
+@pytest.mark.parametrize("plant", ["ORACLE_PLANT_L2_NO_SQRT", "ORACLE_PLANT_L2_GRAD_TWO"])
+def test_planted_l2_mistakes_are_caught(plant):
+    assert not _l2_pins_fail(())
+    assert _l2_pins_fail((plant,))
