@@ -96,8 +96,19 @@ typedef struct wts_options {
                                       (anomaly_score, dtw_align, dba_iterate, softdtw_forward / _backward and
                                       the barycenters); for soft-DTW, cells outside the band take no part in the
                                       soft minimum (forward) and carry no weight (backward). */
-    int32_t reserved[6];
+    int32_t cost_kind;             /* local cost delta(b_i, y_j) (Definition "Distance Matrix", Sec. 3.2):
+                                      WTS_COST_SQEUCLID (0, default) = sum_c (b_ic - y_jc)^2;
+                                      WTS_COST_L2 (1) = its IEEE square root, the l2 norm.  Every DTW,
+                                      Sub-DTW and soft-DTW operation; the DTW kernels then hold 16 rows per
+                                      lane (rows_per_thread 0 or 16, else WTS_EINVAL).  The soft-DTW
+                                      gradient of the norm is (b_ic - y_jc) / delta, taken as 0 where
+                                      delta = 0.  dba_iterate still averages the aligned samples (the mean
+                                      minimises the squared cost only, so the DBA cost need not decrease). */
+    int32_t reserved[5];
 } wts_options;
+
+/* Values of wts_options.cost_kind. */
+enum { WTS_COST_SQEUCLID = 0, WTS_COST_L2 = 1 };
 
 /* Library version (major * 100 + minor). */
 int wts_version(void);
@@ -176,8 +187,8 @@ int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* 
  *   a_star, b_star [T]           out (int32), 0-based inclusive bounds in Y_k
  *   plen [T]                     out, |pi| (may be NULL)
  *   jlo, jhi [T][M]              out (int32), columns of each row of X
- * rows_per_thread must be 0 (16), 8 or 16; dir_mode 1 (checkpointing) is
- * not offered.
+ * rows_per_thread must be 0 (16), 8 or 16 (0 or 16 with cost_kind = 1);
+ * dir_mode 1 (checkpointing) is not offered.
  * Workspace: wts_workspace_size(WTS_OP_SUBDTW, M, Y, ...).
  */
 int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_options* opt,
@@ -206,7 +217,7 @@ int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_option
  * workspace holds two window slots.  On return `stream` is ordered after all
  * of the call's work.  A window is
  * a single pair, so rows_per_thread = 0 means 8 here (twice the warps of 16,
- * half the serial chain per step).  Workspace: wts_segment_workspace_size
+ * half the serial chain per step; 16 with cost_kind = 1).  Workspace: wts_segment_workspace_size
  * (with the same options).
  */
 int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, size_t* bytes);

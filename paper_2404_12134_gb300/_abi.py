@@ -16,6 +16,7 @@ WTS_OK, WTS_EINVAL, WTS_ENOMEM, WTS_ECUDA, WTS_ETIMEOUT = 0, 1, 2, 3, 4
 OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE, OP_COMPACT_NAN = 1, 2, 3, 4, 5, 6
 OP_SUBDTW = 7
 OP_SOFTDTW_LBFGS = 8
+COST_SQEUCLID, COST_L2 = 0, 1
 
 # every symbol declared in include/wetsand.h
 EXPORTS = (
@@ -50,7 +51,8 @@ class wts_options(ctypes.Structure):
         ("spin_limit", ctypes.c_int32),
         ("fault_skip_handoff", ctypes.c_int32),
         ("band", ctypes.c_double),
-        ("reserved", ctypes.c_int32 * 6),
+        ("cost_kind", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 

@@ -58,11 +58,13 @@ class Batch:
 
 
 def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0, dir_mode=0,
-            ckpt_bands=0, spin_limit=0, fault_skip_handoff=0, band=0.0) -> wts_options:
+            ckpt_bands=0, spin_limit=0, fault_skip_handoff=0, band=0.0, cost_kind=0) -> wts_options:
     """Launch and method options (see wts_options in include/wetsand.h); band > 0
-    is the Sakoe-Chiba width (Table I) for the DTW operations."""
+    is the Sakoe-Chiba width (Table I) for the DTW operations; cost_kind 1 takes
+    the l2 norm as the local cost instead of its square (Sec. 3.2)."""
     o = wts_options()
     o.band = float(band)
+    o.cost_kind = cost_kind
     o.rows_per_thread = rows_per_thread
     o.warps_per_block = warps_per_block
     o.max_blocks = max_blocks

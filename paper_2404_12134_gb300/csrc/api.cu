@@ -120,6 +120,8 @@ int check_opt(const wts_options* opt, int D)
     if (opt->ckpt_bands < 0) return fail(WTS_EINVAL, "ckpt_bands must be >= 0");
     if (opt->spin_limit < 0) return fail(WTS_EINVAL, "spin_limit must be >= 0");
     if (!(opt->band >= 0.0) || opt->band > 1e6) return fail(WTS_EINVAL, "band must be a finite value >= 0");
+    if (opt->cost_kind != WTS_COST_SQEUCLID && opt->cost_kind != WTS_COST_L2)
+        return fail(WTS_EINVAL, "cost_kind must be 0 (squared l2) or 1 (l2 norm), got %d", opt->cost_kind);
     return WTS_OK;
 }
 
@@ -158,6 +160,15 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             L->R = 16;
         }
         L->banded = 1;
+    }
+    if (opt && opt->cost_kind == WTS_COST_L2) {
+        if (op != kOpSoft) {
+            if (opt->rows_per_thread && opt->rows_per_thread != 16)
+                return fail(WTS_EINVAL, "with the l2-norm cost, rows_per_thread must be 0 or 16 (got %d)",
+                            opt->rows_per_thread);
+            L->R = 16;
+        }
+        L->cost_kind = WTS_COST_L2;
     }
     L->BR = 32 * L->R;
     L->M = M;
@@ -300,7 +311,7 @@ int grid_for(int mode, const Layout& L, const wts_options* opt, int* grid, int* 
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    int occ = dtw_wavefront_max_blocks_per_sm(mode, L.D, L.R, *block, L.banded);
+    int occ = dtw_wavefront_max_blocks_per_sm(mode, L.D, L.R, *block, L.banded, L.cost_kind);
     if (occ < 1) return fail(WTS_ECUDA, "no resident block for D=%d R=%d block=%d", L.D, L.R, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;
@@ -331,6 +342,7 @@ DPParams base_params(const Layout& L, char* ws, const wts_options* opt = nullptr
     p.dirs = L.off_dirs ? reinterpret_cast<uint32_t*>(ws + L.off_dirs) : nullptr;
     p.T = L.T;
     p.banded = L.banded;
+    p.cost_kind = L.cost_kind;
     return p;
 }
 
@@ -431,6 +443,7 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     p.rstore = reinterpret_cast<float*>(ws + L.off_rstore);
     p.gpart = reinterpret_cast<float*>(ws + L.off_gpart);
     p.banded = L.banded;
+    p.cost_kind = L.cost_kind;
     return p;
 }
 
@@ -442,7 +455,7 @@ int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, 
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded);
+    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind);
     if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;
@@ -678,11 +691,12 @@ int segment_layout(int64_t M, int32_t d, const wts_options* opt, SegLayout* S)
 }
 
 // One window is one pair: the wavefront has only M / (32 R) warps, so the
-// shorter serial chain of 8 rows per lane (twice the warps) is the default.
+// shorter serial chain of 8 rows per lane (twice the warps) is the default
+// (16 with the l2-norm cost, whose kernels hold 16 rows per lane).
 wts_options segment_options(const wts_options* opt)
 {
     wts_options o = opt ? *opt : wts_options{};
-    if (o.rows_per_thread == 0) o.rows_per_thread = 8;
+    if (o.rows_per_thread == 0) o.rows_per_thread = o.cost_kind == WTS_COST_L2 ? 16 : 8;
     return o;
 }
 

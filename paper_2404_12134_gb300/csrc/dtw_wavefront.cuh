@@ -40,10 +40,27 @@ struct DPParams {
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); R = 16 only;
                              // items then run band-major (every pair's band 0, then band 1, ...)
+    int cost_kind;           // LocalCost; kCostL2 runs with R = 16 only
 };
 
-// Launch the persistent wavefront for D (padded channels) and R (rows/lane).
+// Launch the persistent wavefront for D (padded channels) and R (rows/lane);
+// p.banded and p.cost_kind select the instance set.
 cudaError_t launch_dtw_wavefront(int mode, int D, int R, const DPParams& p, int grid, int block, cudaStream_t st);
-int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block, int banded = 0);
+int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block, int banded = 0, int cost_kind = 0);
+
+// The instance sets, one per translation unit (dtw_wavefront_<set>.cu):
+// rows per lane, band, local cost.
+#define WTS_WF_SETS(X) \
+    X(r8)     /* R = 8,  no band, squared l2 */ \
+    X(r16)    /* R = 16, no band, squared l2 */ \
+    X(r16b)   /* R = 16, band,    squared l2 */ \
+    X(r32)    /* R = 32, no band, squared l2 (d <= 3) */ \
+    X(l2)     /* R = 16, no band, l2 norm */ \
+    X(l2b)    /* R = 16, band,    l2 norm */
+#define WTS_WF_DECL(TAG)                                                                                  \
+    cudaError_t wf_launch_##TAG(int mode, int D, const DPParams& p, int grid, int block, cudaStream_t st); \
+    int wf_occ_##TAG(int mode, int D, int block);
+WTS_WF_SETS(WTS_WF_DECL)
+#undef WTS_WF_DECL
 
 }  // namespace wts

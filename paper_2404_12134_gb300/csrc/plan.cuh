@@ -53,6 +53,7 @@ struct Layout {
     size_t off_hbuf = 0, off_dirs = 0, off_jlo = 0, off_jhi = 0, off_costs = 0, off_btstate = 0;
     int group_bands = 0;  // checkpoint mode: bands whose codes are recomputed at a time (0 = codes stored)
     int banded = 0;       // a Sakoe-Chiba band applies (the banded kernels run with R = 16)
+    int cost_kind = 0;    // local cost: 0 squared l2, 1 the l2 norm (DTW kernels with R = 16)
 
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
     size_t total = 0;

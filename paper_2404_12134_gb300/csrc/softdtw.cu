@@ -17,7 +17,10 @@
 // which the paper cites): e(M,N) = 1 and
 //   e(i,j) = sum over successors s of exp(((r(s) - r(i,j)) - delta(s)) / gamma) e(s),
 // successors beyond the matrix contributing 0, then
-//   d/db_ic sum_j ... = sum_j e(i,j) 2 (b_ic - y_jc).
+//   d/db_ic sum_j ... = sum_j e(i,j) 2 (b_ic - y_jc)
+// for the squared l2 local cost, and sum_j e(i,j) (b_ic - y_jc) / delta(i,j)
+// (0 where delta = 0) for the l2 norm (COST = kCostL2: delta is the IEEE square
+// root of the same sum).
 // The difference r(s) - r(i,j) of neighbouring cells is taken first (exact in
 // floating point when the two are within a factor of two), then delta(s) is
 // subtracted: the exponent keeps the accuracy of the small quantity it is.
@@ -91,7 +94,8 @@ __device__ __forceinline__ void load_rows(float (&b)[R][D], const float* X, int 
             b[k][c] = (i0 + k < M && c < d) ? __ldg(X + (int64_t)(i0 + k) * d + c) : 0.f;
 }
 
-template <int D>
+// delta(b_i, y_j): the squared l2 norm, or (COST = kCostL2) its IEEE square root
+template <int D, int COST>
 __device__ __forceinline__ float local_cost(const float* bk, const float* y, float* t)
 {
     t[0] = __fsub_rn(bk[0], y[0]);
@@ -101,10 +105,10 @@ __device__ __forceinline__ float local_cost(const float* bk, const float* y, flo
         t[c] = __fsub_rn(bk[c], y[c]);
         acc = __fmaf_rn(t[c], t[c], acc);
     }
-    return acc;
+    return COST == kCostL2 ? __fsqrt_rn(acc) : acc;
 }
 
-template <int D, int R, bool BANDED>
+template <int D, int R, bool BANDED, int COST>
 __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane)
 {
     constexpr int BR = 32 * R;
@@ -206,7 +210,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
             for (int k = 0; k < R; ++k) {
                 const float lf = col[k];
                 float t[D];
-                const float delta = local_cost<D>(b[k], y, t);
+                const float delta = local_cost<D, COST>(b[k], y, t);
                 // off the serial path (dg, lf known): m2 and S2
                 const float m2 = fminf(dg, lf);
                 const float S2 = __fadd_rn(1.f, ex2a(__fmul_rn(-fabsf(__fsub_rn(dg, lf)), kk)));
@@ -248,7 +252,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     }
 }
 
-template <int D, int R, bool BANDED>
+template <int D, int R, bool BANDED, int COST>
 __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring)
 {
     constexpr int BR = 32 * R;
@@ -410,7 +414,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                     if (!CHECKED || (i0 + k < M && k >= klo && k <= khi)) {
                         const float r = rv[kq];
                         float t[D];
-                        const float delta = local_cost<D>(b[k], y, t);
+                        const float delta = local_cost<D, COST>(b[k], y, t);
                         // successor s: 2^((r(s) - r) k - delta(s) k), the difference
                         // exact, then one fused multiply-add with delta(s) k kept per cell
                         const float a = ex2a(__fmaf_rn(__fsub_rn(nr, r), kk, -nd));
@@ -421,8 +425,15 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                         // rows is one fused multiply-add per row
                         float e = __fmaf_rn(a, ne, __fmaf_rn(cc, xe, __fmul_rn(bb, re)));
                         if (CHECKED && i0 + k == M - 1 && j == N - 1) e = 1.f;
+                        if (COST != kCostL2) {
 #pragma unroll
-                        for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(e, t[c], g[k][c]);
+                            for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(e, t[c], g[k][c]);
+                        } else {
+                            // d delta / d b = t / delta (0 where delta = 0)
+                            const float w = delta > 0.f ? __fdividef(e, delta) : 0.f;
+#pragma unroll
+                            for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(w, t[c], g[k][c]);
+                        }
                         rn = r; dn = __fmul_rn(delta, kk); en = e;
                     }
                     xr = rr; xd = rd; xe = re;
@@ -452,10 +463,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         if (i0 + k < M)
 #pragma unroll
             for (int c = 0; c < D; ++c)
-                if (c < d) gout[(int64_t)(i0 + k) * d + c] = __fmul_rn(2.f, g[k][c]);
+                if (c < d) gout[(int64_t)(i0 + k) * d + c] = COST == kCostL2 ? g[k][c] : __fmul_rn(2.f, g[k][c]);
 }
 
-template <int D, int R, bool BWD, bool BANDED>
+template <int D, int R, bool BWD, bool BANDED, int COST>
 __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
 {
     extern __shared__ float4 rring_all[];
@@ -483,10 +494,10 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
         const PairDesc pd = p.pairs[p.order[q]];
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
-            bwd_band<D, R, BANDED>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane,
+            bwd_band<D, R, BANDED, COST>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane,
                            rring_all + (threadIdx.x >> 5) * kRPre * (R / 4) * 32);
         } else {
-            fwd_band<D, R, BANDED>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
+            fwd_band<D, R, BANDED, COST>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
         }
     }
 }
@@ -518,37 +529,45 @@ __global__ void adam_kernel(float* x, const float* grad, float* m, float* v, int
     x[i] = __fsub_rn(x[i], __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(sqrtf(vh), eps)));
 }
 
-template <int D, bool BWD, bool BANDED>
+template <int D, bool BWD, bool BANDED, int COST>
 cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
     const size_t smem = BWD ? rring_bytes<R>(block) : 0;
-    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    softdtw_kernel<D, R, BWD, BANDED><<<grid, block, smem, st>>>(p);
+    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    softdtw_kernel<D, R, BWD, BANDED, COST><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 template <int D, bool BWD>
 cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
-    return p.banded ? launch_db<D, BWD, true>(p, grid, block, st) : launch_db<D, BWD, false>(p, grid, block, st);
+    if (p.cost_kind == kCostL2)
+        return p.banded ? launch_db<D, BWD, true, kCostL2>(p, grid, block, st)
+                        : launch_db<D, BWD, false, kCostL2>(p, grid, block, st);
+    return p.banded ? launch_db<D, BWD, true, kCostSqEuclid>(p, grid, block, st)
+                    : launch_db<D, BWD, false, kCostSqEuclid>(p, grid, block, st);
 }
 
-template <int D, bool BWD, bool BANDED>
+template <int D, bool BWD, bool BANDED, int COST>
 int occ_db(int block)
 {
     constexpr int R = 8;
     const size_t smem = BWD ? rring_bytes<R>(block) : 0;
     int n = 0;
-    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD, BANDED>, block, smem);
+    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD, BANDED, COST>, block, smem);
     return n;
 }
 
 template <int D, bool BWD>
-int occ_d(int block, int banded)
+int occ_d(int block, int banded, int cost_kind)
 {
-    return banded ? occ_db<D, BWD, true>(block) : occ_db<D, BWD, false>(block);
+    if (cost_kind == kCostL2)
+        return banded ? occ_db<D, BWD, true, kCostL2>(block) : occ_db<D, BWD, false, kCostL2>(block);
+    return banded ? occ_db<D, BWD, true, kCostSqEuclid>(block) : occ_db<D, BWD, false, kCostSqEuclid>(block);
 }
 
 }  // namespace
@@ -576,12 +595,12 @@ cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, 
     return cudaErrorInvalidValue;
 }
 
-int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded)
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded, int cost_kind)
 {
     if (backward) {
-        WTS_SOFT_DISPATCH(occ_d, true, block, banded)
+        WTS_SOFT_DISPATCH(occ_d, true, block, banded, cost_kind)
     } else {
-        WTS_SOFT_DISPATCH(occ_d, false, block, banded)
+        WTS_SOFT_DISPATCH(occ_d, false, block, banded, cost_kind)
     }
     return 0;
 }

@@ -20,7 +20,8 @@ struct SoftParams {
                          // per column; pre-filled with NaN
     float* rstore;       // R, per band [(N+31) steps][R/4][32 lanes][4]
     float* value_out;    // [P] Soft-DTW value per pair (forward)
-    float* gpart;        // [P][M][d] per-pair gradient sum_j e_ij * 2 (b_i - y_j) (backward)
+    float* gpart;        // [P][M][d] per-pair gradient sum_j e_ij * d delta_ij / d b_i (backward):
+                         // 2 (b_i - y_j), or (b_i - y_j) / delta_ij for the l2 norm
     // checkpoint mode: R is kept only for bands [band_lo, band_lo + band_cnt)
     // (band b at R offset b - band_lo); the forward then recomputes those
     // bands from their stored top rows (recompute = 1, no hand-off writes)
@@ -30,6 +31,7 @@ struct SoftParams {
     long long spin_limit;    // polls before a wait gives up
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
+    int cost_kind;           // LocalCost
 };
 
 // Rows held per lane by the soft-DTW kernels (8 for every padded channel
@@ -38,7 +40,7 @@ inline int soft_rows(int /*D*/) { return 8; }
 
 cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
-int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0);
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0, int cost_kind = 0);
 
 // grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending)
 cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, int T, int64_t M, int d,

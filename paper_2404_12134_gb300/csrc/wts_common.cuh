@@ -23,6 +23,8 @@ constexpr long long kSpinLimit = 1ll << 27;   // polls before a wait gives up (~
 
 // Device status word values (first word of every workspace).
 enum DevStatus : int { kDevOk = 0, kDevTimeout = 1 };
+// local cost delta(b_i, y_j) (Sec. 3.2): the squared l2 norm, or the norm itself
+enum LocalCost : int { kCostSqEuclid = 0, kCostL2 = 1 };
 
 // One alignment problem of a batch.
 struct PairDesc {

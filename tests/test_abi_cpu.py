@@ -158,3 +158,48 @@ def test_band_option_layout_and_validation(lib):
     assert _size(lib, _abi.OP_SUBDTW, 1000, b, o)[0] == _abi.WTS_EINVAL
     o.band = -1.0
     assert _size(lib, _abi.OP_DTW_ALIGN, 1000, b, o)[0] == _abi.WTS_EINVAL
+
+
+def test_cost_kind_option_layout_and_validation(lib):
+    """cost_kind sits after the band in the same 64 bytes; 0 and 1 are the only
+    values; the l2-norm DTW kernels hold 16 rows per lane (8 or 32 refused, 0
+    means 16, also where d <= 2 would otherwise pick 32); soft-DTW takes it
+    with its own row count; the segmentation workspace follows R = 16."""
+    assert ctypes.sizeof(_abi.wts_options) == 64
+    assert _abi.wts_options.cost_kind.offset == 40
+    b, offs = _batch([1200, 800], d=2)
+    o = _abi.wts_options()
+    o.cost_kind = 1
+    for op in (_abi.OP_ANOMALY_SCORE, _abi.OP_DTW_ALIGN, _abi.OP_DBA_ITERATE, _abi.OP_SOFTDTW, _abi.OP_SUBDTW,
+               _abi.OP_PAIRWISE):
+        assert _size(lib, op, 1000, b, o)[0] == 0, op
+    # default R for d = 2 is 32 (two bands of 1024 rows); with the l2 norm, 16
+    # (two of 512): the code store of dtw_align is the same size, the hand-off
+    # rows are not
+    o0 = _abi.wts_options()
+    o16 = _abi.wts_options()
+    o16.rows_per_thread = 16
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 1000, b, o)[1] == _size(lib, _abi.OP_ANOMALY_SCORE, 1000, b, o16)[1]
+    assert _size(lib, _abi.OP_ANOMALY_SCORE, 1000, b, o)[1] != _size(lib, _abi.OP_ANOMALY_SCORE, 1000, b, o0)[1]
+    for r in (8, 32):
+        o.rows_per_thread = r
+        assert _size(lib, _abi.OP_DTW_ALIGN, 1000, b, o)[0] == _abi.WTS_EINVAL
+        assert b"l2-norm" in lib.wts_last_error()
+    o.rows_per_thread = 0
+    o.band = 0.6
+    assert _size(lib, _abi.OP_DTW_ALIGN, 1000, b, o)[0] == 0
+    assert _size(lib, _abi.OP_SOFTDTW, 1000, b, o)[0] == 0
+    o.band = 0.0
+    for bad in (2, -1):
+        o.cost_kind = bad
+        assert _size(lib, _abi.OP_ANOMALY_SCORE, 1000, b, o)[0] == _abi.WTS_EINVAL
+        assert b"cost_kind" in lib.wts_last_error()
+    o.cost_kind = 1
+    n16 = ctypes.c_size_t(0)
+    n8 = ctypes.c_size_t(0)
+    assert lib.wts_segment_workspace_size(600, 3, ctypes.byref(o), ctypes.byref(n16)) == 0
+    assert lib.wts_segment_workspace_size(600, 3, None, ctypes.byref(n8)) == 0
+    o16.cost_kind = 0
+    n16b = ctypes.c_size_t(0)
+    assert lib.wts_segment_workspace_size(600, 3, ctypes.byref(o16), ctypes.byref(n16b)) == 0
+    assert n16.value == n16b.value
