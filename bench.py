@@ -544,6 +544,32 @@ def banded_dba_leg(api, torch, dev, barrier, gb, b, B0, band: float = 0.6, iters
             "gcups_in_band": cells / (ms * 1e-3) / 1e9, "device_status": api.read_status(ws.buf)}
 
 
+def l2_cost_leg(api, torch, dev, st, barrier, gb, B0, cells: int, ws, iters: int = 2):
+    """The l2-norm local cost (cost_kind 1, Sec. 3.2's wording) on the benchmark
+    batch: one DBA iteration and one anomaly-score pass, GCUPS over the full
+    matrices (the kernels take the IEEE square root of every cell's sum)."""
+    opt = api.options(cost_kind=1)
+    B = B0.clone()
+    api.dba_iterate(B, gb, opt, ws=ws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(iters):
+        api.dba_iterate(B, gb, opt, ws=ws)
+    e1.record(st)
+    barrier()
+    dba_ms = e0.elapsed_time(e1) / iters
+    api.anomaly_score(B, gb, opt, ws=ws)
+    barrier()
+    e0.record(st)
+    api.anomaly_score(B, gb, opt, ws=ws)
+    e1.record(st)
+    barrier()
+    sc_ms = e0.elapsed_time(e1)
+    return {"cost_kind": 1, "ms_per_dba_iter": dba_ms, "dba_gcups": cells / (dba_ms * 1e-3) / 1e9,
+            "anomaly_score_gcups": cells / (sc_ms * 1e-3) / 1e9, "device_status": api.read_status(ws.buf)}
+
+
 def table_leg(api, torch, dev, barrier):
     """Entries of the results table not covered by the other legs: the small
     DBA workload end to end (medoid init, 10 DBA iterations, scores), the
@@ -812,6 +838,7 @@ def run_gpu(args):
         s1.record(st)
         barrier()
         out["anomaly_score_gcups"] = cells / (s0.elapsed_time(s1) * 1e-3) / 1e9
+        out["l2_cost"] = l2_cost_leg(api, torch, dev, st, barrier, gb, B0, cells, ws)
 
     if not args.no_extras:
         out["scoring"] = scoring_leg(api, torch, dev, barrier)
