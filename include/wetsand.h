@@ -380,6 +380,27 @@ int wts_compact_nan(const wts_batch* Y, void* workspace, size_t workspace_bytes,
                     int64_t* out_offsets);
 
 /*
+ * wts_pad_last - the equal-length form of Sec. 4.1: every cycle extended with
+ * its last sample to a common length L (the paper pads this way for its
+ * Soft-DTW runs):  out[k][j][c] = y_k[min(j, N_k - 1)][c],  j < L.
+ *   L: 0 = the longest cycle's length; a shorter L than that is WTS_EINVAL
+ *   out [T][L][d] out (device); with offsets k * L it is a batch of T cycles
+ *   of length L.
+ * No workspace; asynchronous on `stream`.
+ */
+int wts_pad_last(const wts_batch* Y, int64_t L, void* stream, float* out);
+
+/*
+ * wts_select_channel - channel c of every cycle (the paper aligns, averages
+ * and scores each joint on its own, Sec. 5):  out[t] = data[t][c] for every
+ * sample t of the packed batch; with Y's offsets and d = 1, out is the batch
+ * of that channel.
+ *   c in [0, d); out [sum_k N_k] out (device).
+ * No workspace; asynchronous on `stream`.
+ */
+int wts_select_channel(const wts_batch* Y, int32_t c, void* stream, float* out);
+
+/*
  * wts_pairwise_dtw - DTW between every two cycles of the batch (rows = the
  * lower-index cycle), for the medoid that initialises DBA.
  *   C [T][T] out: symmetric, C[a][a] = 0.

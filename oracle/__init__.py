@@ -330,6 +330,29 @@ def euclid_mean(data, offsets, M: int) -> np.ndarray:
     return (acc / T).astype(np.float32)
 
 
+# --- the paper's own data forms ---------------------------------------------------
+
+def pad_last(data, offsets, L: int = 0) -> np.ndarray:
+    """Sec. 4.1: every cycle extended with its last sample to length L (0: the
+    longest), as [T, L, d]."""
+    data = _as2d(data)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    T = offsets.shape[0] - 1
+    n = np.diff(offsets)
+    L = int(n.max()) if L == 0 else int(L)
+    assert L >= n.max()
+    out = np.zeros((T, L, data.shape[1]), dtype=np.float32)
+    for k in range(T):
+        for j in range(L):
+            out[k, j] = data[offsets[k] + min(j, n[k] - 1)]
+    return out
+
+
+def select_channel(data, c: int) -> np.ndarray:
+    """Channel c of every sample of a packed batch (each joint on its own, Sec. 5)."""
+    return np.ascontiguousarray(_as2d(data)[:, c])
+
+
 # --- detection thresholds (Sec. 5.3) ------------------------------------------
 
 def thresholds(scores):

@@ -26,7 +26,7 @@ EXPORTS = (
     "wts_resample", "wts_euclid_mean", "anomaly_score_noalloc",
     "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune", "wts_compact_nan",
     "subdtw_align", "wts_segment_workspace_size", "wts_segment", "wts_thresholds", "wts_f2",
-    "wts_lbfgs_minimize", "wts_softdtw_barycenter_lbfgs",
+    "wts_lbfgs_minimize", "wts_softdtw_barycenter_lbfgs", "wts_pad_last", "wts_select_channel",
 )
 
 
@@ -115,6 +115,8 @@ _SIGS = {
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),
     "anomaly_score_noalloc": ([VP, I64, PB, PO, VP, VP, VP, VP], ctypes.c_int),
     "wts_compact_nan": ([PB, VP, SZ, VP, VP, VP], ctypes.c_int),
+    "wts_pad_last": ([PB, I64, VP, VP], ctypes.c_int),
+    "wts_select_channel": ([PB, I32, VP, VP], ctypes.c_int),
     "wts_autotune": ([ctypes.c_int, VP, I64, PB, VP, SZ, VP, PO, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "softdtw_forward": ([VP, I64, PB, ctypes.c_float, PO, VP, SZ, VP, VP], ctypes.c_int),
     "softdtw_backward": ([VP, I64, PB, ctypes.c_float, VP, PO, VP, SZ, VP, VP], ctypes.c_int),

@@ -391,6 +391,25 @@ def compact_nan(batch: Batch, ws: Workspace | None = None) -> Batch:
     return Batch(out[: int(host[-1])], offs, host)
 
 
+def pad_last(batch: Batch, L: int = 0) -> Batch:
+    """Sec. 4.1's equal-length form: every cycle extended with its last sample
+    to length L (0: the longest cycle's); returns the padded batch of T cycles
+    of length L."""
+    Lh = int(batch.lengths.max()) if L == 0 else int(L)
+    out = torch.empty((batch.T * Lh, batch.d), dtype=torch.float32, device=batch.data.device)
+    check(_abi.load().wts_pad_last(ctypes.byref(batch.c()), int(L), _stream(), out.data_ptr()))
+    offs_h = np.arange(batch.T + 1, dtype=np.int64) * Lh
+    return Batch(out, torch.from_numpy(offs_h).to(batch.data.device), offs_h)
+
+
+def select_channel(batch: Batch, c: int) -> Batch:
+    """Channel c of every cycle as a d = 1 batch with the same offsets (the
+    paper treats each joint on its own)."""
+    out = torch.empty((batch.data.shape[0], 1), dtype=torch.float32, device=batch.data.device)
+    check(_abi.load().wts_select_channel(ctypes.byref(batch.c()), int(c), _stream(), out.data_ptr()))
+    return Batch(out, batch.offsets, batch.offsets_host)
+
+
 def pairwise_dtw(batch: Batch, opts=None, ws: Workspace | None = None) -> torch.Tensor:
     """[T, T] symmetric matrix of DTW costs between cycles."""
     lib = _abi.load()

@@ -20,6 +20,9 @@
 namespace wts {
 int run_probe(int which, double* ops_per_s);
 size_t compact_workspace_bytes(int64_t rows);
+cudaError_t launch_pad_last(const float* in, const int64_t* offsets, int T, int d, int64_t L, float* out,
+                            cudaStream_t st);
+cudaError_t launch_select_channel(const float* in, int64_t rows, int d, int c, float* out, cudaStream_t st);
 cudaError_t launch_compact_nan(const float* in, const int64_t* in_offsets, int T, int d, int64_t rows, float* out,
                                int64_t* out_offsets, void* ws, cudaStream_t st);
 namespace {
@@ -1076,6 +1079,44 @@ int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* wo
     }
     *best = best_o;
     if (best_ms) *best_ms = best_t;
+    return ok();
+}
+
+int wts_pad_last(const wts_batch* Y, int64_t L, void* stream, float* out)
+{
+    int rc = check_batch(Y, true);
+    if (rc) return rc;
+    if (!out) return fail(WTS_EINVAL, "out is NULL");
+    int64_t longest = 0;
+    for (int k = 0; k < Y->T; ++k) {
+        const int64_t n = Y->offsets_host[k + 1] - Y->offsets_host[k];
+        if (n > longest) longest = n;
+    }
+    if (L == 0) L = longest;
+    if (L < longest) return fail(WTS_EINVAL, "L=%lld is shorter than the longest cycle (%lld)", (long long)L,
+                                 (long long)longest);
+    if (L > ((int64_t)1 << 40) / ((int64_t)Y->T * Y->d)) return fail(WTS_EINVAL, "L=%lld too large", (long long)L);
+    cudaError_t e;
+    {
+        Prof pr("pad_last", (cudaStream_t)stream);
+        e = launch_pad_last(Y->data, Y->offsets, Y->T, Y->d, L, out, (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pad_last launch");
+    return ok();
+}
+
+int wts_select_channel(const wts_batch* Y, int32_t c, void* stream, float* out)
+{
+    int rc = check_batch(Y, true);
+    if (rc) return rc;
+    if (!out) return fail(WTS_EINVAL, "out is NULL");
+    if (c < 0 || c >= Y->d) return fail(WTS_EINVAL, "channel %d outside 0..%d", c, Y->d - 1);
+    cudaError_t e;
+    {
+        Prof pr("select_channel", (cudaStream_t)stream);
+        e = launch_select_channel(Y->data, Y->offsets_host[Y->T], Y->d, c, out, (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "select_channel launch");
     return ok();
 }
 

@@ -6,6 +6,11 @@
 // packed batch (block sums, one-block scan of the block sums, add back);
 // out[pos[t]] = in[t] for kept rows; out_offsets[k] = pos[in_offsets[k]].
 // Row order is preserved, so the result does not depend on scheduling.
+//
+// Two re-layouts for the paper's own forms of the data: last-value padding
+// (Sec. 4.1: every cycle extended with its last sample to a common length, as
+// the paper's Soft-DTW runs need) and the selection of one channel (the paper
+// aligns, averages and scores each joint on its own, Sec. 5).
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -116,7 +121,52 @@ __global__ void offsets_kernel(const int64_t* __restrict__ in_offsets, int T, in
     out_offsets[k] = block_sums[t / kScanBlock] + local;
 }
 
+// out[k][j][c] = in[offsets[k] + min(j, N_k - 1)][c]: one thread per output
+// float, consecutive threads on consecutive floats (coalesced writes; the
+// reads are the same rows, or the one last row, of one cycle).
+__global__ void pad_last_kernel(const float* __restrict__ in, const int64_t* __restrict__ offsets, int T, int d,
+                                int64_t L, float* __restrict__ out)
+{
+    const int64_t per = L * d;
+    const int64_t n = per * T;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = q / per;
+        const int64_t r = q - k * per;
+        const int64_t j = r / d;
+        const int c = (int)(r - j * d);
+        const int64_t o = __ldg(offsets + k), N = __ldg(offsets + k + 1) - o;
+        out[q] = __ldg(in + (o + (j < N ? j : N - 1)) * d + c);
+    }
+}
+
+// out[t] = in[t][c] over every sample of the packed batch.
+__global__ void select_channel_kernel(const float* __restrict__ in, int64_t rows, int d, int c,
+                                      float* __restrict__ out)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < rows; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = __ldg(in + t * d + c);
+}
+
+unsigned grid_for_elems(int64_t n)
+{
+    const int64_t g = (n + 255) / 256;
+    return (unsigned)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
 }  // namespace
+
+cudaError_t launch_pad_last(const float* in, const int64_t* offsets, int T, int d, int64_t L, float* out,
+                            cudaStream_t st)
+{
+    pad_last_kernel<<<grid_for_elems(L * d * T), 256, 0, st>>>(in, offsets, T, d, L, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_channel(const float* in, int64_t rows, int d, int c, float* out, cudaStream_t st)
+{
+    select_channel_kernel<<<grid_for_elems(rows), 256, 0, st>>>(in, rows, d, c, out);
+    return cudaGetLastError();
+}
 
 size_t compact_workspace_bytes(int64_t rows)
 {

@@ -679,3 +679,31 @@ def _l2_pins_fail(defines) -> bool:
 def test_planted_l2_mistakes_are_caught(plant):
     assert not _l2_pins_fail(())
     assert _l2_pins_fail((plant,))
+
+
+# --- the paper's data forms: last-value padding (Sec. 4.1), one joint (Sec. 5) --
+
+def test_pad_last_and_select_channel():
+    """Padding: the first N_k rows are the cycle, the rest repeat its last
+    sample; an equal-length batch is unchanged; DTW against a prototype whose
+    last sample equals the cycle's is unchanged by the padding (the extra
+    columns align to the last row at cost 0, and folding them back onto column
+    N gives a path of the unpadded pair that costs no more).  Channel
+    selection: the channels stacked back give the batch."""
+    rng = np.random.default_rng(71)
+    cyc = [rng.normal(size=(n, 3)).astype(np.float32) for n in (5, 9, 1, 7)]
+    data = np.concatenate(cyc); offs = np.array([0, 5, 14, 15, 22])
+    P = oracle.pad_last(data, offs)
+    assert P.shape == (4, 9, 3)
+    for k, y in enumerate(cyc):
+        assert (P[k, :len(y)] == y).all() and (P[k, len(y):] == y[-1]).all()
+    P12 = oracle.pad_last(data, offs, 12)
+    assert P12.shape == (4, 12, 3) and (P12[:, :9] == P).all()
+    eq = np.concatenate([rng.normal(size=(6, 2)).astype(np.float32) for _ in range(3)])
+    assert (oracle.pad_last(eq, np.array([0, 6, 12, 18])).reshape(-1, 2) == eq).all()
+    assert (np.stack([oracle.select_channel(data, c) for c in range(3)], 1) == data).all()
+    # DTW is unchanged by last-value padding when the prototype ends at the
+    # cycle's last value (the extra columns align to the last row at cost 0)
+    B = np.concatenate([rng.normal(size=(6, 3)).astype(np.float32), cyc[1][-1:]])
+    assert oracle.dtw(B, P[1][:9], "f64")["cost"] == oracle.dtw(B, cyc[1], "f64")["cost"]
+    assert oracle.dtw(B, P12[1], "f64")["cost"] == oracle.dtw(B, cyc[1], "f64")["cost"]
