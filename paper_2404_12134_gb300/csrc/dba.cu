@@ -35,7 +35,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
 // band, so a window of kBtWords / 32 consecutive word rows (one contiguous
 // block of global memory) is brought into shared memory by one bulk
 // asynchronous copy (completion on an mbarrier, bounded wait) and the walk
-// reads it; every lane walks the same path (broadcast reads), lane 0 writes.
+// reads it; every lane walks the same path, and the lanes look ahead along a
+// run of equal moves (one vote per run).
 // Row i's range is [jlo(i), jhi(i)]: jhi when the walk enters the row, jlo
 // when it leaves it (Definition "Alignment path": monotone, so each row's
 // columns are contiguous).
@@ -79,10 +80,7 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             ++len;
             if (i == 0 && j == 0) break;
             const int b = i >> (LOG_R + 5);
-            const int t = (i >> LOG_R) & 31;
-            const int k = i & (R - 1);
-            const int s = j + t;
-            const int row = s / SPW;
+            const int row = (j + ((i >> LOG_R) & 31)) / SPW;     // word row of step s = j + t
             if (b != band || row < wlo || row > whi) {
                 band = b;
                 whi = row;
@@ -109,12 +107,20 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
                     break;
                 }
             }
-            // plane 0 ("not diag") is bit k, plane 1 ("not up") bit R + k of
-            // the step's code bits of lane t
-            const uint32_t* wp = win + ((row - wlo) * 32 + t) * W;
-            const uint32_t w0 = R == 8 ? wp[0] >> ((s & 1) * 16) : wp[0];
-            const uint32_t nd = (w0 >> k) & 1u;
-            const uint32_t nu = R <= 16 ? (w0 >> (R + k)) & 1u : (wp[W - 1] >> k) & 1u;
+            // cell (ii, jj) of the window: lane t = (ii mod BR) / R, row k =
+            // ii mod R, step s = jj + t; plane 0 ("not diag") is bit k, plane 1
+            // ("not up") bit R + k of the step's code bits of lane t
+            auto code_at = [&](int ii, int jj, uint32_t& nd, uint32_t& nu) {
+                const int tt = (ii >> LOG_R) & 31;
+                const int kk = ii & (R - 1);
+                const int ss = jj + tt;
+                const uint32_t* wp = win + ((ss / SPW - wlo) * 32 + tt) * W;
+                const uint32_t w0 = R == 8 ? wp[0] >> ((ss & 1) * 16) : wp[0];
+                nd = (w0 >> kk) & 1u;
+                nu = R <= 16 ? (w0 >> (R + kk)) & 1u : (wp[W - 1] >> kk) & 1u;
+            };
+            uint32_t nd, nu;
+            code_at(i, j, nd, nu);
             // codes: diag (nd = 0) moves up-left, up (nd = 1, nu = 0) moves up,
             // left (nd = nu = 1) moves left
             const int di = (nd == 0u || nu == 0u) ? 1 : 0;
@@ -124,12 +130,35 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             // a valid code matrix only moves left on row 0 and only up on
             // column 0; anything else is reported as |pi| = -1
             if ((i == 0 && di) || (j == 0 && dj)) { len = -1; break; }
-            if (di && lane == 0) {
-                jlo[i] = j;
-                jhi[i - 1] = j - dj;
+            // Runs: lane u > 0 reads the cell c_u = (i - u di, j - u dj) that u
+            // more moves of the same kind would reach, and agrees if that cell
+            // is in the window, codes the same move, and the move from it is an
+            // ordinary one (not the path's start, not out of the grid, not out
+            // of the rows loaded).  The moves of c_0 .. c_{run-1} are then
+            // taken at once, run = the first lane that does not agree: the same
+            // walk as one cell at a time, with one shared-memory round trip and
+            // one vote per run; lane u writes the rows that c_u leaves.
+            const int iu = i - lane * di, ju = j - lane * dj;
+            bool agree = false;
+            if (lane > 0 && iu >= 0 && ju >= 0 && (iu | ju) != 0 && (iu >> (LOG_R + 5)) == band) {
+                const int ru = (ju + ((iu >> LOG_R) & 31)) / SPW;
+                if (ru >= wlo && ru <= whi) {
+                    uint32_t ndu, nuu;
+                    code_at(iu, ju, ndu, nuu);
+                    const int diu = (ndu == 0u || nuu == 0u) ? 1 : 0;
+                    const int dju = (ndu == 0u || nuu == 1u) ? 1 : 0;
+                    agree = diu == di && dju == dj && !(iu == 0 && di) && !(ju == 0 && dj) && iu - di >= i_lo;
+                }
             }
-            i -= di;
-            j -= dj;
+            const uint32_t votes = __ballot_sync(FULL, agree) | 1u;
+            const int run = votes == FULL ? 32 : __ffs(~votes) - 1;
+            if (di && lane < run) {
+                jlo[iu] = ju;
+                jhi[iu - 1] = ju - dj;
+            }
+            i -= run * di;
+            j -= run * dj;
+            len += run - 1;
             if (i < i_lo) { left_group = true; break; }    // the rest lies in bands not loaded
         }
         if (left_group) {
