@@ -229,6 +229,9 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         if (opt && opt->dir_mode == 1) {
             L->group_bands = opt->ckpt_bands ? opt->ckpt_bands : 16;
             L->off_btstate = take((size_t)L->T * 3 * sizeof(int32_t));
+        } else if (op != kOpSubdtw) {
+            L->nseg = (int)cdiv(M, kBtSegRows);
+            L->off_seg = take((size_t)L->P * L->nseg * 4 * sizeof(int32_t));
         }
     }
     if (op == kOpDba) {
@@ -387,9 +390,19 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
         if (rc) return rc;
         bt.band_lo = 0;
         bt.band_hi = (int)cdiv(L.M, L.BR);
+        // segmented walk: nseg rounds (a round only re-walks the segments
+        // whose start changed), then |pi| from the ranges
+        bt.nseg = L.nseg;
+        bt.seg_rows = kBtSegRows;
+        bt.seg = reinterpret_cast<int32_t*>(ws + L.off_seg);
         {
             Prof pr("backtrack", st);
-            e = launch_backtrack(bt, st);
+            for (int r = 0; r < L.nseg; ++r) {
+                bt.round = r;
+                e = launch_backtrack(bt, st);
+                if (e != cudaSuccess) break;
+            }
+            if (e == cudaSuccess) e = launch_backtrack_seg_final(bt, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "backtrack launch");
         return WTS_OK;

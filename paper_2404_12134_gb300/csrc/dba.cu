@@ -60,20 +60,55 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
     __syncwarp();
     uint32_t phase = 0;
     bool failed = false;
-    for (int q = blockIdx.x * kBtWarps + wid; q < p.P && !failed; q += gridDim.x * kBtWarps) {
+    const int units = p.nseg > 0 ? p.P * p.nseg : p.P;
+    for (int u = blockIdx.x * kBtWarps + wid; u < units && !failed; u += gridDim.x * kBtWarps) {
+        const int q = p.nseg > 0 ? u / p.nseg : u;
         const PairDesc pd = p.pairs[q];
         const int N = pd.N;
         int32_t* jlo = p.jlo + (int64_t)pd.out * p.M;
         int32_t* jhi = p.jhi + (int64_t)pd.out * p.M;
         int i, j, len;
-        if (p.state == nullptr || p.first) {
+        int i_lo = p.band_lo * 32 * R;
+        int32_t* sg = p.nseg > 0 ? p.seg + 4 * (int64_t)u : nullptr;
+        const int cur = p.round & 1;
+        if (p.nseg > 0) {
+            // segment sk: rows [sk * seg_rows, top]; the last one holds (M-1, N-1)
+            const int sk = u - q * p.nseg;
+            const int top = min(pd.M, (sk + 1) * p.seg_rows) - 1;
+            i_lo = sk * p.seg_rows;
+            int start;
+            if (top == pd.M - 1) {
+                if (p.round > 0) {                   // walked from the path's end in round 0
+                    if (lane == 0) sg[1 + cur] = sg[2 - cur];
+                    continue;
+                }
+                start = N - 1;
+            } else if (p.round == 0) {
+                // a guess: the column this row was entered at by the previous
+                // walk of this pair (the ranges of an earlier call on the same
+                // arrays; any value is safe), else the diagonal
+                start = jhi[top];
+                if (start < 0 || start >= N) start = (int)((int64_t)top * (N - 1) / max(pd.M - 1, 1));
+            } else {
+                start = p.seg[4 * (int64_t)(u + 1) + 2 - cur];     // exit of the segment above, last round
+                if (start == sg[0]) {                // unchanged: the walk recorded stands
+                    if (lane == 0) sg[1 + cur] = sg[2 - cur];
+                    continue;
+                }
+            }
+            if (start < 0 || start >= N) {           // the segment above failed
+                if (lane == 0) { sg[0] = start; sg[1 + cur] = -1; sg[3] = 1; }
+                continue;
+            }
+            i = top; j = start; len = 0;
+            if (lane == 0) { jhi[i] = j; sg[0] = start; }
+        } else if (p.state == nullptr || p.first) {
             i = pd.M - 1; j = p.subseq ? p.bstar[pd.out] : N - 1; len = 0;
             if (lane == 0) jhi[i] = j;
         } else {
             i = p.state[3 * q]; j = p.state[3 * q + 1]; len = p.state[3 * q + 2];
             if (i < 0 || len < 0) continue;          // finished, or failed earlier
         }
-        const int i_lo = p.band_lo * 32 * R;
         int band = -1, wlo = 0, whi = -1;           // word rows in the window
         bool left_group = false;
         for (;;) {
@@ -161,6 +196,14 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             len += run - 1;
             if (i < i_lo) { left_group = true; break; }    // the rest lies in bands not loaded
         }
+        if (sg != nullptr) {
+            if (lane == 0) {
+                sg[1 + cur] = left_group ? j : -1;    // the path's column in the row below
+                sg[3] = len < 0 ? 1 : 0;
+                if (!left_group && i == 0 && j == 0 && len > 0) jlo[0] = 0;
+            }
+            continue;
+        }
         if (left_group) {
             if (lane == 0) { p.state[3 * q] = i; p.state[3 * q + 1] = j; p.state[3 * q + 2] = len; }
             continue;
@@ -176,6 +219,34 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             if (p.state) { p.state[3 * q] = -1; p.state[3 * q + 2] = len; }
         }
     }
+}
+
+// One warp per pair, after the last round of a segmented walk: the segments
+// must join up (each one's start = the exit of the one above) and none may
+// have failed; then |pi| = sum_i (jhi(i) - jlo(i) + 1), the cells of a monotone
+// path being row by row contiguous.
+__global__ void __launch_bounds__(128) bt_seg_final_kernel(BTParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (q >= p.P) return;
+    const PairDesc pd = p.pairs[q];
+    const int last = (p.round & 1);                  // exit slot of the last round
+    const int nseg = (int)((pd.M + p.seg_rows - 1) / p.seg_rows);
+    bool bad = false;
+    for (int k = lane; k < nseg; k += 32) {
+        const int32_t* sg = p.seg + 4 * ((int64_t)q * p.nseg + k);
+        if (sg[3] != 0) bad = true;
+        if (k + 1 < nseg && sg[0] != p.seg[4 * ((int64_t)q * p.nseg + k + 1) + 1 + last]) bad = true;
+    }
+    bad = __any_sync(FULL, bad);
+    const int32_t* jlo = p.jlo + (int64_t)pd.out * p.M;
+    const int32_t* jhi = p.jhi + (int64_t)pd.out * p.M;
+    long long cells = 0;
+    for (int i = lane; i < pd.M; i += 32) cells += (long long)(jhi[i] - jlo[i] + 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(FULL, cells, o);
+    if (lane == 0 && p.plen) p.plen[pd.out] = bad ? -1 : (int32_t)cells;
 }
 
 // One thread per (prototype row i, channel c); the sum of channel c of row i
@@ -297,12 +368,21 @@ cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int need = (p.P + kBtWarps - 1) / kBtWarps;
-    const int grid = need < 4 * sms ? need : 4 * sms;
+    const int units = p.nseg > 0 ? p.P * p.nseg : p.P;
+    const int need = (units + kBtWarps - 1) / kBtWarps;
+    const int cap = (p.nseg > 0 ? 8 : 4) * sms;
+    const int grid = need < cap ? need : cap;
     if (p.R == 8) backtrack_kernel<8><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else if (p.R == 16) backtrack_kernel<16><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else if (p.R == 32) backtrack_kernel<32><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backtrack_seg_final(const BTParams& p, cudaStream_t st)
+{
+    const int warps = 4;
+    bt_seg_final_kernel<<<(p.P + warps - 1) / warps, 32 * warps, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -27,9 +27,25 @@ struct BTParams {
     int subseq;
     const int32_t* bstar;
     int32_t* astar;
+    // segmented walk (every code stored, not Sub-DTW): the rows are cut into
+    // nseg segments of seg_rows rows, walked at once, each from a start column
+    // in its top row; round r re-walks a segment whose start differs from the
+    // exit of the segment above in round r - 1, so after nseg rounds every
+    // segment starts where the path enters it.  seg[(q * nseg + k) * 4 + ..] =
+    // {start column, exit column in even rounds, in odd rounds, status (1 = the
+    // codes were invalid or a wait gave up)}; the exit is the path's column in
+    // the row below the segment.
+    int nseg, seg_rows, round;
+    int32_t* seg;
 };
 
+// Rows per segment of the segmented walk.
+constexpr int kBtSegRows = 2048;
+
 cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st);
+// After the nseg rounds of a segmented walk: |pi| = sum_i (jhi(i) - jlo(i) + 1)
+// per pair, or -1 if a segment failed or the segments do not join up.
+cudaError_t launch_backtrack_seg_final(const BTParams& p, cudaStream_t st);
 
 // B_out[i] = mean of the cycle samples aligned to row i over all cycles;
 // counts[i] = number of aligned samples; cost_before = sum_k costs[k].

@@ -54,6 +54,8 @@ struct Layout {
     int group_bands = 0;  // checkpoint mode: bands whose codes are recomputed at a time (0 = codes stored)
     int banded = 0;       // a Sakoe-Chiba band applies (the banded kernels run with R = 16)
     int cost_kind = 0;    // local cost: 0 squared l2, 1 the l2 norm (DTW kernels with R = 16)
+    int nseg = 0;         // segments of the segmented backtrack (codes stored, not Sub-DTW)
+    size_t off_seg = 0;
 
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
     size_t total = 0;

@@ -120,7 +120,9 @@ def test_subdtw_workspace_and_validation(lib):
     b, offs = _batch([1200, 37], d=9)
     rc, sub = _size(lib, _abi.OP_SUBDTW, 600, b)
     rc2, align = _size(lib, _abi.OP_DTW_ALIGN, 600, b)
-    assert rc == 0 and rc2 == 0 and sub >= align        # the same codes, plus nothing smaller
+    # the same codes; dtw_align adds the segmented walk's state (16 bytes per
+    # pair and segment of 2048 rows, in a 256-byte aligned block)
+    assert rc == 0 and rc2 == 0 and sub + 256 >= align
     o = _abi.wts_options()
     o.rows_per_thread = 8
     assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == 0
