@@ -166,7 +166,13 @@ int anomaly_score(const float* B, int64_t M, const wts_batch* Y, const wts_optio
  * visits each row on one contiguous run of columns), and |pi_k| = sum_i
  * (jhi - jlo + 1).
  *   cost [T], plen [T]           out (either may be NULL)
- *   jlo  [T][M], jhi [T][M]      out (int32)
+ *   jlo  [T][M], jhi [T][M]      out (int32); with every code stored
+ *                                (dir_mode 0) the walk reads the jhi values
+ *                                found there on entry as guesses of where
+ *                                the path enters rows 2048 apart (a repeated
+ *                                call on the same arrays walks faster); any
+ *                                contents are safe and the result does not
+ *                                depend on them
  * A 2-bit predecessor code per cell is kept in the workspace (M*N_k/4 bytes
  * per cycle, plus a skew margin); wts_workspace_size(WTS_OP_DTW_ALIGN, ...).
  */

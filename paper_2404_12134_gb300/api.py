@@ -188,8 +188,11 @@ def anomaly_score_noalloc(B: torch.Tensor, batch: Batch, opts=None):
     return score, cost, plen
 
 
-def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None):
-    """DTW and tie-rule path per cycle: (cost [T], plen [T], jlo [T, M], jhi [T, M])."""
+def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None,
+              jlo: torch.Tensor | None = None, jhi: torch.Tensor | None = None):
+    """DTW and tie-rule path per cycle: (cost [T], plen [T], jlo [T, M], jhi [T, M]).
+    jlo / jhi may be given (int32 [T, M], written in place); the ranges they
+    hold on entry serve the walk as guesses (the previous call's paths)."""
     B = _check_B(B, batch.d)
     M = B.shape[0]
     lib = _abi.load()
@@ -198,8 +201,12 @@ def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = N
     dev = B.device
     cost = torch.empty(batch.T, dtype=torch.float32, device=dev)
     plen = torch.empty(batch.T, dtype=torch.int32, device=dev)
-    jlo = torch.empty((batch.T, M), dtype=torch.int32, device=dev)
-    jhi = torch.empty((batch.T, M), dtype=torch.int32, device=dev)
+    for t in (jlo, jhi):
+        if t is not None and not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
+                                  and tuple(t.shape) == (batch.T, M)):
+            raise ValueError("jlo / jhi must be contiguous int32 CUDA tensors of shape [T, M]")
+    jlo = torch.empty((batch.T, M), dtype=torch.int32, device=dev) if jlo is None else jlo
+    jhi = torch.empty((batch.T, M), dtype=torch.int32, device=dev) if jhi is None else jhi
     check(lib.dtw_align(B.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts), buf.data_ptr(), buf.numel(),
                         _stream(), cost.data_ptr(), plen.data_ptr(), jlo.data_ptr(), jhi.data_ptr()))
     return cost, plen, jlo, jhi

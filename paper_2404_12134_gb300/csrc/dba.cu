@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
         int i_lo = p.band_lo * 32 * R;
         int32_t* sg = p.nseg > 0 ? p.seg + 4 * (int64_t)u : nullptr;
         const int cur = p.round & 1;
+        bool mergeable = false, merged = false;
+        int prev_exit = -1;
         if (p.nseg > 0) {
             // segment sk: rows [sk * seg_rows, top]; the last one holds (M-1, N-1)
             const int sk = u - q * p.nseg;
@@ -98,6 +100,17 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             }
             if (start < 0 || start >= N) {           // the segment above failed
                 if (lane == 0) { sg[0] = start; sg[1 + cur] = -1; sg[3] = 1; }
+                continue;
+            }
+            // A re-walk (round > 0) stops where it enters the previous walk of
+            // this segment, whose ranges the arrays hold: from a shared cell
+            // the walks are the same.  Row top of that walk is [jlo(top), old
+            // start].
+            mergeable = p.round > 0 && sg[3] == 0;
+            prev_exit = sg[2 - cur];
+            if (mergeable && jlo[top] <= start && start <= sg[0]) {
+                __syncwarp();
+                if (lane == 0) { jhi[top] = start; sg[0] = start; sg[1 + cur] = prev_exit; }
                 continue;
             }
             i = top; j = start; len = 0;
@@ -186,7 +199,16 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
                 }
             }
             const uint32_t votes = __ballot_sync(FULL, agree) | 1u;
-            const int run = votes == FULL ? 32 : __ffs(~votes) - 1;
+            int run = votes == FULL ? 32 : __ffs(~votes) - 1;
+            // a re-walk: does the move of c_u enter a row at a cell of the
+            // previous walk (read before this run's writes)?
+            bool mg = false;
+            if (mergeable && di && lane < run && iu - 1 >= i_lo) {
+                const int je = ju - dj;
+                mg = jlo[iu - 1] <= je && je <= jhi[iu - 1];
+            }
+            const uint32_t mv = __ballot_sync(FULL, mg);
+            if (mv) run = __ffs(mv);                 // up to and including the first such move
             if (di && lane < run) {
                 jlo[iu] = ju;
                 jhi[iu - 1] = ju - dj;
@@ -194,13 +216,18 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             i -= run * di;
             j -= run * dj;
             len += run - 1;
+            if (mv) { merged = true; break; }
             if (i < i_lo) { left_group = true; break; }    // the rest lies in bands not loaded
         }
         if (sg != nullptr) {
             if (lane == 0) {
-                sg[1 + cur] = left_group ? j : -1;    // the path's column in the row below
-                sg[3] = len < 0 ? 1 : 0;
-                if (!left_group && i == 0 && j == 0 && len > 0) jlo[0] = 0;
+                if (merged) {
+                    sg[1 + cur] = prev_exit;          // the rest is the previous walk's
+                } else {
+                    sg[1 + cur] = left_group ? j : -1;    // the path's column in the row below
+                    sg[3] = len < 0 ? 1 : 0;
+                    if (!left_group && i == 0 && j == 0 && len > 0) jlo[0] = 0;
+                }
             }
             continue;
         }

@@ -271,3 +271,48 @@ def test_half_word_codes(wts, d):
     Bn, cnt, cb, ck = wts.dba_iterate(Bt, gb, o8)
     Bo, cnt_o, cb_o, ck_o = oracle.dba_iterate(B, data, offs, "f32")
     assert (Bn.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all()
+
+
+def test_segmented_walk_any_guess(wts):
+    """Prototype rows cut into three 2048-row segments, walked at once: the
+    paths are the oracle's whatever the range arrays hold on entry (the walk
+    reads them as guesses): all columns 0, invalid values, the right answer,
+    a wrong path; and DBA iterations reusing their workspace."""
+    rng = np.random.default_rng(77)
+    d = 3
+    M = 5000
+    walk = lambda n: np.cumsum(rng.normal(size=(n, d)), 0).astype(np.float32) * 0.1
+    B = walk(M)
+    cyc = [walk(n) for n in (4000, 5200, 6100, 1, 2047)]
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    Bt = torch.from_numpy(B).cuda()
+    ref = [oracle.dtw(B, y, "f32", path=False) for y in cyc]
+    T = len(cyc)
+    ws = wts.Workspace()
+
+    def check(jlo, jhi):
+        c, pl, lo, hi = wts.dtw_align(Bt, gb, ws=ws, jlo=jlo, jhi=jhi)
+        c, pl, lo, hi = (t.cpu().numpy() for t in (c, pl, lo, hi))
+        for k, r in enumerate(ref):
+            assert c[k] == r["cost"] and pl[k] == r["plen"], k
+            assert (lo[k] == r["jlo"]).all() and (hi[k] == r["jhi"]).all(), k
+        return lo, hi
+
+    z = torch.zeros((T, M), dtype=torch.int32, device="cuda")
+    check(z.clone(), z.clone())
+    check(torch.full((T, M), -7, dtype=torch.int32, device="cuda"), torch.full((T, M), 1 << 30, dtype=torch.int32,
+                                                                            device="cuda"))
+    lo, hi = check(None, None)
+    good_lo, good_hi = torch.from_numpy(lo).cuda(), torch.from_numpy(hi).cuda()
+    check(good_lo.clone(), good_hi.clone())
+    # another pair's path as the guess
+    check(good_lo.roll(1, 0).contiguous(), good_hi.roll(1, 0).contiguous())
+    # DBA iterations on one workspace: each walk guesses from the previous one
+    wsd = wts.Workspace()
+    Bc = B.copy()
+    for _ in range(2):
+        Bn, cnt, cb, ck = wts.dba_iterate(torch.from_numpy(Bc).cuda(), gb, ws=wsd)
+        Bo, cnt_o, cb_o, _ = oracle.dba_iterate(Bc, data, offs, "f32")
+        assert (Bn.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all() and float(cb) == cb_o
+        Bc = Bo
