@@ -129,10 +129,12 @@ int wts_read_status(const void* workspace, void* stream, int32_t* status);
  * stream (library-owned events, created per launch).  Host-only switch. */
 int wts_profile_enable(int enable);
 
-/* Sum of the recorded durations (ms) and launch count of one kernel
+/* Sum of the recorded durations (ms) and kernel launches of one stage
  * ("setup", "wavefront", "backtrack", "dba_average", "softdtw_fwd",
- * "softdtw_bwd", "softdtw_grad"; "" = all), then forget those records.
- * Waits for the recorded events to complete. */
+ * "softdtw_bwd", "softdtw_grad"; "" = all), then forget those records.  A
+ * stage may launch several kernels (the segmented backtrack: one per round
+ * and a last one); `launches` counts them all.  Waits for the recorded events
+ * to complete. */
 int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches);
 
 /* Measured roofline denominators (not part of the method): lane operations

@@ -56,6 +56,7 @@ int cuda_fail(cudaError_t e, const char* what)
 struct ProfRec {
     std::string name;
     cudaEvent_t a, b;
+    int kernels;
 };
 std::mutex g_prof_mu;
 bool g_prof = false;
@@ -65,6 +66,7 @@ struct Prof {
     cudaEvent_t a = nullptr, b = nullptr;
     cudaStream_t st;
     const char* name;
+    int kernels = 1;             // kernel launches inside the region
     Prof(const char* n, cudaStream_t s) : st(s), name(n)
     {
         std::lock_guard<std::mutex> g(g_prof_mu);
@@ -77,7 +79,7 @@ struct Prof {
         if (!a) return;
         cudaEventRecord(b, st);
         std::lock_guard<std::mutex> g(g_prof_mu);
-        g_recs.push_back({name, a, b});
+        g_recs.push_back({name, a, b, kernels});
     }
 };
 
@@ -397,6 +399,7 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
         bt.seg = reinterpret_cast<int32_t*>(ws + L.off_seg);
         {
             Prof pr("backtrack", st);
+            pr.kernels = L.nseg + 1;
             for (int r = 0; r < L.nseg; ++r) {
                 bt.round = r;
                 e = launch_backtrack(bt, st);
@@ -517,7 +520,9 @@ int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches)
     }
     double tot = 0;
     int err = WTS_OK;
+    int32_t kernels = 0;
     for (auto& r : mine) {
+        kernels += r.kernels;
         float ms = 0;
         cudaError_t e = cudaEventSynchronize(r.b);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
@@ -527,7 +532,7 @@ int wts_profile_read(const char* kernel, double* total_ms, int32_t* launches)
         cudaEventDestroy(r.b);
     }
     *total_ms = tot;
-    *launches = (int32_t)mine.size();
+    *launches = kernels;
     return err ? err : ok();
 }
 
