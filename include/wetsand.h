@@ -314,7 +314,11 @@ int wts_softdtw_barycenter_lbfgs(float* B, int64_t M, const wts_batch* Y, float 
  *   B_in [M][d], B_out [M][d] (must not alias B_in)
  *   counts [M] out (may be NULL), cost_before: one double, out (may be NULL),
  *   cost [T] out (may be NULL): DTW(B_in, Y_k)
- * Workspace: wts_workspace_size(WTS_OP_DBA_ITERATE, ...).
+ * Workspace: wts_workspace_size(WTS_OP_DBA_ITERATE, ...).  The paths are kept
+ * in the workspace; with every code stored (dir_mode 0) the next call on the
+ * same workspace and batch starts its walk from them as guesses (faster
+ * between DBA iterations, whose paths move little); any workspace contents
+ * give the same result.
  */
 int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, const wts_options* opt,
                 void* workspace, size_t workspace_bytes, void* stream,
