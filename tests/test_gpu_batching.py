@@ -85,3 +85,24 @@ def test_one_launch_per_pair_matches_batched(wts):
         one = wts.Batch(gb.data[o0:o1], torch.tensor([0, o1 - o0], device="cuda"), np.array([0, o1 - o0]))
         sk, ck, Lk = wts.anomaly_score(Bt, one)
         assert float(ck[0]) == float(c[k]) and int(Lk[0]) == int(L[k])
+
+
+def test_segmented_dba_iteration_in_a_graph(wts):
+    """A prototype of three 2048-row segments: the segmented walk's rounds and
+    its last kernel are captured with the rest of the iteration; each replay
+    guesses from the paths the previous replay left in the workspace."""
+    rng = np.random.default_rng(55)
+    walk = lambda n: (np.cumsum(rng.normal(size=(n, 2)), 0) * 0.05).astype(np.float32)
+    cyc = [walk(n) for n in (4100, 4700, 3900)]
+    b = synth.pack(cyc)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    B0 = walk(4500)
+    Bin = torch.from_numpy(B0).cuda()
+    ws = wts.Workspace()
+    g, (Bout, cnt, cb, ck) = wts.capture(lambda: wts.dba_iterate(Bin, gb, ws=ws))
+    Bo = B0
+    for it in range(3):
+        g.replay()
+        Bo, cnt_o, cb_o, _ = oracle.dba_iterate(Bo, b.data, b.offsets, "f32")
+        assert (Bout.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all() and float(cb) == cb_o, it
+        Bin.copy_(Bout)
