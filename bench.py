@@ -446,7 +446,7 @@ def segment_leg(api, torch, dev, barrier, K: int = 36, cpu_window: bool = True):
     reference cycle of ~16,300 samples x 9 channels, a stream of K cycles
     (pre-gap U(15k, 18k), ~6e5 samples), windows of 2M, alpha = 0.15 M.  The
     whole loop (one Sub-DTW launch pair per window, the window bounds read
-    back each time) is timed from the host, for 16 and 8 rows per lane; one
+    back each time) is timed from the host, for 16, 8 and 4 rows per lane; one
     2M-column window is also timed on the device, and once by the oracle on
     the host (the CPU baseline of this leg)."""
     import oracle
@@ -457,7 +457,7 @@ def segment_leg(api, torch, dev, barrier, K: int = 36, cpu_window: bool = True):
     res = {"workload": f"reference {M} x 9 ch, stream {N} samples ({K} cycles, pre-gap U(15k,18k), 2% gaps), "
                        f"windows of 2M, alpha = {alpha}", "M": M, "N": N}
     segs = None
-    for rows in (16, 8):
+    for rows in (16, 8, 4):
         opt = api.options(rows_per_thread=rows)
         ws = api.Workspace(dev)
         api.segment(Xt, Yt[:4 * M], alpha, opt, ws=ws)            # warm-up

@@ -75,7 +75,8 @@ typedef struct wts_batch {
 
 /* Launch options; a zeroed struct (or NULL) selects the defaults. */
 typedef struct wts_options {
-    int32_t rows_per_thread;       /* prototype rows held per lane: 0 = default (32 if d <= 2, else 16); 8, 16 or 32 (32 needs d <= 3) */
+    int32_t rows_per_thread;       /* prototype rows held per lane: 0 = default (32 if d <= 2, else 16); 8, 16 or 32 (32 needs d <= 3);
+                                      4 for Sub-DTW only */
     int32_t warps_per_block;       /* 0 = 4; 1..4 */
     int32_t max_blocks;            /* 0 = as many as are resident at once (persistent grid); else a cap */
     int32_t keep_batch_order;      /* 0 = schedule the longest pairs first; 1 = batch order */
@@ -195,7 +196,7 @@ int dtw_align(const float* B, int64_t M, const wts_batch* Y, const wts_options* 
  *   a_star, b_star [T]           out (int32), 0-based inclusive bounds in Y_k
  *   plen [T]                     out, |pi| (may be NULL)
  *   jlo, jhi [T][M]              out (int32), columns of each row of X
- * rows_per_thread must be 0 (16), 8 or 16 (0 or 16 with cost_kind = 1);
+ * rows_per_thread must be 0 (16), 4, 8 or 16 (0 or 16 with cost_kind = 1);
  * dir_mode 1 (checkpointing) is not offered.
  * Workspace: wts_workspace_size(WTS_OP_SUBDTW, M, Y, ...).
  */
@@ -223,10 +224,10 @@ int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_option
  * (the stream is synchronised once per window) and its backtrack (a*) runs on
  * a second stream of the library's, beside the next window's wavefront; the
  * workspace holds two window slots.  On return `stream` is ordered after all
- * of the call's work.  A window is
- * a single pair, so rows_per_thread = 0 means 8 here (twice the warps of 16,
- * half the serial chain per step; 16 with cost_kind = 1).  Workspace: wts_segment_workspace_size
- * (with the same options).
+ * of the call's work.  A window is a single pair, so rows_per_thread = 0
+ * means 4 here (four times the warps of 16, a quarter of the serial chain per
+ * step; 16 with cost_kind = 1).  Workspace: wts_segment_workspace_size (with
+ * the same options).
  */
 int wts_segment_workspace_size(int64_t M, int32_t d, const wts_options* opt, size_t* bytes);
 int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_t d, int64_t alpha,

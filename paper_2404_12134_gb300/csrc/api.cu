@@ -116,8 +116,9 @@ int check_batch(const wts_batch* Y, bool need_device)
 int check_opt(const wts_options* opt, int D)
 {
     if (!opt) return WTS_OK;
-    if (opt->rows_per_thread && opt->rows_per_thread != 8 && opt->rows_per_thread != 16 && opt->rows_per_thread != 32)
-        return fail(WTS_EINVAL, "rows_per_thread must be 0, 8, 16 or 32");
+    if (opt->rows_per_thread && opt->rows_per_thread != 4 && opt->rows_per_thread != 8 &&
+        opt->rows_per_thread != 16 && opt->rows_per_thread != 32)
+        return fail(WTS_EINVAL, "rows_per_thread must be 0, 4 (Sub-DTW), 8, 16 or 32");
     if (opt->rows_per_thread == 32 && D > 3) return fail(WTS_EINVAL, "rows_per_thread=32 needs d <= 3");
     if (opt->warps_per_block < 0 || opt->warps_per_block > 4) return fail(WTS_EINVAL, "warps_per_block must be 0..4");
     if (opt->max_blocks < 0) return fail(WTS_EINVAL, "max_blocks must be >= 0");
@@ -148,11 +149,14 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->d = Y->d;
     L->D = D;
     L->R = pick_R(D, opt);
+    if (op != kOpSubdtw && opt && opt->rows_per_thread == 4)
+        return fail(WTS_EINVAL, "rows_per_thread = 4 is for Sub-DTW only");
     if (op == kOpSubdtw) {
-        if (opt && opt->rows_per_thread && opt->rows_per_thread != 16 && opt->rows_per_thread != 8)
-            return fail(WTS_EINVAL, "Sub-DTW runs with rows_per_thread = 8 or 16 (got %d)", opt->rows_per_thread);
+        if (opt && opt->rows_per_thread && opt->rows_per_thread != 16 && opt->rows_per_thread != 8 &&
+            opt->rows_per_thread != 4)
+            return fail(WTS_EINVAL, "Sub-DTW runs with rows_per_thread = 4, 8 or 16 (got %d)", opt->rows_per_thread);
         if (opt && opt->dir_mode == 1) return fail(WTS_EINVAL, "Sub-DTW keeps every code (dir_mode must be 0)");
-        L->R = (opt && opt->rows_per_thread == 8) ? 8 : 16;
+        L->R = (opt && (opt->rows_per_thread == 8 || opt->rows_per_thread == 4)) ? opt->rows_per_thread : 16;
     }
     if (op == kOpSoft) {
         if (D > 8) return fail(WTS_EINVAL, "soft-DTW supports d <= 8 (got %d)", Y->d);
@@ -712,12 +716,12 @@ int segment_layout(int64_t M, int32_t d, const wts_options* opt, SegLayout* S)
 }
 
 // One window is one pair: the wavefront has only M / (32 R) warps, so the
-// shorter serial chain of 8 rows per lane (twice the warps) is the default
-// (16 with the l2-norm cost, whose kernels hold 16 rows per lane).
+// shorter serial chain of 4 rows per lane (four times the warps of 16) is the
+// default (16 with the l2-norm cost, whose kernels hold 16 rows per lane).
 wts_options segment_options(const wts_options* opt)
 {
     wts_options o = opt ? *opt : wts_options{};
-    if (o.rows_per_thread == 0) o.rows_per_thread = o.cost_kind == WTS_COST_L2 ? 16 : 8;
+    if (o.rows_per_thread == 0) o.rows_per_thread = o.cost_kind == WTS_COST_L2 ? 16 : 4;
     return o;
 }
 

@@ -29,9 +29,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
 // A cell (i, j) of band b sits in lane t = (i mod BR) / R at step s = j + t,
 // as bit k = i mod R ("not diag") and bit R + k ("not up") of the lane's 2R
 // code bits of that step.  For R >= 16 those are the W = R / 16 words at
-// dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]; for R = 8 the word
-// dirs[dir_off + b*((N+32)/2)*32 + (s/2)*32 + t] holds steps s and s+1 of the
-// lane (the even step in bits 0..15).  Along the walk s only decreases inside a
+// dirs[dir_off + b*(N+31)*32*W + (s*32 + t)*W + w]; for R = 8 and 4 the word
+// dirs[dir_off + b*band_dir_words(N, R) + (s/S)*32 + t] holds the S = 32/(2R)
+// steps S*(s/S) .. of the lane (2R bits each, the earliest in the lowest
+// bits).  Along the walk s only decreases inside a
 // band, so a window of kBtWords / 32 consecutive word rows (one contiguous
 // block of global memory) is brought into shared memory by one bulk
 // asynchronous copy (completion on an mbarrier, bounded wait) and the walk
@@ -44,8 +45,8 @@ template <int R>
 __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
 {
     constexpr int W = R >= 16 ? R / 16 : 1;         // words per (word row, lane)
-    constexpr int SPW = R >= 16 ? 1 : 2;            // steps per word row
-    constexpr int LOG_R = R == 8 ? 3 : (R == 16 ? 4 : 5);
+    constexpr int SPW = R >= 16 ? 1 : 32 / (2 * R); // steps per word row
+    constexpr int LOG_R = R == 4 ? 2 : (R == 8 ? 3 : (R == 16 ? 4 : 5));
     constexpr int kBtRows = kBtWords / (32 * W);    // word rows of one band in the window
     __shared__ __align__(128) uint32_t win_all[kBtWarps][kBtWords];
     __shared__ __align__(8) uint64_t bars[kBtWarps];
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
                 const int kk = ii & (R - 1);
                 const int ss = jj + tt;
                 const uint32_t* wp = win + ((ss / SPW - wlo) * 32 + tt) * W;
-                const uint32_t w0 = R == 8 ? wp[0] >> ((ss & 1) * 16) : wp[0];
+                const uint32_t w0 = R < 16 ? wp[0] >> ((ss % SPW) * 2 * R) : wp[0];
                 nd = (w0 >> kk) & 1u;
                 nu = R <= 16 ? (w0 >> (R + kk)) & 1u : (wp[W - 1] >> kk) & 1u;
             };
@@ -399,7 +400,8 @@ cudaError_t launch_backtrack(const BTParams& p, cudaStream_t st)
     const int need = (units + kBtWarps - 1) / kBtWarps;
     const int cap = (p.nseg > 0 ? 8 : 4) * sms;
     const int grid = need < cap ? need : cap;
-    if (p.R == 8) backtrack_kernel<8><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    if (p.R == 4) backtrack_kernel<4><<<grid, 32 * kBtWarps, 0, st>>>(p);
+    else if (p.R == 8) backtrack_kernel<8><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else if (p.R == 16) backtrack_kernel<16><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else if (p.R == 32) backtrack_kernel<32><<<grid, 32 * kBtWarps, 0, st>>>(p);
     else return cudaErrorInvalidValue;

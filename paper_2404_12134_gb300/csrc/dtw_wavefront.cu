@@ -14,6 +14,7 @@ cudaError_t launch_dtw_wavefront(int mode, int D, int R, const DPParams& p, int 
     if (p.cost_kind != kCostSqEuclid) return cudaErrorInvalidValue;
     if (p.banded) return R == 16 ? wf_launch_r16b(mode, D, p, grid, block, st) : cudaErrorInvalidValue;
     switch (R) {
+        case 4: return wf_launch_r4(mode, D, p, grid, block, st);
         case 8: return wf_launch_r8(mode, D, p, grid, block, st);
         case 16: return wf_launch_r16(mode, D, p, grid, block, st);
         case 32: return wf_launch_r32(mode, D, p, grid, block, st);
@@ -30,6 +31,7 @@ int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block, int bande
     if (cost_kind != kCostSqEuclid) return 0;
     if (banded) return R == 16 ? wf_occ_r16b(mode, D, block) : 0;
     switch (R) {
+        case 4: return wf_occ_r4(mode, D, block);
         case 8: return wf_occ_r8(mode, D, block);
         case 16: return wf_occ_r16(mode, D, block);
         case 32: return wf_occ_r32(mode, D, block);

@@ -51,6 +51,7 @@ int dtw_wavefront_max_blocks_per_sm(int mode, int D, int R, int block, int bande
 // The instance sets, one per translation unit (dtw_wavefront_<set>.cu):
 // rows per lane, band, local cost.
 #define WTS_WF_SETS(X) \
+    X(r4)     /* R = 4,  Sub-DTW only, squared l2 */ \
     X(r8)     /* R = 8,  no band, squared l2 */ \
     X(r16)    /* R = 16, no band, squared l2 */ \
     X(r16b)   /* R = 16, band,    squared l2 */ \

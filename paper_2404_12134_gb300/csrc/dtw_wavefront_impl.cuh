@@ -34,8 +34,8 @@
 // Predecessor codes (kModeDirs) are two bit-planes per lane and step: bit
 // p*R + k of the lane's W = R/16 words is plane p of row k, plane 0 = "not
 // diag", plane 1 = "not up" (meaningful only when plane 0 is set).  With R = 8
-// a step has 16 bits and two consecutive steps share one word (the even step
-// in the low half).
+// (R = 4) a step has 16 (8) bits and two (four) consecutive steps share one
+// word, the earliest step in the lowest bits.
 #pragma once
 
 #include "dtw_wavefront.cuh"
@@ -119,7 +119,8 @@ __device__ __forceinline__ float pick_row(const float (&c)[R], int k)
 template <int D, int R, int MODE, bool BANDED, int COST>
 struct Band {
     static constexpr int BR = 32 * R;
-    static constexpr int W = R / 16;        // code words per lane per step (0: half a word)
+    static constexpr int W = R / 16;        // code words per lane per step (0: part of a word)
+    static constexpr int SPW = R >= 16 ? 1 : 32 / (2 * R);     // steps per code word
     static constexpr int Q = R / 2;         // row pairs
 
     u64 bp[Q][D];                           // prototype rows as pairs
@@ -130,7 +131,7 @@ struct Band {
     int prev_upc;
     float topv;                             // lane l: r(band top - 1, s0 + l)
     int topc;
-    uint32_t half;                          // R = 8: codes of the last even step
+    uint32_t half;                          // R < 16: codes of the word's earlier steps
     // kModeSubDirs, matrix's last band: running minimum of r(M-1, j) over the
     // lane's columns (row kk of the lane), and its first column
     bool track;
@@ -252,11 +253,15 @@ struct Band {
             for (int q = 0; q < Q; ++q) cost_pair(yy, q);
         }
         if (CODES) {
-            if (W == 0) {
+            if (W == 0 && SPW == 2) {
                 if ((s & 1) == 0)
                     half = word[0];
                 else
                     __stcs(dout + (int64_t)(s >> 1) * 32 + lane, __byte_perm(half, word[0], 0x5410));
+            } else if (W == 0) {
+                const int sl = s & (SPW - 1);
+                half = sl == 0 ? word[0] : (half | (word[0] << (sl * 2 * R)));
+                if (sl == SPW - 1) __stcs(dout + (int64_t)(s / SPW) * 32 + lane, half);
             } else if (W == 1) {
                 __stcs(dout + (int64_t)s * 32 + lane, word[0]);
             } else {
@@ -418,7 +423,9 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
         }
     }
 
-    if (BandT::CODES && W == 0 && (s_end & 1)) __stcs(dout + (int64_t)(s_end >> 1) * 32 + lane, st.half);
+    constexpr int SPW = BandT::SPW;
+    if (BandT::CODES && W == 0 && (s_end % SPW) != 0)
+        __stcs(dout + (int64_t)((s_end - 1) / SPW) * 32 + lane, st.half);
 
     if (MODE == kModeSubDirs) {
         if (last && lane == (M - 1 - band * BR) / R) {
@@ -456,7 +463,10 @@ __device__ __forceinline__ void run_band(const DPParams& p, const PairDesc& pd, 
 // halves the prototype registers: four blocks (16 warps, <= 128 registers) up
 // to 6 channels.
 template <int D, int R>
-constexpr int min_blocks() { return R == 8 ? (D <= 6 ? 4 : (D <= 8 ? 3 : 2)) : ((R == 16 && D <= 4) ? 3 : 2); }
+constexpr int min_blocks()
+{
+    return R == 4 ? (D <= 8 ? 4 : 3) : R == 8 ? (D <= 6 ? 4 : (D <= 8 ? 3 : 2)) : ((R == 16 && D <= 4) ? 3 : 2);
+}
 
 template <int D, int R, int MODE, bool BANDED, int COST>
 __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(DPParams p)
@@ -523,32 +533,42 @@ int occ_one(int block)
 template <int D, int R, bool BANDED, int COST>
 cudaError_t launch_mode(int mode, const DPParams& p, int grid, int block, cudaStream_t st)
 {
-    switch (mode) {
-        case kModeCost: return launch_one<D, R, kModeCost, BANDED, COST>(p, grid, block, st);
-        case kModePlen: return launch_one<D, R, kModePlen, BANDED, COST>(p, grid, block, st);
-        case kModeDirs: return launch_one<D, R, kModeDirs, BANDED, COST>(p, grid, block, st);
-        case kModeSubDirs:
-            if constexpr (!BANDED && (R == 16 || R == 8))
-                return launch_one<D, R, kModeSubDirs, false, COST>(p, grid, block, st);
-            break;
-        default: break;
+    if constexpr (R == 4) {                  // Sub-DTW windows only (one pair: more, shorter bands)
+        if (mode == kModeSubDirs && !BANDED) return launch_one<D, 4, kModeSubDirs, false, COST>(p, grid, block, st);
+        return cudaErrorInvalidValue;
+    } else {
+        switch (mode) {
+            case kModeCost: return launch_one<D, R, kModeCost, BANDED, COST>(p, grid, block, st);
+            case kModePlen: return launch_one<D, R, kModePlen, BANDED, COST>(p, grid, block, st);
+            case kModeDirs: return launch_one<D, R, kModeDirs, BANDED, COST>(p, grid, block, st);
+            case kModeSubDirs:
+                if constexpr (!BANDED && (R == 16 || R == 8))
+                    return launch_one<D, R, kModeSubDirs, false, COST>(p, grid, block, st);
+                break;
+            default: break;
+        }
+        return cudaErrorInvalidValue;
     }
-    return cudaErrorInvalidValue;
 }
 
 template <int D, int R, bool BANDED, int COST>
 int occ_mode(int mode, int block)
 {
-    switch (mode) {
-        case kModeCost: return occ_one<D, R, kModeCost, BANDED, COST>(block);
-        case kModePlen: return occ_one<D, R, kModePlen, BANDED, COST>(block);
-        case kModeDirs: return occ_one<D, R, kModeDirs, BANDED, COST>(block);
-        case kModeSubDirs:
-            if constexpr (!BANDED && (R == 16 || R == 8)) return occ_one<D, R, kModeSubDirs, false, COST>(block);
-            break;
-        default: break;
+    if constexpr (R == 4) {
+        if (mode == kModeSubDirs && !BANDED) return occ_one<D, 4, kModeSubDirs, false, COST>(block);
+        return 0;
+    } else {
+        switch (mode) {
+            case kModeCost: return occ_one<D, R, kModeCost, BANDED, COST>(block);
+            case kModePlen: return occ_one<D, R, kModePlen, BANDED, COST>(block);
+            case kModeDirs: return occ_one<D, R, kModeDirs, BANDED, COST>(block);
+            case kModeSubDirs:
+                if constexpr (!BANDED && (R == 16 || R == 8)) return occ_one<D, R, kModeSubDirs, false, COST>(block);
+                break;
+            default: break;
+        }
+        return 0;
     }
-    return 0;
 }
 
 // One set of instances: every padded channel count D (1, 2, 3 only for R = 32).

@@ -35,7 +35,8 @@ __host__ __device__ inline int64_t pair_hbuf_slots(int64_t nb, int64_t N) { retu
 // (steps 2u and 2u+1 in its low and high halves).
 __host__ __device__ inline int64_t band_dir_words(int64_t N, int R)
 {
-    return R >= 16 ? (N + 31) * 32 * (R / 16) : ((N + 32) / 2) * 32;
+    // N + 31 steps; R < 16: 32 / (2R) steps per word
+    return R >= 16 ? (N + 31) * 32 * (R / 16) : ((N + 30 + 32 / (2 * R)) / (32 / (2 * R))) * 32;
 }
 __host__ __device__ inline int64_t pair_dir_words(int64_t nb, int64_t N, int R) { return nb * band_dir_words(N, R); }
 __host__ __device__ inline int64_t pair_rstore_floats(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * R; }

@@ -128,6 +128,12 @@ def test_subdtw_workspace_and_validation(lib):
     assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == 0
     o.rows_per_thread = 32
     assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == _abi.WTS_EINVAL
+    # four rows per lane: Sub-DTW windows only
+    o.rows_per_thread = 4
+    assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == 0
+    for op in (_abi.OP_ANOMALY_SCORE, _abi.OP_DTW_ALIGN, _abi.OP_DBA_ITERATE, _abi.OP_PAIRWISE):
+        assert _size(lib, op, 600, b, o)[0] == _abi.WTS_EINVAL
+        assert b"Sub-DTW only" in lib.wts_last_error()
     o.rows_per_thread = 0
     o.dir_mode = 1
     assert _size(lib, _abi.OP_SUBDTW, 600, b, o)[0] == _abi.WTS_EINVAL

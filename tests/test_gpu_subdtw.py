@@ -37,7 +37,7 @@ def _check(wts, X, cyc, rows=0):
         assert abs(cost[k] - r64["cost"]) <= 1e-5 * max(1.0, r64["cost"]), k
 
 
-@pytest.mark.parametrize("rows", [16, 8])
+@pytest.mark.parametrize("rows", [16, 8, 4])
 @pytest.mark.parametrize("M,lengths,d", [
     (1, [1, 7, 300], 1),
     (37, [1, 2, 40, 95], 3),
@@ -70,7 +70,7 @@ def test_subdtw_embedded_copy(wts):
     assert float(cost[0]) == 0.0 and (int(a[0]), int(b[0]), int(plen[0])) == (333, 1032, 700)
 
 
-@pytest.mark.parametrize("d,seed,rows", [(3, 7, 16), (9, 8, 16), (9, 8, 8)])
+@pytest.mark.parametrize("d,seed,rows", [(3, 7, 16), (9, 8, 16), (9, 8, 8), (9, 8, 4), (1, 9, 4)])
 def test_segment_matches_oracle(wts, d, seed, rows):
     X, Y, bounds = synth.segmentation_stream(6, 550, 650, d, 600, seed)
     alpha = int(0.15 * len(X))
