@@ -397,11 +397,15 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
         bt.band_lo = 0;
         bt.band_hi = (int)cdiv(L.M, L.BR);
         // segmented walk: nseg rounds (a round only re-walks the segments
-        // whose start changed), then |pi| from the ranges
-        bt.nseg = L.nseg;
+        // whose start changed), then |pi| from the ranges; a single segment
+        // is one plain walk per pair
+        bt.nseg = L.nseg > 1 ? L.nseg : 0;
         bt.seg_rows = kBtSegRows;
         bt.seg = reinterpret_cast<int32_t*>(ws + L.off_seg);
-        {
+        if (bt.nseg == 0) {
+            Prof pr("backtrack", st);
+            e = launch_backtrack(bt, st);
+        } else {
             Prof pr("backtrack", st);
             pr.kernels = L.nseg + 1;
             for (int r = 0; r < L.nseg; ++r) {

@@ -203,13 +203,16 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             int run = votes == FULL ? 32 : __ffs(~votes) - 1;
             // a re-walk: does the move of c_u enter a row at a cell of the
             // previous walk (read before this run's writes)?
-            bool mg = false;
-            if (mergeable && di && lane < run && iu - 1 >= i_lo) {
-                const int je = ju - dj;
-                mg = jlo[iu - 1] <= je && je <= jhi[iu - 1];
+            uint32_t mv = 0u;
+            if (mergeable) {                         // warp-uniform
+                bool mg = false;
+                if (di && lane < run && iu - 1 >= i_lo) {
+                    const int je = ju - dj;
+                    mg = jlo[iu - 1] <= je && je <= jhi[iu - 1];
+                }
+                mv = __ballot_sync(FULL, mg);
+                if (mv) run = __ffs(mv);             // up to and including the first such move
             }
-            const uint32_t mv = __ballot_sync(FULL, mg);
-            if (mv) run = __ffs(mv);                 // up to and including the first such move
             if (di && lane < run) {
                 jlo[iu] = ju;
                 jhi[iu - 1] = ju - dj;
