@@ -17,7 +17,7 @@
  *    sample must be finite; results for non-finite samples are unspecified
  *    (no fault, no hang).
  *  - Local cost delta(b_i, y_j) = sum_c (b_ic - y_jc)^2 (the Euclidean norm of
- *    Sec. 3.2, squared).
+ *    Sec. 3.2, squared), or the norm itself with wts_options.cost_kind = 1.
  *  - Equal predecessors resolve diag (i-1,j-1) first, then up (i-1,j), then
  *    left (i,j-1): the path returned is, among all optimal complete alignment
  *    paths, the one whose steps read backwards from (M-1,N-1) are
