@@ -122,10 +122,10 @@ def in_band(i: int, j: int, M: int, N: int, band: float) -> bool:
     return abs(i * N - j * M) <= bound
 
 
-def dtw_band(B, Y, band: float):
+def dtw_band(B, Y, band: float, cost_kind: int = 0):
     """Eq. 1 restricted to the complete paths that stay inside the band:
     (min cost, the tie-rule path)."""
-    D = cost_matrix(B, Y)
+    D = cost_matrix(B, Y, cost_kind)
     M, N = D.shape
     ps = [p for p in paths(M, N) if all(in_band(i, j, M, N, band) for i, j in p)]
     costs = [sum(D[i, j] for i, j in p) for p in ps]
@@ -134,9 +134,9 @@ def dtw_band(B, Y, band: float):
     return best, chosen
 
 
-def softdtw_band(B, Y, gamma: float, band: float):
+def softdtw_band(B, Y, gamma: float, band: float, cost_kind: int = 0):
     """Eq. 4 over the complete paths inside the band: (value, E)."""
-    D = cost_matrix(B, Y)
+    D = cost_matrix(B, Y, cost_kind)
     M, N = D.shape
     ps = [p for p in paths(M, N) if all(in_band(i, j, M, N, band) for i, j in p)]
     costs = np.array([sum(D[i, j] for i, j in p) for p in ps])

@@ -707,3 +707,23 @@ def test_pad_last_and_select_channel():
     B = np.concatenate([rng.normal(size=(6, 3)).astype(np.float32), cyc[1][-1:]])
     assert oracle.dtw(B, P[1][:9], "f64")["cost"] == oracle.dtw(B, cyc[1], "f64")["cost"]
     assert oracle.dtw(B, P12[1], "f64")["cost"] == oracle.dtw(B, cyc[1], "f64")["cost"]
+
+
+def test_l2_with_band_matches_brute_force():
+    """Both options at once: the l2-norm cost inside the Sakoe-Chiba band,
+    DTW (d = 1 integers, exact) and Soft-DTW (value and E) against the
+    enumeration of the in-band paths."""
+    rng = np.random.default_rng(69)
+    for M in range(2, 6):
+        for N in range(2, 6):
+            for w in _bands(M, N)[:3]:
+                B, Y = synth.integer_pair(rng, M, N, 1, -3, 3)
+                best, chosen = brute.dtw_band(B, Y, w, cost_kind=1)
+                r = oracle.dtw(B, Y, "f64", band=w, cost_kind=1)
+                assert float(r["cost"]) == best, (M, N, w)
+                assert list(zip(r["path_i"].tolist(), r["path_j"].tolist())) == chosen, (M, N, w)
+                Br, Yr = _real_pair(rng, M, N, 2)
+                v, E = brute.softdtw_band(Br, Yr, 0.5, w, cost_kind=1)
+                s = oracle.softdtw(Br, Yr, 0.5, "f64", want_E=True, band=w, cost_kind=1)
+                assert abs(s["value"] - v) <= 1e-10 * max(1.0, abs(v)), (M, N, w)
+                assert np.allclose(s["E"][1:M + 1, 1:N + 1], E, rtol=1e-9, atol=1e-12), (M, N, w)
