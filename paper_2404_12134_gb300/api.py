@@ -128,12 +128,13 @@ def read_status(buf: torch.Tensor) -> int:
 
 
 def profile_enable(enable: bool = True):
-    """Record CUDA events around every library kernel launch (measurement)."""
+    """Record CUDA events around every stage of the library's calls (measurement)."""
     check(_abi.load().wts_profile_enable(1 if enable else 0))
 
 
 def profile_read(kernel: str = ""):
-    """(total ms, launches) of the recorded launches of one kernel ("" = all)."""
+    """(total ms, kernel launches) of the recorded runs of one stage ("" = all);
+    a stage may launch several kernels (the segmented backtrack's rounds)."""
     ms = ctypes.c_double(0)
     n = ctypes.c_int32(0)
     check(_abi.load().wts_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
