@@ -36,15 +36,15 @@ WORKLOAD = ("batched DBA: 200 cycles x 6 ch FP32, pre-gap N ~ U(20k,30k), 2% gap
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per cell of the code-writing wavefront, from one
-# ncu capture of the same kernel build on 36 cycles of this workload
-# (profiles/wavefront_dirs_36x25k_d6.md): (0.1582 + 5.6421)e9 bytes /
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
+# kernel build on 36 cycles of this workload: (0.1582 + 5.6421)e9 bytes /
 # 2.2029e10 cells.  Traffic grows in proportion to the cells (codes +
 # hand-off rows).
 WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1582 + 5.6421) * 1e9 / 2.2029e10
 # DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
-# ncu capture of both kernels on 8 cycles of the soft-DTW workload
-# (profiles/softdtw_fwd_bwd_8x10k_d1.md): (0.0120 + 3.2474 + 3.3395 + 0.0522)e9
-# bytes / 8.0226e8 cells (stored R plus hand-off rows, in proportion to cells).
+# ncu capture of both kernels on 8 cycles of the soft-DTW workload:
+# (0.0120 + 3.2474 + 3.3395 + 0.0522)e9 bytes / 8.0226e8 cells (stored R plus
+# hand-off rows, in proportion to cells).
 SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0120 + 3.2474 + 3.3395 + 0.0522) * 1e9 / 8.0226e8
 
 
@@ -398,10 +398,10 @@ def bary_leg(api, torch, dev, barrier, gammas=(1.0, 0.1, 0.01), steps: int = 50,
     res["dba"] = dict(quality(B), iterations=dba_iters, seconds=time.perf_counter() - t0)
     for gamma in gammas:
         t0 = time.perf_counter()
-        Bs, hist, w = api.softdtw_barycenter(gb, M, gamma, steps=steps, lr=lr, init=B0)
+        Bs, hist = api.softdtw_barycenter(gb, M, gamma, steps=steps, lr=lr, init=B0)
         barrier()
         el = time.perf_counter() - t0
-        obj = (hist.double() * w.double()).sum(1).cpu().numpy()
+        obj = (hist.double().cpu().numpy() * (1.0 / sb.lengths).astype(np.float32)).sum(1)
         res[f"softdtw_barycenter_gamma_{gamma:g}"] = dict(quality(Bs), adam_steps=steps, lr=lr, seconds=el,
                                                           objective_first=float(obj[0]),
                                                           objective_last=float(obj[-1]))

@@ -14,8 +14,10 @@
  *  - Samples are d-channel FP32 vectors, row-major: B is [M][d]; a batch packs
  *    T cycles back to back, cycle k = data[offsets[k]*d .. offsets[k+1]*d).
  *    Time steps with missing values must already be removed (Sec. 3.1): every
- *    sample must be finite; results for non-finite samples are unspecified
- *    (no fault, no hang).
+ *    sample must be finite.  Every call that runs a DP first scans B and the
+ *    batch on the device; a NaN or +-inf sample makes each kernel of the call
+ *    leave before doing any work (outputs are then unspecified) and leaves
+ *    WTS_EINVAL in the workspace's device status word (wts_read_status).
  *  - Local cost delta(b_i, y_j) = sum_c (b_ic - y_jc)^2 (the Euclidean norm of
  *    Sec. 3.2, squared), or the norm itself with wts_options.cost_kind = 1.
  *  - Equal predecessors resolve diag (i-1,j-1) first, then up (i-1,j), then
@@ -30,9 +32,10 @@
  *    stream).  Outputs are valid once the stream has reached the call.
  *    Inputs are validated on the host before any launch.
  *  - Return value: WTS_OK or an error code; wts_last_error() gives the text
- *    (thread-local).  A wait inside a kernel that gives up (it never does in
- *    normal operation) leaves WTS_ETIMEOUT in the workspace's device status
- *    word, read by wts_read_status().
+ *    (thread-local).  What a call can only find on the device is reported in
+ *    the workspace's device status word, read by wts_read_status(): a
+ *    non-finite sample (WTS_EINVAL), or a wait inside a kernel that gave up
+ *    (WTS_ETIMEOUT; it never does in normal operation).
  */
 #ifndef WETSAND_H
 #define WETSAND_H
@@ -62,6 +65,7 @@ enum {
     WTS_OP_COMPACT_NAN = 6,    /* wts_compact_nan (M ignored) */
     WTS_OP_SUBDTW = 7,         /* subdtw_align (M = length of X) */
     WTS_OP_SOFTDTW_LBFGS = 8,  /* wts_softdtw_barycenter_lbfgs */
+    WTS_OP_SOFTDTW_ADAM = 9,   /* wts_softdtw_barycenter_adam */
 };
 
 /* A packed batch of T cycles (Sec. 3.1: d-channel series of uneven lengths). */
@@ -121,8 +125,10 @@ const char* wts_last_error(void);
  * batch Y (M is ignored for WTS_OP_PAIRWISE).  Host-only; no CUDA call. */
 int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes);
 
-/* Synchronise `stream` and read the device status word of `workspace`
- * (0 = ok, WTS_ETIMEOUT = an in-kernel wait gave up) into *status (host). */
+/* Synchronise `stream` and read the device status word of `workspace` into
+ * *status (host): WTS_OK, WTS_EINVAL (a sample of B or of the batch is NaN or
+ * +-inf; the call's kernels did no work) or WTS_ETIMEOUT (an in-kernel wait
+ * gave up).  The word is reset by the next call on the workspace. */
 int wts_read_status(const void* workspace, void* stream, int32_t* status);
 
 /* Kernel timing for measurement: while enabled, every kernel the library
@@ -210,7 +216,8 @@ int subdtw_align(const float* X, int64_t M, const wts_batch* Y, const wts_option
  * ([M][d], device).  Window [ws, we) with ws = 0, we = ws + 2M (cut at N);
  * Sub-DTW of X against the window gives [a*, b*]; the piece
  * [ws + a*, ws + b*] is recorded and the next window starts at
- * ws + b* - alpha (the paper takes alpha = 0.15 M), while ws < N.  Two
+ * ws + b* - alpha, while ws < N; alpha < 0 selects the paper's
+ * alpha = 0.15 M (rounded down).  Two
  * readings where the paper does not say: the window that reaches the end of
  * Y is the last one, and when b* - alpha would not move the window forward
  * the next one starts at ws + b* + 1.
@@ -350,8 +357,9 @@ int softdtw_forward(const float* B, int64_t M, const wts_batch* Y, float gamma, 
  * is the gradient of the barycenter objective Eq. 7.
  * The workspace must still hold the R written by softdtw_forward for the same
  * B, Y, gamma and options (the call may be repeated with other g).
- *   grad_value [T] in (g_k), grad_B [M][d] out; the sum over k is in FP64, k
- *   ascending.
+ *   grad_value [T] in (g_k), or NULL for Eq. 7's weights with lambda_k = 1:
+ *   g_k = 1 / N_k (rounded to FP32, computed on the device);
+ *   grad_B [M][d] out; the sum over k is in FP64, k ascending.
  */
 int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma, const float* grad_value,
                      const wts_options* opt, void* workspace, size_t workspace_bytes, void* stream,
@@ -364,6 +372,22 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
  */
 int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
                   float eps, int32_t t, void* stream);
+
+/*
+ * wts_softdtw_barycenter_adam - the Soft-DTW barycenter of Eq. 7,
+ * argmin_B sum_k g_k Soft-DTW^gamma(B, Y_k) (g_k = lambda_k / m_k; weights
+ * NULL = 1 / N_k), by `steps` Adam steps (Kingma and Ba; the paper's optimiser
+ * is L-BFGS, see wts_softdtw_barycenter_lbfgs): step t = 1..steps runs
+ * softdtw_forward, softdtw_backward with the weights, and wts_adam_step(t)
+ * on B, all queued on `stream` (no synchronisation; the moments start at 0).
+ *   B [M][d]              in: the start (device), out: B after the last step
+ *   values [steps][T]     out (may be NULL): Soft-DTW^gamma(B_t, Y_k) at the
+ *                         start of each step
+ * Workspace: wts_workspace_size(WTS_OP_SOFTDTW_ADAM, M, Y, opt, ...).
+ */
+int wts_softdtw_barycenter_adam(float* B, int64_t M, const wts_batch* Y, float gamma, const float* weights,
+                                int32_t steps, float lr, float beta1, float beta2, float eps, const wts_options* opt,
+                                void* workspace, size_t workspace_bytes, void* stream, float* values);
 
 /*
  * wts_autotune - pick the launch options (rows per lane, warps per block) of
@@ -457,16 +481,30 @@ int wts_euclid_mean(const wts_batch* Y, int64_t M, float* out, void* stream);
  *  - A batch whose scratch need (the WTS_OP_ANOMALY_SCORE workspace size)
  *    exceeds 32 MiB is rejected with WTS_ENOMEM before anything is launched;
  *    for M = 25,000 and d > 2 that is about two 30,000-sample cycles per call.
- *  - The first call on each device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *  - Each call looks up the array's device address with the current device
+ *    current (outside stream capture; a call being captured uses the address
+ *    found by an earlier call on that device).  Make the first call on each
+ *    device before any stream capture; after a cudaDeviceReset, make one call
+ *    outside capture before capturing again.
  *  - All calls share the one array and it keeps the last call's contents; each
  *    call clears what must start at zero.  Calls whose work overlaps on the
  *    GPU (other streams, other host threads, without ordering between them)
  *    race on the array: serialise them.
- *  - The device status word of this scratch is not readable by the caller.
+ *  - The array's device status word (a non-finite sample, or a wait that gave
+ *    up) is read by wts_noalloc_read_status; it holds the last call's status.
  */
 int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch* Y, const wts_options* opt,
                           void* stream, float* score, float* cost, int32_t* plen);
+
+/*
+ * wts_noalloc_read_status - synchronise `stream` and read the device status
+ * word of the fixed scratch of anomaly_score_noalloc on the current device
+ * into *status (host): WTS_OK, WTS_EINVAL (a non-finite sample) or
+ * WTS_ETIMEOUT, as wts_read_status reports them for a workspace.  Call it
+ * after the anomaly_score_noalloc call it should report on, on the same
+ * stream, before the next one.  No allocation.
+ */
+int wts_noalloc_read_status(void* stream, int32_t* status);
 
 #ifdef __cplusplus
 }

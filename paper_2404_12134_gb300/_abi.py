@@ -16,6 +16,7 @@ WTS_OK, WTS_EINVAL, WTS_ENOMEM, WTS_ECUDA, WTS_ETIMEOUT = 0, 1, 2, 3, 4
 OP_ANOMALY_SCORE, OP_DTW_ALIGN, OP_DBA_ITERATE, OP_SOFTDTW, OP_PAIRWISE, OP_COMPACT_NAN = 1, 2, 3, 4, 5, 6
 OP_SUBDTW = 7
 OP_SOFTDTW_LBFGS = 8
+OP_SOFTDTW_ADAM = 9
 COST_SQEUCLID, COST_L2 = 0, 1
 
 # every symbol declared in include/wetsand.h
@@ -27,6 +28,7 @@ EXPORTS = (
     "softdtw_forward", "softdtw_backward", "wts_adam_step", "wts_autotune", "wts_compact_nan",
     "subdtw_align", "wts_segment_workspace_size", "wts_segment", "wts_thresholds", "wts_f2",
     "wts_lbfgs_minimize", "wts_softdtw_barycenter_lbfgs", "wts_pad_last", "wts_select_channel",
+    "wts_softdtw_barycenter_adam", "wts_noalloc_read_status",
 )
 
 
@@ -114,6 +116,9 @@ _SIGS = {
     "wts_resample": ([VP, I64, I32, VP, I64, VP], ctypes.c_int),
     "wts_euclid_mean": ([PB, I64, VP, VP], ctypes.c_int),
     "anomaly_score_noalloc": ([VP, I64, PB, PO, VP, VP, VP, VP], ctypes.c_int),
+    "wts_noalloc_read_status": ([VP, ctypes.POINTER(I32)], ctypes.c_int),
+    "wts_softdtw_barycenter_adam": ([VP, I64, PB, ctypes.c_float, VP, I32, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, PO, VP, SZ, VP, VP], ctypes.c_int),
     "wts_compact_nan": ([PB, VP, SZ, VP, VP, VP], ctypes.c_int),
     "wts_pad_last": ([PB, I64, VP, VP], ctypes.c_int),
     "wts_select_channel": ([PB, I32, VP, VP], ctypes.c_int),

@@ -177,7 +177,8 @@ def anomaly_score_noalloc(B: torch.Tensor, batch: Batch, opts=None):
     """anomaly_score for callers that cannot allocate device memory: the
     library's fixed 32 MiB scratch replaces the workspace (small batches only;
     calls must not overlap on the GPU).  Outputs are allocated here by torch
-    only for convenience; a C caller passes its own."""
+    only for convenience; a C caller passes its own.  The scratch's device
+    status is read by noalloc_status()."""
     B = _check_B(B, batch.d)
     M = B.shape[0]
     dev = B.device
@@ -187,6 +188,14 @@ def anomaly_score_noalloc(B: torch.Tensor, batch: Batch, opts=None):
     check(_abi.load().anomaly_score_noalloc(B.data_ptr(), M, ctypes.byref(batch.c()), _opt(opts), _stream(),
                                             score.data_ptr(), cost.data_ptr(), plen.data_ptr()))
     return score, cost, plen
+
+
+def noalloc_status() -> int:
+    """Device status of the fixed scratch after the last anomaly_score_noalloc
+    on the current stream (0, WTS_EINVAL or WTS_ETIMEOUT; synchronises)."""
+    s = ctypes.c_int32(0)
+    check(_abi.load().wts_noalloc_read_status(_stream(), ctypes.byref(s)))
+    return s.value
 
 
 def dtw_align(B: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None = None,
@@ -235,7 +244,7 @@ def subdtw_align(X: torch.Tensor, batch: Batch, opts=None, ws: Workspace | None 
 def segment(X: torch.Tensor, Y: torch.Tensor, alpha: int | None = None, opts=None, max_segments: int = 4096,
             ws: Workspace | None = None):
     """Cut the long series Y [N, d] (device) into cycles matching X [M, d]
-    (Sec. 3.2; alpha defaults to 0.15 M).  Returns a list of
+    (Sec. 3.2; alpha None: the library's default 0.15 M).  Returns a list of
     (start, end, cost), inclusive bounds."""
     if Y.dim() == 1:
         Y = Y[:, None]
@@ -245,7 +254,7 @@ def segment(X: torch.Tensor, Y: torch.Tensor, alpha: int | None = None, opts=Non
     M, d = X.shape
     N = Y.shape[0]
     if alpha is None:
-        alpha = int(0.15 * M)
+        alpha = -1
     lib = _abi.load()
     nbytes = ctypes.c_size_t(0)
     check(lib.wts_segment_workspace_size(M, d, _opt(opts), ctypes.byref(nbytes)))
@@ -468,19 +477,22 @@ def softdtw_forward(B: torch.Tensor, batch: Batch, gamma: float, opts=None, ws: 
     return values
 
 
-def softdtw_backward(B: torch.Tensor, batch: Batch, gamma: float, grad_value: torch.Tensor, opts=None,
-                     ws: Workspace | None = None, grad_B: torch.Tensor | None = None):
-    """d/dB of sum_k grad_value[k] * Soft-DTW^gamma(B, Y_k) (Eq. 6): [M, d].
-    ``ws`` must be the workspace of the matching softdtw_forward."""
+def softdtw_backward(B: torch.Tensor, batch: Batch, gamma: float, grad_value: torch.Tensor | None = None,
+                     opts=None, ws: Workspace | None = None, grad_B: torch.Tensor | None = None):
+    """d/dB of sum_k grad_value[k] * Soft-DTW^gamma(B, Y_k) (Eq. 6): [M, d];
+    grad_value None: the library's Eq. 7 weights 1 / N_k.  ``ws`` must be the
+    workspace of the matching softdtw_forward."""
     B = _check_B(B, batch.d)
     M = B.shape[0]
     nb = workspace_size(_abi.OP_SOFTDTW, M, batch, opts)
     buf = _ws(ws, nb)
-    gv = grad_value.to(device=B.device, dtype=torch.float32).contiguous()
-    if gv.numel() != batch.T:
-        raise ValueError("grad_value must have T entries")
+    gv = None
+    if grad_value is not None:
+        gv = grad_value.to(device=B.device, dtype=torch.float32).contiguous()
+        if gv.numel() != batch.T:
+            raise ValueError("grad_value must have T entries")
     grad_B = torch.empty_like(B) if grad_B is None else grad_B
-    check(_abi.load().softdtw_backward(B.data_ptr(), M, ctypes.byref(batch.c()), float(gamma), gv.data_ptr(),
+    check(_abi.load().softdtw_backward(B.data_ptr(), M, ctypes.byref(batch.c()), float(gamma), _p(gv),
                                        _opt(opts), buf.data_ptr(), buf.numel(), _stream(), grad_B.data_ptr()))
     return grad_B
 
@@ -517,22 +529,23 @@ def softdtw(B: torch.Tensor, batch: Batch, gamma: float, opts=None) -> torch.Ten
 
 
 def softdtw_barycenter(batch: Batch, M: int, gamma: float, steps: int = 50, lr: float = 1e-2,
-                       init: torch.Tensor | None = None, weights: torch.Tensor | None = None, opts=None):
-    """Soft-DTW barycenter (Eq. 7) by Adam: B minimises sum_k w_k Soft-DTW^gamma(B, Y_k),
-    w_k = lambda_k / m_k with lambda_k = 1 by default.  Starts from the Euclidean
-    mean of the cycles resampled to M (Table I's default initialisation).
-    Returns (B, values per step [steps, T] on the device, weights)."""
+                       init: torch.Tensor | None = None, weights: torch.Tensor | None = None, opts=None,
+                       beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, ws: Workspace | None = None):
+    """Soft-DTW barycenter (Eq. 7) by Adam (the library's loop on the current
+    stream): B minimises sum_k w_k Soft-DTW^gamma(B, Y_k), w_k = lambda_k / m_k
+    (weights None: the library's 1 / N_k).  Starts from the Euclidean mean of
+    the cycles resampled to M (Table I's default initialisation) unless
+    ``init`` is given.  Returns (B, values per step [steps, T] on the device)."""
     dev = batch.data.device
     B = euclid_mean(batch, M) if init is None else init.detach().clone().contiguous()
-    if weights is None:
-        weights = torch.from_numpy((1.0 / batch.lengths).astype(np.float32)).to(dev)
-    m = torch.zeros_like(B)
-    v = torch.zeros_like(B)
-    ws = Workspace(dev)
-    grad = torch.empty_like(B)
+    B = _check_B(B, batch.d)
+    if weights is not None:
+        weights = weights.to(device=dev, dtype=torch.float32).contiguous()
+    nb = workspace_size(_abi.OP_SOFTDTW_ADAM, M, batch, opts)
+    buf = _ws(ws if ws is not None else Workspace(dev), nb)
     hist = torch.empty((steps, batch.T), dtype=torch.float32, device=dev)
-    for t in range(1, steps + 1):
-        hist[t - 1] = softdtw_forward(B, batch, gamma, opts, ws)
-        softdtw_backward(B, batch, gamma, weights, opts, ws, grad_B=grad)
-        adam_step(B, grad, m, v, t, lr=lr)
-    return B, hist, weights
+    check(_abi.load().wts_softdtw_barycenter_adam(B.data_ptr(), M, ctypes.byref(batch.c()), float(gamma), _p(weights),
+                                                  int(steps), float(lr), float(beta1), float(beta2), float(eps),
+                                                  _opt(opts), buf.data_ptr(), buf.numel(), _stream(),
+                                                  hist.data_ptr() if steps > 0 else None))
+    return B, hist

@@ -289,6 +289,18 @@ int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const
         e = cudaMemsetAsync(ws + L.off_hbuf, 0xFF, L.hbuf_bytes, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(hand-off rows)");
     }
+    // every sample must be finite (Sec. 3.1 removes missing values first): a
+    // non-finite one sets the status and abort words, and every kernel of the
+    // call then leaves at once
+    DevInfo di;
+    int rc = device_info(&di);
+    if (rc) return rc;
+    {
+        Prof pr("setup", st);
+        e = launch_check_finite(B, B ? L.M * L.d : 0, Y->data, Y->offsets_host[Y->T] * Y->d,
+                                reinterpret_cast<WsHeader*>(ws + L.off_hdr), di.sms, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "input check launch");
     SetupParams sp{};
     sp.op = L.op;
     sp.T = L.T;
@@ -492,6 +504,12 @@ int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, 
     return WTS_OK;
 }
 
+// The caller-visible code of a workspace's device status word.
+int status_of(const WsHeader& h)
+{
+    return h.status == kDevTimeout ? WTS_ETIMEOUT : (h.status == kDevBadInput ? WTS_EINVAL : WTS_OK);
+}
+
 int check_gamma(float gamma)
 {
     if (!(gamma > 0.f) || !(gamma < 1e30f)) return fail(WTS_EINVAL, "gamma must be finite and > 0 (gamma = 0 is DTW)");
@@ -559,24 +577,32 @@ size_t lbfgs_extra_bytes(int64_t M, const wts_batch* Y)
     return 2 * align256((size_t)Y->T * sizeof(float)) + align256((size_t)M * Y->d * sizeof(float));
 }
 
+// After the soft-DTW workspace: Adam's moments m, v and the gradient ([M][d]
+// each, FP32), then the values of one step [T] when the caller keeps none.
+size_t adam_extra_bytes(int64_t M, const wts_batch* Y)
+{
+    return 3 * align256((size_t)M * Y->d * sizeof(float)) + align256((size_t)Y->T * sizeof(float));
+}
+
 }  // namespace
 
 int wts_workspace_size(int op, int64_t M, const wts_batch* Y, const wts_options* opt, size_t* bytes)
 {
     if (!bytes) return fail(WTS_EINVAL, "bytes is NULL");
-    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise, 0, kOpSubdtw, kOpSoft};
+    static const int map[] = {0, kOpScore, kOpAlign, kOpDba, kOpSoft, kOpPairwise, 0, kOpSubdtw, kOpSoft, kOpSoft};
     if (op == WTS_OP_COMPACT_NAN) {
         int rc = check_batch(Y, false);
         if (rc) return rc;
         *bytes = align256(compact_workspace_bytes(Y->offsets_host[Y->T]));
         return ok();
     }
-    if (op < 1 || op > 8 || op == WTS_OP_COMPACT_NAN) return fail(WTS_EINVAL, "unknown op %d", op);
+    if (op < 1 || op > 9 || op == WTS_OP_COMPACT_NAN) return fail(WTS_EINVAL, "unknown op %d", op);
     Layout L;
     int rc = compute_layout(map[op], M, Y, opt, &L);
     if (rc) return rc;
     *bytes = L.total;
     if (op == WTS_OP_SOFTDTW_LBFGS) *bytes += lbfgs_extra_bytes(M, Y);
+    if (op == WTS_OP_SOFTDTW_ADAM) *bytes += adam_extra_bytes(M, Y);
     return ok();
 }
 
@@ -588,7 +614,7 @@ int wts_read_status(const void* workspace, void* stream, int32_t* status)
     cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "reading workspace status");
-    *status = h.status == kDevTimeout ? WTS_ETIMEOUT : WTS_OK;
+    *status = status_of(h);
     return ok();
 }
 
@@ -770,8 +796,9 @@ int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_
     if (!X || !Ydata || !n_segments || (max_segments > 0 && (!seg_start || !seg_end)))
         return fail(WTS_EINVAL, "X, Ydata, n_segments (and seg_start/seg_end) must not be NULL");
     if (N < 1) return fail(WTS_EINVAL, "N=%lld (need >= 1)", (long long)N);
-    if (alpha < 0) return fail(WTS_EINVAL, "alpha must be >= 0");
     if (max_segments < 0) return fail(WTS_EINVAL, "max_segments must be >= 0");
+    if (M < 1) return fail(WTS_EINVAL, "M=%lld (need >= 1)", (long long)M);
+    if (alpha < 0) alpha = (int64_t)(0.15 * (double)M);   // Sec. 3.2: alpha = 0.15 M
     SegLayout S;
     const wts_options o = segment_options(opt);
     opt = &o;
@@ -847,6 +874,8 @@ int wts_segment(const float* X, int64_t M, const float* Ydata, int64_t N, int32_
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "window result read-back");
         if (h.status == kDevTimeout) return fail(WTS_ETIMEOUT, "a wait in the window at %lld gave up", (long long)pos);
+        if (h.status == kDevBadInput)
+            return fail(WTS_EINVAL, "a sample of X or of the window at %lld is not finite", (long long)pos);
         if (bstar < 0 || bstar >= n) return fail(WTS_ECUDA, "window at %lld gave an invalid end %d", (long long)pos, bstar);
         // backtrack of this window on the second stream, after its wavefront
         if ((e = cudaStreamWaitEvent(ss.bt, ss.dp_done, 0)) != cudaSuccess) return cuda_fail(e, "backtrack order");
@@ -959,7 +988,7 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     if (rc) return rc;
     if ((rc = check_batch(Y, true))) return rc;
     if ((rc = check_gamma(gamma))) return rc;
-    if (!B || !grad_value || !grad_B) return fail(WTS_EINVAL, "B, grad_value and grad_B must not be NULL");
+    if (!B || !grad_B) return fail(WTS_EINVAL, "B and grad_B must not be NULL");
     if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
@@ -1010,7 +1039,7 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     }
     {
         Prof pr("softdtw_grad", st);
-        e = launch_softdtw_grad_reduce(p.gpart, grad_value, L.T, M, L.d, grad_B, st);
+        e = launch_softdtw_grad_reduce(p.gpart, grad_value, Y->offsets, L.T, M, L.d, grad_B, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
     return ok();
@@ -1025,6 +1054,43 @@ int wts_adam_step(float* x, const float* grad, float* m, float* v, int64_t n, fl
         return fail(WTS_EINVAL, "need 0 <= beta < 1 and eps > 0");
     cudaError_t e = launch_adam(x, grad, m, v, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+    return ok();
+}
+
+int wts_softdtw_barycenter_adam(float* B, int64_t M, const wts_batch* Y, float gamma, const float* weights,
+                                int32_t steps, float lr, float beta1, float beta2, float eps, const wts_options* opt,
+                                void* workspace, size_t workspace_bytes, void* stream, float* values)
+{
+    Layout L;
+    int rc = compute_layout(kOpSoft, M, Y, opt, &L);
+    if (rc) return rc;
+    if ((rc = check_batch(Y, true))) return rc;
+    if ((rc = check_gamma(gamma))) return rc;
+    if (!B) return fail(WTS_EINVAL, "B must not be NULL");
+    if (steps < 0) return fail(WTS_EINVAL, "steps must be >= 0");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+        return fail(WTS_EINVAL, "need 0 <= beta < 1 and eps > 0");
+    const size_t need = L.total + adam_extra_bytes(M, Y);
+    if (!workspace || ((uintptr_t)workspace & 255) != 0) return fail(WTS_EINVAL, "workspace must be 256-byte aligned");
+    if (workspace_bytes < need) return fail(WTS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    char* extra = ws + L.total;
+    const size_t vec = align256((size_t)M * Y->d * sizeof(float));
+    float* m = reinterpret_cast<float*>(extra);
+    float* v = reinterpret_cast<float*>(extra + vec);
+    float* grad = reinterpret_cast<float*>(extra + 2 * vec);
+    float* vscratch = reinterpret_cast<float*>(extra + 3 * vec);
+    // the moments start at zero (step t = 1 of Adam)
+    cudaError_t e = cudaMemsetAsync(m, 0, 2 * vec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(moments)");
+    const int64_t n = M * Y->d;
+    for (int32_t t = 1; t <= steps; ++t) {
+        float* vals = values ? values + (int64_t)(t - 1) * Y->T : vscratch;
+        if ((rc = softdtw_forward(B, M, Y, gamma, opt, ws, L.total, stream, vals))) return rc;
+        if ((rc = softdtw_backward(B, M, Y, gamma, weights, opt, ws, L.total, stream, grad))) return rc;
+        if ((rc = wts_adam_step(B, grad, m, v, n, lr, beta1, beta2, eps, t, stream))) return rc;
+    }
     return ok();
 }
 
@@ -1216,19 +1282,28 @@ void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-int noalloc_scratch(void** out)
+// with that device current: on the first call on each device, and again on
+// every call made outside stream capture (a cheap host call), so that a
+// context torn down and re-created in between (cudaDeviceReset) is followed.
+// During capture the address cached by an earlier call is used; a capture with
+// no earlier call on that device is refused.
+int noalloc_scratch(cudaStream_t st, void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(WTS_EINVAL, "device ordinal %d not supported", dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, wts_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
         g_noalloc_addr[dev] = p;
+    } else if (!g_noalloc_addr[dev]) {
+        return fail(WTS_EINVAL, "the first no-allocation call on device %d must come before any stream capture", dev);
     }
     *out = g_noalloc_addr[dev];
     return WTS_OK;
@@ -1251,9 +1326,9 @@ extern "C" int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch*
                     "anomaly_score_noalloc: this batch needs %zu bytes of scratch but the fixed scratch holds %zu; "
                     "score fewer or shorter cycles per call, or use anomaly_score with a workspace",
                     L.total, kNoAllocScratchBytes);
-    void* scratch = nullptr;
-    if ((rc = noalloc_scratch(&scratch))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    void* scratch = nullptr;
+    if ((rc = noalloc_scratch(st, &scratch))) return rc;
     char* ws = (char*)scratch;
     // prepare() zeroes the header and progress counters left by the previous call
     if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
@@ -1263,6 +1338,20 @@ extern "C" int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch*
     p.score_out = score;
     if ((rc = launch_dp(kModePlen, L, p, opt, st))) return rc;
     return ok();
+}
+
+// The status word of the fixed scratch (the header at its start), read like
+// wts_read_status reads a workspace's: after the stream has reached every call
+// queued on it.
+extern "C" int wts_noalloc_read_status(void* stream, int32_t* status)
+{
+    using namespace wts;
+    if (!status) return fail(WTS_EINVAL, "status is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    void* scratch = nullptr;
+    int rc = noalloc_scratch(st, &scratch);
+    if (rc) return rc;
+    return wts_read_status(scratch, stream, status);
 }
 
 // Detection thresholds and F2 (Sec. 5.3): host arithmetic on the T scores.
@@ -1435,8 +1524,15 @@ int soft_objective(const double* x, double* f, double* g, void* ctx)
     e = cudaMemcpyAsync(o.vals.data(), o.d_values, (size_t)o.Y->T * sizeof(float), cudaMemcpyDeviceToHost, o.st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(o.gf.data(), o.d_grad, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, o.st);
+    WsHeader h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, o.ws, sizeof(h), cudaMemcpyDeviceToHost, o.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(o.st);
     if (e != cudaSuccess) { o.err = cuda_fail(e, "objective read-back"); return 1; }
+    if (status_of(h) != WTS_OK) {
+        o.err = fail(status_of(h), status_of(h) == WTS_EINVAL ? "a sample of B or of the batch is not finite"
+                                                              : "a wait inside the soft-DTW kernels gave up");
+        return 1;
+    }
     double s = 0.0;
     for (int k = 0; k < o.Y->T; ++k) s += o.w[k] * (double)o.vals[k];
     *f = s;

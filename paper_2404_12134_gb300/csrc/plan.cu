@@ -120,7 +120,51 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
     if (threadIdx.x == 0) sp.prefix[P] = (int32_t)run;
 }
 
+// true if the float with these bits is NaN or +-inf
+__device__ __forceinline__ bool nonfinite_bits(uint32_t u) { return (u & 0x7f800000u) == 0x7f800000u; }
+
+// Grid-stride scan of two arrays; 16-byte loads where the pointer allows.
+__device__ bool scan_nonfinite(const float* x, int64_t n, int64_t tid, int64_t nthr)
+{
+    if (x == nullptr || n <= 0) return false;
+    bool bad = false;
+    const int64_t head = min(n, (int64_t)(((16 - ((uintptr_t)x & 15)) & 15) >> 2));
+    for (int64_t i = tid; i < head; i += nthr) bad |= nonfinite_bits(__float_as_uint(x[i]));
+    const int64_t n4 = (n - head) >> 2;
+    const uint4* x4 = reinterpret_cast<const uint4*>(x + head);
+    for (int64_t i = tid; i < n4; i += nthr) {
+        const uint4 v = __ldcs(x4 + i);
+        bad |= nonfinite_bits(v.x) | nonfinite_bits(v.y) | nonfinite_bits(v.z) | nonfinite_bits(v.w);
+    }
+    for (int64_t i = head + 4 * n4 + tid; i < n; i += nthr) bad |= nonfinite_bits(__float_as_uint(x[i]));
+    return bad;
+}
+
+__global__ void __launch_bounds__(256) check_finite_kernel(const float* a, int64_t na, const float* b, int64_t nb,
+                                                           WsHeader* hdr)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const bool bad = scan_nonfinite(a, na, tid, nthr) | scan_nonfinite(b, nb, tid, nthr);
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) {
+        atomicExch(&hdr->status, kDevBadInput);
+        atomicExch(&hdr->abort, 1);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_check_finite(const float* a, int64_t na, const float* b, int64_t nb, WsHeader* hdr, int sms,
+                                cudaStream_t st)
+{
+    const int64_t n = (na > 0 ? na : 0) + (nb > 0 ? nb : 0);
+    int64_t blocks = (n / 4 + 255) / 256;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    check_finite_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, na, b, nb, hdr);
+    return cudaGetLastError();
+}
 
 void launch_setup(const SetupParams& sp, cudaStream_t st)
 {

@@ -88,4 +88,11 @@ __host__ __device__ inline int64_t band_bound_of(double band, int64_t M, int64_t
 
 void launch_setup(const SetupParams& sp, cudaStream_t st);
 
+// Scan a[0..na) and b[0..nb) (either may be null) for a non-finite value (NaN
+// or +-inf, Sec. 3.1 removes missing values before alignment); if one is
+// found, set hdr->status = kDevBadInput and hdr->abort = 1, so that every
+// kernel of the call leaves before doing any work.  sms sizes the grid.
+cudaError_t launch_check_finite(const float* a, int64_t na, const float* b, int64_t nb, WsHeader* hdr, int sms,
+                                cudaStream_t st);
+
 }  // namespace wts

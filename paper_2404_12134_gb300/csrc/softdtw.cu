@@ -229,7 +229,9 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
                 column(std::true_type{});
             else
                 column(std::false_type{});
-            if (hcur != nullptr && lane == 31) __stcg(hcur + j, col[R - 1]);
+            // NaN (from finite samples whose squared differences overflow) is
+            // stored as -inf: a slot is NaN only while it is unwritten
+            if (hcur != nullptr && lane == 31) __stcg(hcur + j, fmaxf(col[R - 1], -inf_f()));
         }
         if (rs != nullptr) {
             float4* dst = reinterpret_cast<float4*>(rs + (int64_t)s * 32 * R);
@@ -448,8 +450,9 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
             else
                 column(std::false_type{});
             if (emine != nullptr && lane == 0 && !p.skip_handoff) {
-                __stcg(emine + 2 * j, pack2(rp[0], dp[0]));
-                __stcg(emine + 2 * j + 1, pack2(ep[0], 0.f));
+                // (NaN from overflowing samples stored as -inf, as in the forward)
+                __stcg(emine + 2 * j, pack2(fmaxf(rp[0], NINF), dp[0]));
+                __stcg(emine + 2 * j + 1, pack2(fmaxf(ep[0], NINF), 0.f));
             }
         }
         // the slot just read (its values are consumed) takes step s + kRPre
@@ -502,15 +505,21 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
     }
 }
 
-__global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g, int T, int64_t M,
-                                   int d, float* __restrict__ out)
+// g == null: Eq. 7's weights lambda_k / m_k with lambda_k = 1, i.e. 1 / N_k
+// (N_k from the offsets), rounded to FP32 as a caller's FP32 weights would be.
+__global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g,
+                                   const int64_t* __restrict__ offsets, int T, int64_t M, int d,
+                                   float* __restrict__ out)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = M * d;
     if (q >= n) return;
     double acc = 0.0;
-    for (int k = 0; k < T; ++k)
-        acc = __fma_rn((double)__ldg(g + k), (double)__ldg(gpart + (int64_t)k * n + q), acc);
+    for (int k = 0; k < T; ++k) {
+        const float gk = g ? __ldg(g + k)
+                           : __double2float_rn(__ddiv_rn(1.0, (double)(__ldg(offsets + k + 1) - __ldg(offsets + k))));
+        acc = __fma_rn((double)gk, (double)__ldg(gpart + (int64_t)k * n + q), acc);
+    }
     out[q] = __double2float_rn(acc);
 }
 
@@ -605,11 +614,11 @@ int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded, int co
     return 0;
 }
 
-cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, int T, int64_t M, int d,
-                                       float* grad_B, cudaStream_t st)
+cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, const int64_t* offsets, int T, int64_t M,
+                                       int d, float* grad_B, cudaStream_t st)
 {
     const int64_t n = M * d;
-    grad_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gpart, g, T, M, d, grad_B);
+    grad_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gpart, g, offsets, T, M, d, grad_B);
     return cudaGetLastError();
 }
 

@@ -42,9 +42,10 @@ cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, 
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0, int cost_kind = 0);
 
-// grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending)
-cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, int T, int64_t M, int d,
-                                       float* grad_B, cudaStream_t st);
+// grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending); g == null
+// takes g[k] = 1 / N_k (Eq. 7 with lambda_k = 1) from the cycle offsets
+cudaError_t launch_softdtw_grad_reduce(const float* gpart, const float* g, const int64_t* offsets, int T, int64_t M,
+                                       int d, float* grad_B, cudaStream_t st);
 
 // One Adam step on n parameters (m, v: first / second moments, t >= 1).
 cudaError_t launch_adam(float* x, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,

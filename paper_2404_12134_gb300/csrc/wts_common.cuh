@@ -21,8 +21,9 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kMaxD = 16;              // channels handled (zero-padded up to the template D)
 constexpr long long kSpinLimit = 1ll << 27;   // polls before a wait gives up (~tens of seconds)
 
-// Device status word values (first word of every workspace).
-enum DevStatus : int { kDevOk = 0, kDevTimeout = 1 };
+// Device status word values (first word of every workspace): a wait gave up,
+// or a sample of the inputs is not finite (found before any DP work).
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevBadInput = 2 };
 // local cost delta(b_i, y_j) (Sec. 3.2): the squared l2 norm, or the norm itself
 enum LocalCost : int { kCostSqEuclid = 0, kCostL2 = 1 };
 
@@ -61,7 +62,10 @@ __device__ __forceinline__ int ld_volatile(const int* p)
 // before every launch; a producer writes each slot once with a plain store and
 // a consumer polls the slot until it is no longer NaN.  Each slot is one
 // single-copy-atomic word (4 or 8 bytes), so no flag and no fence is needed.
-// Costs are never NaN for finite inputs.
+// Hard-min costs are never NaN for finite inputs (a non-finite sample is
+// rejected before the wavefront runs); the soft-DTW kernels also map a NaN
+// from overflowing finite inputs to a non-NaN value before storing a slot, so
+// no wait can be set off by data.
 __device__ __forceinline__ bool is_nan_bits(uint32_t bits) { return (bits & 0x7fffffffu) > 0x7f800000u; }
 
 // Spin (warp-uniform) until no lane reports `missing`; `reload` re-reads the

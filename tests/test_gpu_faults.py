@@ -54,3 +54,71 @@ def test_wait_gives_up_and_reports(wts, call):
     assert wts.read_status(ws.buf) == 0
     s32, c32, L32 = oracle.score(B, b.data, b.offsets, "f32")
     assert (c.cpu().numpy() == c32).all() and (L.cpu().numpy() == L32).all()
+
+
+def _nonfinite_case(where, value):
+    B, b = _case()
+    B = B.copy()
+    data = b.data.copy()
+    if where == "cycle":
+        data[int(b.offsets[1]) + 37, 1] = value       # one sample of the second cycle
+    else:
+        B[611, 0] = value                             # one prototype sample
+    return B, synth.pack([data[int(b.offsets[k]):int(b.offsets[k + 1])] for k in range(b.T)])
+
+
+@pytest.mark.parametrize("value", [np.nan, np.inf, -np.inf], ids=["nan", "inf", "-inf"])
+@pytest.mark.parametrize("where", ["cycle", "prototype"])
+@pytest.mark.parametrize("call", ["score", "align", "dba", "soft", "subdtw", "pairwise"])
+def test_nonfinite_sample_is_rejected_on_the_device(wts, call, where, value):
+    """Sec. 3.1 removes missing values before alignment: a NaN or +-inf sample
+    is found by the device-side scan before any DP work, every kernel of the
+    call leaves at once, and the workspace status reads WTS_EINVAL (not a
+    timeout: a short poll limit makes a regression show as WTS_ETIMEOUT
+    quickly).  The next call on the same workspace is exact."""
+    from paper_2404_12134_gb300._abi import WTS_EINVAL
+    if call == "pairwise" and where == "prototype":
+        pytest.skip("the pairwise matrix has no prototype")
+    B, b = _nonfinite_case(where, value)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    ws = wts.Workspace()
+    o = wts.options(spin_limit=1 << 16)
+    if call == "score":
+        wts.anomaly_score(Bt, gb, o, ws=ws)
+    elif call == "align":
+        wts.dtw_align(Bt, gb, o, ws=ws)
+    elif call == "dba":
+        wts.dba_iterate(Bt, gb, o, ws=ws)
+    elif call == "soft":
+        wts.softdtw_forward(Bt, gb, 0.5, o, ws=ws)
+        wts.softdtw_backward(Bt, gb, 0.5, None, o, ws=ws)
+    elif call == "subdtw":
+        wts.subdtw_align(Bt, gb, o, ws=ws)
+    else:
+        wts.pairwise_dtw(gb, o, ws=ws)
+    assert wts.read_status(ws.buf) == WTS_EINVAL
+    B0, b0 = _case()
+    gb0 = wts.Batch.from_numpy(b0.data, b0.offsets)
+    s, c, L = wts.anomaly_score(torch.from_numpy(B0).cuda(), gb0, ws=ws)
+    assert wts.read_status(ws.buf) == 0
+    s32, c32, L32 = oracle.score(B0, b0.data, b0.offsets, "f32")
+    assert (c.cpu().numpy() == c32).all() and (L.cpu().numpy() == L32).all()
+
+
+def test_softdtw_overflowing_finite_samples_never_look_unwritten(wts):
+    """Finite samples whose squared differences overflow FP32 make the soft
+    recursion produce NaN; the kernels store such a value in a hand-off slot
+    as -inf, so a consumer never mistakes it for a slot still unwritten: the
+    forward and backward finish without a timeout."""
+    B, b = _case()
+    big = (b.data * np.float32(3e19)).astype(np.float32)
+    bb = synth.pack([big[int(b.offsets[k]):int(b.offsets[k + 1])] for k in range(b.T)])
+    assert np.isfinite(bb.data).all()
+    gb = wts.Batch.from_numpy(bb.data, bb.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    ws = wts.Workspace()
+    o = wts.options(spin_limit=1 << 20)
+    wts.softdtw_forward(Bt, gb, 0.5, o, ws=ws)
+    wts.softdtw_backward(Bt, gb, 0.5, None, o, ws=ws)
+    assert wts.read_status(ws.buf) == 0

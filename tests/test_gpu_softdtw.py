@@ -116,12 +116,42 @@ def test_soft_barycenter_decreases_objective(wts):
     gb = wts.Batch.from_numpy(b.data, b.offsets)
     M = 200
     B0 = wts.euclid_mean(gb, M)
-    B, hist, w = wts.softdtw_barycenter(gb, M, gamma=0.1, steps=30, lr=2e-2, init=B0)
+    B, hist = wts.softdtw_barycenter(gb, M, gamma=0.1, steps=30, lr=2e-2, init=B0)
     f0 = oracle.softdtw_batch(B0.cpu().numpy(), b.data, b.offsets, 0.1, want_grad=False)[1]
     f1 = oracle.softdtw_batch(B.cpu().numpy(), b.data, b.offsets, 0.1, want_grad=False)[1]
     assert f1 < f0
-    h = (hist.cpu().numpy() * w.cpu().numpy()).sum(1)
+    w = (1.0 / b.lengths).astype(np.float32)
+    h = (hist.cpu().numpy().astype(np.float64) * w).sum(1)
     assert h[-1] < h[0]
+
+
+@pytest.mark.parametrize("explicit_weights", [False, True])
+def test_adam_barycenter_call_equals_primitive_loop(wts, explicit_weights):
+    """wts_softdtw_barycenter_adam (the library's own loop) equals, bit for
+    bit, the same steps driven one C-ABI call at a time: softdtw_forward,
+    softdtw_backward with the weights (NULL: the library's 1 / N_k), and
+    wts_adam_step.  Also: NULL weights give exactly the FP32 1 / N_k."""
+    b = synth.config_batch(2, scale=0.03, T=6)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M, gamma, steps, lr = 300, 0.1, 7, 3e-2
+    B0 = wts.euclid_mean(gb, M)
+    w = torch.from_numpy((1.0 / b.lengths).astype(np.float32)).cuda()
+    B, hist = wts.softdtw_barycenter(gb, M, gamma, steps=steps, lr=lr, init=B0,
+                                     weights=w if explicit_weights else None)
+    Bp = B0.clone()
+    m = torch.zeros_like(Bp)
+    v = torch.zeros_like(Bp)
+    ws = wts.Workspace()
+    grad = torch.empty_like(Bp)
+    hp = []
+    for t in range(1, steps + 1):
+        hp.append(wts.softdtw_forward(Bp, gb, gamma, ws=ws))
+        wts.softdtw_backward(Bp, gb, gamma, w, ws=ws, grad_B=grad)
+        g_null = wts.softdtw_backward(Bp, gb, gamma, None, ws=ws)
+        assert torch.equal(g_null, grad)
+        wts.adam_step(Bp, grad, m, v, t, lr=lr)
+    assert torch.equal(B, Bp)
+    assert torch.equal(hist, torch.stack(hp))
 
 
 def test_gamma_validation(wts):

@@ -45,6 +45,36 @@ def test_noalloc_matches_anomaly_score_on_consecutive_calls():
             assert torch.equal(x, y)
 
 
+@pytest.mark.gpu
+def test_noalloc_status_is_readable():
+    """The fixed scratch's device status word is readable by the caller: a
+    wait made to give up (host-set fault injection, short poll limit) shows as
+    WTS_ETIMEOUT, a non-finite sample as WTS_EINVAL, and the next normal call
+    reads WTS_OK with the same output as anomaly_score."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12134_gb300 import api
+    _lib()
+    rng = np.random.default_rng(99)
+    B = rng.normal(size=(1300, 2)).astype(np.float32)          # several bands: hand-off waits exist
+    cyc = [rng.normal(size=(n, 2)).astype(np.float32) for n in (700, 900)]
+    b = synth.pack(cyc)
+    gb = api.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    api.anomaly_score_noalloc(Bt, gb, api.options(fault_skip_handoff=1, spin_limit=2000))
+    assert api.noalloc_status() == _abi.WTS_ETIMEOUT
+    bad = b.data.copy()
+    bad[5, 1] = np.nan
+    gbad = api.Batch.from_numpy(bad, b.offsets)
+    api.anomaly_score_noalloc(Bt, gbad, api.options(spin_limit=1 << 16))
+    assert api.noalloc_status() == _abi.WTS_EINVAL
+    got = api.anomaly_score_noalloc(Bt, gb)
+    assert api.noalloc_status() == _abi.WTS_OK
+    ref = api.anomaly_score(Bt, gb)
+    for x, y in zip(got, ref):
+        assert torch.equal(x, y)
+
+
 def test_noalloc_rejects_oversized_batch_before_launch():
     lib = _lib()
     lengths = np.array([30000] * 8, dtype=np.int64)
