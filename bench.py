@@ -193,16 +193,18 @@ def hbm_peak_gbs() -> float:
 
 
 def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None, ckpt: bool = False,
-                band: float = 0.0):
+                band: float = 0.0, per_pair: bool = False, peaks: dict | None = None):
     """Soft-DTW forward + backward on the single-channel barycenter workload:
-    64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB);
+    64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB), the
+    Eq. 7 weights 1 / N_k (the library's default);
     band > 0: with the Sakoe-Chiba band (GCUPS then also over the cells in
-    the band)."""
+    the band); per_pair: also the plain form, one forward + backward call per
+    cycle; peaks (measured ex2 / lg2 rates): a roofline for each kernel."""
     sb = synth.config_batch(2, T=T)
     M = synth.PROTO_LEN[2]
     gb = api.Batch.from_numpy(sb.data, sb.offsets, device=dev)
     B = api.euclid_mean(gb, M)
-    w = torch.from_numpy((1.0 / sb.lengths).astype(np.float32)).to(dev)
+    w = None
     ws = api.Workspace(dev)
     grad = torch.empty_like(B)
     opt = api.options(dir_mode=1, ckpt_bands=1 << 20, band=band) if ckpt else (api.options(band=band) if band else None)
@@ -229,10 +231,46 @@ def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None 
            "fwd_bwd_gcups": cells / ((fwd + bwd) * 1e-3) / 1e9,
            "fwd_gcups": cells / (fwd * 1e-3) / 1e9, "bwd_gcups": cells / (bwd * 1e-3) / 1e9,
            "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf),
-           "loss": float((vals * w).sum())}
+           "loss": float((vals.double().cpu().numpy() * (1.0 / sb.lengths).astype(np.float32)).sum())}
     if band:
         inb = band_cells(M, sb.lengths, band)
         res.update(band=band, cells_in_band=inb, fwd_bwd_gcups_in_band=inb / ((fwd + bwd) * 1e-3) / 1e9)
+    if peaks and not band and not ckpt:
+        # per kernel: the MUFU bound (forward 2 ex2 + 1 lg2 per cell, backward
+        # 3 ex2) and the HBM bound of the stored R (4 B written per cell
+        # forward, 4 B read backward); the larger one is the kernel's roofline
+        hbm = hbm_peak_gbs() * 1e9
+        for name, ms, mufu_s in (("fwd", fwd, cells * (2 / peaks["ex2"] + 1 / peaks["lg2"])),
+                                 ("bwd", bwd, cells * 3 / peaks["ex2"])):
+            hbm_s = cells * 4 / hbm
+            t = ms * 1e-3
+            if hbm_s >= mufu_s:
+                res[f"roofline_{name}"] = {"bound": "hbm", "achieved": cells * 4 / t / 1e9, "peak": hbm / 1e9,
+                                           "unit": "GB/s", "frac": hbm_s / t, "mufu_frac": mufu_s / t}
+            else:
+                res[f"roofline_{name}"] = {"bound": "mufu", "frac": mufu_s / t, "hbm_frac": hbm_s / t}
+    if per_pair:
+        # the plain form: one forward + backward call per cycle, in turn
+        ws1 = api.Workspace(dev)
+        singles = []
+        for k in range(sb.T):
+            o0, o1 = int(sb.offsets[k]), int(sb.offsets[k + 1])
+            singles.append(api.Batch(gb.data[o0:o1], torch.tensor([0, o1 - o0], device=dev),
+                                     np.array([0, o1 - o0], dtype=np.int64)))
+        api.softdtw_forward(B, singles[0], gamma, None, ws=ws1)
+        api.softdtw_backward(B, singles[0], gamma, None, None, ws=ws1, grad_B=grad)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for one in singles:
+            api.softdtw_forward(B, one, gamma, None, ws=ws1)
+            api.softdtw_backward(B, one, gamma, None, None, ws=ws1, grad_B=grad)
+        e1.record()
+        barrier()
+        pp = e0.elapsed_time(e1)
+        res["per_pair_launch_ms"] = pp
+        res["per_pair_launch_fwd_bwd_gcups"] = cells / (pp * 1e-3) / 1e9
+        del ws1
     del ws, gb
     return res
 
@@ -305,7 +343,7 @@ def scoring_leg(api, torch, dev, barrier, T: int | None = None, per_pair: bool =
     return res
 
 
-def long_leg(api, torch, dev, barrier, iters: int = 2):
+def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
     """Very long cycles: 32 cycles x 3 ch, pre-gap N ~ U(100k, 120k), M =
     110,000 (medoid of a seeded 8-cycle subset, resampled; untimed).  DBA with
     every code stored (~95 GB) against checkpoint mode (band rows kept, codes
@@ -322,12 +360,11 @@ def long_leg(api, torch, dev, barrier, iters: int = 2):
     B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M)
     res = {"workload": "32 cycles x 3 ch FP32, pre-gap N ~ U(100k,120k), 2% gaps, M=110000", "cells_per_iter": cells}
     outs = {}
-    from paper_2404_12134_gb300 import _abi
-    tuned, _ = api.autotune(_abi.OP_DBA_ITERATE, B0, gb)
-    res["options"] = {"rows_per_thread": tuned.rows_per_thread, "warps_per_block": tuned.warps_per_block}
+    # the default launch shape (16 rows per lane, 4 warps per block: what the
+    # autotuner keeps for the 6-channel batch; not re-tuned here, for time)
+    res["options"] = {"rows_per_thread": 16, "warps_per_block": 4}
     for name, mode in (("stored", 0), ("checkpoint", 1)):
-        opt = api.options(rows_per_thread=tuned.rows_per_thread, warps_per_block=tuned.warps_per_block,
-                          dir_mode=mode, ckpt_bands=16)
+        opt = api.options(rows_per_thread=16, warps_per_block=4, dir_mode=mode, ckpt_bands=16)
         ws = api.Workspace(dev)
         B = B0.clone()
         Bn, cnt, cb, _ = api.dba_iterate(B, gb, opt, ws=ws)          # warm-up
@@ -344,12 +381,13 @@ def long_leg(api, torch, dev, barrier, iters: int = 2):
         res[name] = {"s_per_dba_iter": ms * 1e-3, "gcups": cells / (ms * 1e-3) / 1e9,
                      "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf)}
         del ws
+        torch.cuda.empty_cache()
     res["checkpoint_prototype_identical"] = bool(torch.equal(outs["stored"], outs["checkpoint"]))
     # soft-DTW forward + backward, 8 pairs, checkpointed (64 bands of R per group)
     gamma = 0.1
     opt = api.options(dir_mode=1, ckpt_bands=64)
     ws = api.Workspace(dev)
-    w = torch.from_numpy((1.0 / sub.lengths).astype(np.float32)).to(dev)
+    w = None                                   # Eq. 7's 1 / N_k (the library's default)
     api.softdtw_forward(B0, gsub, gamma, opt, ws=ws)
     api.softdtw_backward(B0, gsub, gamma, w, opt, ws=ws)
     barrier()
@@ -366,6 +404,26 @@ def long_leg(api, torch, dev, barrier, iters: int = 2):
                                  "bwd_incl_recompute_ms": b_ms, "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
                                  "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf)}
     del ws
+    torch.cuda.empty_cache()
+    if cpu_sample:
+        # the oracle (FP64) on a bounded sample: a full pair keeps a 1-byte
+        # choice per cell (12 GB of host memory) and takes about a minute on
+        # one core, so 16 cycles are cut to their first 2,000 samples and
+        # aligned against the whole 110,000-row prototype, one per thread
+        import oracle
+        ncores = os.cpu_count() or 1
+        os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+        n = min(16, ncores, b.T)
+        cut = [b.cycle(k)[:2000] for k in range(n)]
+        sb = synth.pack(cut)
+        Bh = synth.clean_prototype(b, M)       # the oracle's inputs come from the generator only
+        t0 = time.perf_counter()
+        oracle.score(Bh, sb.data, sb.offsets, "f64")
+        dt = time.perf_counter() - t0
+        c = M * int(sb.lengths.sum())
+        res["cpu_oracle_subset"] = {"sample": f"{n} cycles cut to their first 2,000 samples against the full "
+                                              f"{M}-row prototype, DTW + |pi| (FP64), one cycle per thread",
+                                    "s": dt, "gcups": c / dt / 1e9, "threads": n, "cells": c}
     return res
 
 
@@ -570,6 +628,54 @@ def l2_cost_leg(api, torch, dev, st, barrier, gb, B0, cells: int, ws, iters: int
             "anomaly_score_gcups": cells / (sc_ms * 1e-3) / 1e9, "device_status": api.read_status(ws.buf)}
 
 
+def small_dba_leg(api, torch, dev, barrier, cpu_sample: bool = True):
+    """The small DBA workload end to end: 16 cycles of 1.0-1.2k, the medoid
+    (pairwise DTW on the GPU) as the start, 10 DBA iterations, then the
+    scores; s per iteration from CUDA events; the one-pair-per-launch
+    alignment of the same batch; the oracle's iteration on the host."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    b = synth.config_batch(0)
+    gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
+    ws = api.Workspace(dev)
+    for _ in range(2):                       # warm-up of the whole workflow
+        idx, _ = api.medoid(api.pairwise_dtw(gb, ws=ws))
+        Bw = gb.data[int(b.offsets[int(idx)]):int(b.offsets[int(idx) + 1])].clone()
+        api.dba_iterate(Bw, gb, ws=ws)
+    barrier()
+    t0 = time.perf_counter()
+    idx, _ = api.medoid(api.pairwise_dtw(gb, ws=ws))
+    k = int(idx)
+    B = gb.data[int(b.offsets[k]):int(b.offsets[k + 1])].clone()
+    M0 = B.shape[0]
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        B, _, _, _ = api.dba_iterate(B, gb, ws=ws)
+    e1.record()
+    score, cost, _ = api.anomaly_score(B, gb, ws=ws)
+    barrier()
+    total = time.perf_counter() - t0
+    cells0 = M0 * int(b.lengths.sum())
+    it_ms = e0.elapsed_time(e1) / 10
+    pp_ms = per_pair_align_ms(api, torch, dev, B, b, gb, barrier)
+    res = {"workload": "16 cycles x 1 ch FP32, pre-gap N ~ U(1000,1200), 2% gaps, medoid start, 10 DBA "
+                       "iterations + scores", "M": M0, "cells_per_iter": cells0, "s_per_dba_iter": it_ms * 1e-3,
+           "gcups": cells0 / (it_ms * 1e-3) / 1e9, "medoid_10_iterations_scores_s": total,
+           "per_pair_align_s_per_iter": pp_ms * 1e-3, "device_status": api.read_status(ws.buf)}
+    if cpu_sample:
+        # the oracle's inputs come from the generator only (its time does not
+        # depend on the prototype's values): the first cycle as the prototype
+        B_or = b.cycle(0)
+        t1 = time.perf_counter()
+        oracle.dba_iterate(B_or.astype(np.float64), b.data, b.offsets, "f64")
+        cpu_s = time.perf_counter() - t1
+        res.update(cpu_oracle_s_per_iter=cpu_s, cpu_oracle_gcups=cells0 / cpu_s / 1e9, cpu_oracle_threads=ncores)
+    del ws
+    return res
+
+
 def table_leg(api, torch, dev, barrier):
     """Entries of the results table not covered by the other legs: the small
     DBA workload end to end (medoid init, 10 DBA iterations, scores), the
@@ -601,7 +707,7 @@ def table_leg(api, torch, dev, barrier):
     it_ms = e0.elapsed_time(e1) / 10
     pp_ms = per_pair_align_ms(api, torch, dev, B, b, gb, barrier)
     t1 = time.perf_counter()
-    oracle.dba_iterate(B.cpu().numpy().astype(np.float64), b.data, b.offsets, "f64")
+    oracle.dba_iterate(b.cycle(0).astype(np.float64), b.data, b.offsets, "f64")
     cpu_s = time.perf_counter() - t1
     res["small_dba"] = {"M": M0, "cells_per_iter": cells0, "s_per_dba_iter": it_ms * 1e-3,
                         "gcups": cells0 / (it_ms * 1e-3) / 1e9, "workflow_s": total,
@@ -841,17 +947,25 @@ def run_gpu(args):
         out["l2_cost"] = l2_cost_leg(api, torch, dev, st, barrier, gb, B0, cells, ws)
 
     if not args.no_extras:
-        out["scoring"] = scoring_leg(api, torch, dev, barrier)
-        out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier)
-        out["softdtw_band_0.6"] = softdtw_leg(api, torch, dev, st, barrier, band=0.6)
-        out["barycenters"] = bary_leg(api, torch, dev, barrier)
-        out["segmentation"] = segment_leg(api, torch, dev, barrier)
-        out["banded_dba"] = banded_dba_leg(api, torch, dev, barrier, gb, b, B0)
         out["measured_peaks_probe"] = {k: api.peak_probe(i) / 1e12 for i, k in
                                        enumerate(("fp32_fma_tops", "fp32_minmax_tops", "mufu_ex2_tops",
                                                   "mufu_lg2_tops", "fp32x2_fma_tops", "fp32_min3_tops"))}
         ex2 = out["measured_peaks_probe"]["mufu_ex2_tops"] * 1e12
         lg2 = out["measured_peaks_probe"]["mufu_lg2_tops"] * 1e12
+        # the plain one-pair-per-launch form of the benchmark's alignment
+        pp1 = per_pair_align_ms(api, torch, dev, B, b, gb, barrier)
+        out["batched_dba_per_pair_align"] = {"ms": pp1, "gcups": cells / (pp1 * 1e-3) / 1e9,
+                                             "form": "dtw_align once per cycle, in turn"}
+        out["scoring"] = scoring_leg(api, torch, dev, barrier)
+        out["softdtw"] = softdtw_leg(api, torch, dev, st, barrier, per_pair=True, peaks={"ex2": ex2, "lg2": lg2})
+        out["softdtw_band_0.6"] = softdtw_leg(api, torch, dev, st, barrier, band=0.6)
+        out["barycenters"] = bary_leg(api, torch, dev, barrier)
+        out["segmentation"] = segment_leg(api, torch, dev, barrier)
+        out["banded_dba"] = banded_dba_leg(api, torch, dev, barrier, gb, b, B0)
+        out["small_dba"] = small_dba_leg(api, torch, dev, barrier, cpu_sample=rank == 0)
+        del ws
+        torch.cuda.empty_cache()
+        out["long"] = long_leg(api, torch, dev, barrier, cpu_sample=rank == 0)
         sd = out["softdtw"]
         cells_s = sd["cells"]
         t_mufu = cells_s * (2 / ex2 + 1 / lg2) + cells_s * 3 / ex2          # fwd: 2 ex2 + 1 lg2, bwd: 3 ex2
@@ -874,7 +988,9 @@ def run_gpu(args):
         ncores = os.cpu_count() or 1
         os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
         n = min(ncores, b.T)
-        g, dt, c = oracle_dba_sample(b, B.cpu().numpy(), n)
+        # the oracle's inputs come from the generator only (its time does not
+        # depend on the prototype's values)
+        g, dt, c = oracle_dba_sample(b, synth.clean_prototype(b, M_PROTO), n)
         out["cpu_baseline"] = {"value": g, "unit": "GCUPS", "cores": ncores, "kind": "oracle",
                                "sample": f"{n} of {b.T} cycles, one oracle DBA iteration (FP64), "
                                          f"{dt:.1f} s wall on {ncores} threads"}

@@ -401,6 +401,7 @@ int align_into(const Layout& L, char* ws, const float* B, const wts_batch* Y, co
     bt.jhi = jhi;
     bt.plen = plen;
     bt.M = L.M;
+    bt.hdr = p.hdr;
     cudaError_t e;
     if (L.group_bands == 0) {
         // every cell's code stored, one backtrack
@@ -687,6 +688,7 @@ int subdtw_bt_part(const Layout& L, char* ws, const wts_options* opt, cudaStream
     bt.subseq = 1;
     bt.bstar = b_star;
     bt.astar = a_star;
+    bt.hdr = p.hdr;
     cudaError_t e;
     {
         Prof pr("backtrack", st);

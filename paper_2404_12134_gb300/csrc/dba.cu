@@ -52,6 +52,9 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
     __shared__ __align__(8) uint64_t bars[kBtWarps];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
+    // the call's DP left early (a non-finite sample, or a wait that gave up):
+    // its codes and b* were never written, so there is nothing to walk
+    if (p.hdr != nullptr && ld_volatile(&p.hdr->abort)) return;
     uint32_t* win = win_all[wid];
     uint64_t* bar = &bars[wid];
     if (lane == 0) {
@@ -118,6 +121,13 @@ __global__ void __launch_bounds__(32 * kBtWarps) backtrack_kernel(BTParams p)
             if (lane == 0) { jhi[i] = j; sg[0] = start; }
         } else if (p.state == nullptr || p.first) {
             i = pd.M - 1; j = p.subseq ? p.bstar[pd.out] : N - 1; len = 0;
+            if (j < 0 || j >= N) {                    // b* is not a column of this cycle: no walk
+                if (lane == 0) {
+                    if (p.astar) p.astar[pd.out] = -1;
+                    if (p.plen) p.plen[pd.out] = -1;
+                }
+                continue;
+            }
             if (lane == 0) jhi[i] = j;
         } else {
             i = p.state[3 * q]; j = p.state[3 * q + 1]; len = p.state[3 * q + 2];
@@ -261,6 +271,7 @@ __global__ void __launch_bounds__(128) bt_seg_final_kernel(BTParams p)
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (q >= p.P) return;
+    if (p.hdr != nullptr && ld_volatile(&p.hdr->abort)) return;      // nothing was walked
     const PairDesc pd = p.pairs[q];
     const int last = (p.round & 1);                  // exit slot of the last round
     const int nseg = (int)((pd.M + p.seg_rows - 1) / p.seg_rows);

@@ -37,6 +37,9 @@ struct BTParams {
     // the row below the segment.
     int nseg, seg_rows, round;
     int32_t* seg;
+    // the call's workspace header: a raised abort word (set with the status
+    // when the DP left early) makes the walk do nothing (may be null)
+    const WsHeader* hdr;
 };
 
 // Rows per segment of the segmented walk.

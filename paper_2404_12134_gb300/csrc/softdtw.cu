@@ -338,7 +338,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     load_y(N - 1 - s_begin - lane);
     if (!last) load_e(N - 1 - s_begin - lane);
 
-#pragma unroll 2
+#pragma unroll 1
     for (int s = s_begin; s < steps; ++s) {
         float4 rcur[R / 4];
         cp_async_wait<kRPre - 1>();
@@ -469,8 +469,12 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 if (c < d) gout[(int64_t)(i0 + k) * d + c] = COST == kCostL2 ? g[k][c] : __fmul_rn(2.f, g[k][c]);
 }
 
+// Blocks of at most 4 warps.  The backward for one or two channels is held to
+// 96 registers so that five blocks fit per SM (20 warps, 3,040 on the GPU):
+// the 2,560 (pair, band) items of 64 pairs of 10k then all run at once,
+// instead of the last pairs waiting for the longest ones to finish.
 template <int D, int R, bool BWD, bool BANDED, int COST>
-__global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
+__global__ void __launch_bounds__(128, (BWD && D <= 2) ? 5 : 1) softdtw_kernel(SoftParams p)
 {
     extern __shared__ float4 rring_all[];
     const int lane = threadIdx.x & 31;

@@ -2,9 +2,10 @@
 through the C ABI, plus the autograd wrapper and the Adam barycenter.
 
 Tolerances, derived from the arithmetic:
-* values: within 2e-5 of the FP64 oracle, relative to max(|value|, 1)
-  (FP32 rounding of r along a path of M+N cells plus the ex2 / lg2
-  approximation errors, ~1e-7 per cell);
+* values: within 1e-5 of the FP64 oracle, relative to max(|value|, 1)
+  (the 1e-5 relative bar of the target; the floor 1 keeps the bar
+  meaningful for values near 0, which are differences of path sums; the
+  measured error is below 1.1e-6);
 * gradients: the exponent of every weight exp(((r(s) - r) - delta(s))/gamma)
   carries the FP32 rounding of r, of order ulp(r)/gamma, so no fixed relative
   bound holds at small gamma or large r.  The bar is that the kernel adds
@@ -32,7 +33,7 @@ def wts():
     return api
 
 
-VALUE_TOL = 2e-5
+VALUE_TOL = 1e-5
 
 
 def _grad_bar(B, b, gamma, weights, go):
