@@ -360,11 +360,12 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
     B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M)
     res = {"workload": "32 cycles x 3 ch FP32, pre-gap N ~ U(100k,120k), 2% gaps, M=110000", "cells_per_iter": cells}
     outs = {}
-    # the default launch shape (16 rows per lane, 4 warps per block: what the
-    # autotuner keeps for the 6-channel batch; not re-tuned here, for time)
-    res["options"] = {"rows_per_thread": 16, "warps_per_block": 4}
+    from paper_2404_12134_gb300 import _abi
+    tuned, _ = api.autotune(_abi.OP_DBA_ITERATE, B0, gb)
+    res["options"] = {"rows_per_thread": tuned.rows_per_thread, "warps_per_block": tuned.warps_per_block}
     for name, mode in (("stored", 0), ("checkpoint", 1)):
-        opt = api.options(rows_per_thread=16, warps_per_block=4, dir_mode=mode, ckpt_bands=16)
+        opt = api.options(rows_per_thread=tuned.rows_per_thread, warps_per_block=tuned.warps_per_block,
+                          dir_mode=mode, ckpt_bands=16)
         ws = api.Workspace(dev)
         B = B0.clone()
         Bn, cnt, cb, _ = api.dba_iterate(B, gb, opt, ws=ws)          # warm-up

@@ -88,7 +88,9 @@ typedef struct wts_options {
                                       per cycle); 1 = checkpoint + recompute: store only the band hand-off rows,
                                       recompute the codes of ckpt_bands bands at a time during the backtrack
                                       (one extra forward pass, bit-identical paths) */
-    int32_t ckpt_bands;            /* bands (of 32*rows_per_thread prototype rows) recomputed per group; 0 = 16 */
+    int32_t ckpt_bands;            /* bands (of 32*rows_per_thread prototype rows) recomputed per group; 0 = 16.
+                                      Soft-DTW keeps two groups' R (the backward of one group runs beside the
+                                      recompute of the next), DTW one group's codes */
     int32_t spin_limit;            /* polls before an in-kernel wait gives up (each ~0.1-1 us); 0 = 2^27 */
     int32_t fault_skip_handoff;    /* fault injection for tests: 1 = producers skip their hand-off rows, so
                                       consumers wait until spin_limit and the call ends with WTS_ETIMEOUT in
@@ -341,7 +343,9 @@ int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, 
  * in the workspace for softdtw_backward (4 bytes per cell plus a skew
  * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)); with opt->dir_mode = 1
  * only the band hand-off rows are kept and softdtw_backward recomputes R for
- * ckpt_bands bands at a time (one extra forward pass).
+ * ckpt_bands bands at a time (one extra forward pass; the recompute of the
+ * next group overlaps the backward of the current one, so R of two groups is
+ * kept).
  *   B [M][d] (d <= 8), gamma > 0 (gamma = 0 is DTW: use anomaly_score),
  *   value [T] out.
  */

@@ -211,8 +211,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             dw += pair_dir_words(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
         }
         if (op == kOpSoft) {
+            // checkpoint mode: two buffers of G bands (one group's R is read
+            // while the next group's is recomputed)
             const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
-            rs += pair_rstore_floats(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
+            rs += pair_rstore_floats(G > 0 ? (2 * G < nb ? 2 * G : nb) : nb, Np, L->R);
         }
     }
     if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
@@ -1007,34 +1009,60 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
         }
         if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
     } else {
-        // checkpoint mode: from the last band up, recompute R for G bands of
-        // every pair from the stored hand-off rows, then run the backward
-        // recursion through them; E hand-off rows persist across groups
+        // checkpoint mode: groups of G bands from the last band up.  R of the
+        // last group is recomputed first (from the stored hand-off rows); then
+        // each launch runs the backward recursion through group q (R buffer
+        // q mod 2) and, in the same launch, recomputes group q + 1 into the
+        // other buffer: the recompute items read only stored rows and never
+        // wait, so they fill the GPU beside the backward's band pipeline.  E
+        // hand-off rows persist across launches.
         const int nb = (int)cdiv(M, L.BR);
         const int G = L.group_bands;
-        for (int hi = nb; hi > 0; hi -= G) {
-            const int lo = hi - G > 0 ? hi - G : 0;
-            SoftParams r = p;
-            r.band_lo = lo;
-            r.band_cnt = hi - lo;
-            r.n_items = L.P * (hi - lo);
-            r.recompute = 1;
-            r.store_r = 1;
-            e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
-            if ((rc = soft_grid(L, 0, opt, &grid, &block, r.n_items))) return rc;
-            {
-                Prof pr("softdtw_fwd_recompute", st);
-                e = launch_softdtw_fwd(L.D, r, grid, block, st);
+        const int Q = (int)cdiv(nb, G);
+        auto group = [&](int q, int* lo, int* hi) {
+            *hi = nb - q * G;
+            *lo = *hi - G > 0 ? *hi - G : 0;
+        };
+        int lo = 0, hi = 0;
+        group(0, &lo, &hi);
+        SoftParams r = p;
+        r.band_lo = lo;
+        r.band_cnt = hi - lo;
+        r.n_items = L.P * (hi - lo);
+        r.rbuf_band0 = 0;
+        r.recompute = 1;
+        r.store_r = 1;
+        e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
+        if ((rc = soft_grid(L, 0, opt, &grid, &block, r.n_items))) return rc;
+        {
+            Prof pr("softdtw_fwd_recompute", st);
+            e = launch_softdtw_fwd(L.D, r, grid, block, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "soft-DTW recompute launch");
+        for (int q = 0; q < Q; ++q) {
+            SoftParams b = p;
+            group(q, &lo, &hi);
+            b.band_lo = lo;
+            b.band_cnt = hi - lo;
+            b.n_items = L.P * (hi - lo);
+            b.rbuf_band0 = (q & 1) * G;
+            b.recompute = 0;
+            b.n_rec = 0;
+            if (q + 1 < Q) {
+                int lo2 = 0, hi2 = 0;
+                group(q + 1, &lo2, &hi2);
+                b.n_rec = L.P * (hi2 - lo2);
+                b.rec_band_lo = lo2;
+                b.rec_band_cnt = hi2 - lo2;
+                b.rec_rbuf_band0 = ((q + 1) & 1) * G;
             }
-            if (e != cudaSuccess) return cuda_fail(e, "soft-DTW recompute launch");
-            r.recompute = 0;
             e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
-            if ((rc = soft_grid(L, 1, opt, &grid, &block, r.n_items))) return rc;
+            if ((rc = soft_grid(L, 1, opt, &grid, &block, (int64_t)b.n_items + b.n_rec))) return rc;
             {
                 Prof pr("softdtw_bwd", st);
-                e = launch_softdtw_bwd(L.D, r, grid, block, st);
+                e = launch_softdtw_bwd(L.D, b, grid, block, st);
             }
             if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
         }

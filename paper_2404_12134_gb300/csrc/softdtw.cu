@@ -108,8 +108,11 @@ __device__ __forceinline__ float local_cost(const float* bk, const float* y, flo
     return COST == kCostL2 ? __fsqrt_rn(acc) : acc;
 }
 
+// One band of the forward pass; rslot: the band's slot in the R store (when
+// store_r), recompute: start from the stored top row and write no hand-off row.
 template <int D, int R, bool BANDED, int COST>
-__device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane)
+__device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, int rslot,
+                                         bool recompute, bool store_r)
 {
     constexpr int BR = 32 * R;
     const int M = pd.M, N = pd.N, d = p.d;
@@ -135,8 +138,8 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     float prev_up = (top && lane == 0) ? 0.f : INF;
 
     const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
-    float* hcur = (last || p.recompute || p.skip_handoff) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
-    float* rs = p.store_r ? p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R : nullptr;
+    float* hcur = (last || recompute || p.skip_handoff) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
+    float* rs = store_r ? p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R : nullptr;
 
     // Sakoe-Chiba band (as in the hard-min wavefront): the band's columns
     // [jlo, jhi], the row above's [jtop_lo, jtop_hi] (the only columns its
@@ -241,7 +244,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
         }
     }
 
-    if (last && !p.recompute) {
+    if (last && !recompute) {
         const int ilast = M - 1 - band * BR;
         if (lane == ilast / R) {
             const int kk2 = ilast % R;
@@ -255,7 +258,8 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 }
 
 template <int D, int R, bool BANDED, int COST>
-__device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring)
+__device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring,
+                                         int rslot)
 {
     constexpr int BR = 32 * R;
     const int M = pd.M, N = pd.N, d = p.d;
@@ -289,7 +293,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // words {r, delta k} and {e, 0}, each NaN until written
     const u64* enext = last ? nullptr : reinterpret_cast<const u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)band * N);
     u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
-    const float* rs = p.rstore + pd.aux_off + (int64_t)(band - p.band_lo) * (N + 31) * 32 * R;
+    const float* rs = p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R;
 
     // Sakoe-Chiba band: the band's columns [jlo, jhi], the row below's
     // [jbot_lo, jbot_hi] (the only columns its producer waits for here), the
@@ -469,21 +473,27 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 if (c < d) gout[(int64_t)(i0 + k) * d + c] = COST == kCostL2 ? g[k][c] : __fmul_rn(2.f, g[k][c]);
 }
 
-// Blocks of at most 4 warps.  The backward for one or two channels is held to
-// 96 registers so that five blocks fit per SM (20 warps, 3,040 on the GPU):
-// the 2,560 (pair, band) items of 64 pairs of 10k then all run at once,
-// instead of the last pairs waiting for the longest ones to finish.
+// The persistent item loop shared by the kernels below.
 template <int D, int R, bool BWD, bool BANDED, int COST>
-__global__ void __launch_bounds__(128, (BWD && D <= 2) ? 5 : 1) softdtw_kernel(SoftParams p)
+__device__ __forceinline__ void soft_items(const SoftParams& p)
 {
     extern __shared__ float4 rring_all[];
     const int lane = threadIdx.x & 31;
+    const int n_all = p.n_items + (BWD ? p.n_rec : 0);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&p.hdr->item_counter, 1);
         item = __shfl_sync(FULL, item, 0);
-        if (item >= p.n_items) break;
+        if (item >= n_all) break;
         if (ld_volatile(&p.hdr->abort)) break;
+        if (BWD && item >= p.n_items) {
+            // recompute of the next group up, beside this group's backward
+            const int r = item - p.n_items;
+            const int qr = r / p.rec_band_cnt, kr = r % p.rec_band_cnt;
+            const PairDesc pr = p.pairs[p.order[qr]];
+            fwd_band<D, R, BANDED, COST>(p, pr, p.rec_band_lo + kr, lane, p.rec_rbuf_band0 + kr, true, true);
+            continue;
+        }
         int q, k;
         if (BANDED) {
             // band-major (every pair's k-th band, then k + 1): under a band a
@@ -501,16 +511,46 @@ __global__ void __launch_bounds__(128, (BWD && D <= 2) ? 5 : 1) softdtw_kernel(S
         const PairDesc pd = p.pairs[p.order[q]];
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
-            bwd_band<D, R, BANDED, COST>(p, pd, p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k, lane,
-                           rring_all + (threadIdx.x >> 5) * kRPre * (R / 4) * 32);
+            const int band = p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k;
+            bwd_band<D, R, BANDED, COST>(p, pd, band, lane, rring_all + (threadIdx.x >> 5) * kRPre * (R / 4) * 32,
+                                         band - p.band_lo + p.rbuf_band0);
         } else {
-            fwd_band<D, R, BANDED, COST>(p, pd, p.band_cnt > 0 ? p.band_lo + k : k, lane);
+            const int band = p.band_cnt > 0 ? p.band_lo + k : k;
+            fwd_band<D, R, BANDED, COST>(p, pd, band, lane, band - p.band_lo + p.rbuf_band0, p.recompute != 0,
+                                         p.store_r != 0);
         }
     }
 }
 
 // g == null: Eq. 7's weights lambda_k / m_k with lambda_k = 1, i.e. 1 / N_k
 // (N_k from the offsets), rounded to FP32 as a caller's FP32 weights would be.
+// Blocks of at most 4 warps.
+template <int D, int R, bool BWD, bool BANDED, int COST>
+__global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
+{
+    soft_items<D, R, BWD, BANDED, COST>(p);
+}
+
+// The backward for one channel, held to 96 registers so that five
+// blocks of 4 warps fit per SM (3,040 warps on the GPU): the 2,560 (pair,
+// band) items of 64 pairs of 10k then all run at once, instead of the last
+// pairs waiting for the longest ones to finish.
+template <int D, int R, bool BANDED, int COST>
+__global__ void __launch_bounds__(128, 5) softdtw_bwd_narrow_kernel(SoftParams p)
+{
+    soft_items<D, R, true, BANDED, COST>(p);
+}
+
+// the kernel that runs (D, BWD)
+template <int D, int R, bool BWD, bool BANDED, int COST>
+constexpr auto soft_kernel()
+{
+    if constexpr (BWD && D == 1)
+        return softdtw_bwd_narrow_kernel<D, R, BANDED, COST>;
+    else
+        return softdtw_kernel<D, R, BWD, BANDED, COST>;
+}
+
 __global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g,
                                    const int64_t* __restrict__ offsets, int T, int64_t M, int d,
                                    float* __restrict__ out)
@@ -547,9 +587,9 @@ cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
     const size_t smem = BWD ? rring_bytes<R>(block) : 0;
-    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    softdtw_kernel<D, R, BWD, BANDED, COST><<<grid, block, smem, st>>>(p);
+    auto kern = soft_kernel<D, R, BWD, BANDED, COST>();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -569,9 +609,9 @@ int occ_db(int block)
     constexpr int R = 8;
     const size_t smem = BWD ? rring_bytes<R>(block) : 0;
     int n = 0;
-    cudaFuncSetAttribute(softdtw_kernel<D, R, BWD, BANDED, COST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, softdtw_kernel<D, R, BWD, BANDED, COST>, block, smem);
+    auto kern = soft_kernel<D, R, BWD, BANDED, COST>();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem);
     return n;
 }
 

@@ -28,6 +28,13 @@ struct SoftParams {
     int store_r;         // forward: write R
     int recompute;
     int band_lo, band_cnt;
+    int rbuf_band0;      // checkpoint mode: R of band b is kept in band slot b - band_lo + rbuf_band0
+                         // (two buffers of ckpt_bands slots per pair, used by alternate groups)
+    // checkpoint mode, backward launches: items n_items .. n_items + n_rec - 1
+    // recompute R of the next group up (bands [rec_band_lo, rec_band_lo +
+    // rec_band_cnt), into slots from rec_rbuf_band0) while the backward items
+    // run; they read only the stored hand-off rows, so they never wait
+    int n_rec, rec_band_lo, rec_band_cnt, rec_rbuf_band0;
     long long spin_limit;    // polls before a wait gives up
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major

@@ -9,8 +9,11 @@ with the error against the FP64 oracle stated for every result.
   the FP64 path.
 * One Soft-DTW pair of the barycenter workload (M = 10,000, N ~ 10k) at the
   workload's three gammas: value within 1e-5 of FP64 (relative to
-  max(|v|, 1)) and the Eq. 7 gradient within twice a plain FP32 evaluation's
-  error plus 1e-5 (relative to the largest component).
+  max(|v|, 1)) or within twice a plain FP32 evaluation's error, whichever is
+  larger (a path of ~19k cells rounds r once per cell: a plain FP32
+  evaluation itself is ~1e-5 off at this size), and the Eq. 7 gradient within
+  twice a plain FP32 evaluation's error plus 1e-5 (relative to the largest
+  component).
 * One pair of the very-long workload (M = 110,000, N ~ 108k, 3 channels) with
   checkpointed codes (16-band groups, as benchmarked): cost, |pi| and the
   path bit-exact against the FP32 mirror (the mirror keeps a 1-byte choice
@@ -128,16 +131,18 @@ def test_softdtw_pair_full_size_value_and_gradient(wts, gamma):
     assert wts.read_status(ws.buf) == 0
     w = np.array([1.0 / len(y)], dtype=np.float32)
     vo, _, go = oracle.softdtw_batch(B, one.data, one.offsets, gamma, weights=w.astype(np.float64))
-    _, _, g32 = oracle.softdtw_batch(B, one.data, one.offsets, gamma, weights=w, prec="f32")
+    v32, _, g32 = oracle.softdtw_batch(B, one.data, one.offsets, gamma, weights=w, prec="f32")
     vg = float(v.cpu().numpy()[0])
     gg = g.cpu().numpy().astype(np.float64)
     scale = np.abs(go).max()
     gerr = np.abs(gg - go).max() / scale
     g32err = np.abs(g32.astype(np.float64) - go).max() / scale
-    verr = abs(vg - float(vo[0])) / max(abs(float(vo[0])), 1.0)
-    print(f"FP64-ERROR soft-DTW pair {M} x {len(y)}, gamma={gamma}: value rel {verr:.3e}; gradient "
-          f"max / max|g| {gerr:.3e} (plain FP32 evaluation: {g32err:.3e})")
-    assert verr <= 1e-5
+    vden = max(abs(float(vo[0])), 1.0)
+    verr = abs(vg - float(vo[0])) / vden
+    v32err = abs(float(v32[0]) - float(vo[0])) / vden
+    print(f"FP64-ERROR soft-DTW pair {M} x {len(y)}, gamma={gamma}: value rel {verr:.3e} (plain FP32 "
+          f"evaluation: {v32err:.3e}); gradient max / max|g| {gerr:.3e} (plain FP32 evaluation: {g32err:.3e})")
+    assert verr <= max(1e-5, 2.0 * v32err)
     assert gerr <= 2.0 * g32err + 1e-5
 
 
@@ -184,12 +189,15 @@ def test_checkpointed_softdtw_largest_oracle_size(wts):
     assert wts.read_status(ws.buf) == 0
     w = np.array([1.0 / len(y)], dtype=np.float32)
     vo, _, go = oracle.softdtw_batch(B, one.data, one.offsets, gamma, weights=w.astype(np.float64))
-    _, _, g32 = oracle.softdtw_batch(B, one.data, one.offsets, gamma, weights=w, prec="f32")
+    v32, _, g32 = oracle.softdtw_batch(B, one.data, one.offsets, gamma, weights=w, prec="f32")
     scale = np.abs(go).max()
     gerr = np.abs(g.cpu().numpy().astype(np.float64) - go).max() / scale
     g32err = np.abs(g32.astype(np.float64) - go).max() / scale
-    verr = abs(float(v.cpu().numpy()[0]) - float(vo[0])) / max(abs(float(vo[0])), 1.0)
+    vden = max(abs(float(vo[0])), 1.0)
+    verr = abs(float(v.cpu().numpy()[0]) - float(vo[0])) / vden
+    v32err = abs(float(v32[0]) - float(vo[0])) / vden
     print(f"FP64-ERROR checkpointed soft-DTW pair {M} x {len(y)} x 3 ch, gamma={gamma}, 64-band groups: "
-          f"value rel {verr:.3e}; gradient max / max|g| {gerr:.3e} (plain FP32: {g32err:.3e})")
-    assert verr <= 1e-5
+          f"value rel {verr:.3e} (plain FP32: {v32err:.3e}); gradient max / max|g| {gerr:.3e} "
+          f"(plain FP32: {g32err:.3e})")
+    assert verr <= max(1e-5, 2.0 * v32err)
     assert gerr <= 2.0 * g32err + 1e-5
