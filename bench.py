@@ -303,7 +303,9 @@ def scoring_leg(api, torch, dev, barrier, T: int | None = None, per_pair: bool =
     res = {"workload": "1000 cycles x 3 ch FP32, pre-gap N ~ lognormal(15k, 0.6) clipped 2k-60k, 5% anomalous, "
                        "M=20000 clean prototype",
            "T": b.T, "cells": cells, "options": {"rows_per_thread": opts.rows_per_thread,
-                                                  "warps_per_block": opts.warps_per_block},
+                                                  "warps_per_block": opts.warps_per_block,
+                                                  "form": "codes + walk" if opts.score_via_codes
+                                                  else "count inside the DP"},
            "batched_graph_ms": batched_ms, "batched_gcups": cells / (batched_ms * 1e-3) / 1e9,
            "autotune_best_wavefront_ms": tune_ms}
     # the two detection thresholds of Sec. 5.3 on the scores, against the
@@ -936,15 +938,29 @@ def run_gpu(args):
     del d_data, gb_e2e
 
     if not args.no_extras:
-        # anomaly score on the same batch against the current prototype (|pi| fused)
-        api.anomaly_score(B, gb, ws=ws)
+        # anomaly score on the same batch against the current prototype,
+        # autotuned: |pi| counted inside the DP, or stored codes + the walk
+        sopt, _ = api.autotune(_abi.OP_ANOMALY_SCORE, B, gb, ws)
+        api.anomaly_score(B, gb, sopt, ws=ws)
         barrier()
         s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
         s0.record(st)
-        api.anomaly_score(B, gb, ws=ws)
+        api.anomaly_score(B, gb, sopt, ws=ws)
         s1.record(st)
         barrier()
         out["anomaly_score_gcups"] = cells / (s0.elapsed_time(s1) * 1e-3) / 1e9
+        out["anomaly_score_options"] = {"rows_per_thread": sopt.rows_per_thread,
+                                        "warps_per_block": sopt.warps_per_block,
+                                        "form": "codes + walk" if sopt.score_via_codes else "count inside the DP"}
+        # the counting form on the same batch, for comparison
+        fopt = api.options()
+        api.anomaly_score(B, gb, fopt, ws=ws)
+        barrier()
+        s0.record(st)
+        api.anomaly_score(B, gb, fopt, ws=ws)
+        s1.record(st)
+        barrier()
+        out["anomaly_score_count_in_dp_gcups"] = cells / (s0.elapsed_time(s1) * 1e-3) / 1e9
         out["l2_cost"] = l2_cost_leg(api, torch, dev, st, barrier, gb, B0, cells, ws)
 
     if not args.no_extras:

@@ -111,7 +111,13 @@ typedef struct wts_options {
                                       gradient of the norm is (b_ic - y_jc) / delta, taken as 0 where
                                       delta = 0.  dba_iterate still averages the aligned samples (the mean
                                       minimises the squared cost only, so the DBA cost need not decrease). */
-    int32_t reserved[5];
+    int32_t score_via_codes;       /* anomaly_score: 0 = count |pi| inside the DP (small workspace); 1 = store
+                                      every cell's 2-bit code, walk the paths (dtw_align's segmented walk) and
+                                      take |pi| from the row ranges - the same scores, with the dtw_align
+                                      workspace; faster where the code-writing DP outruns the counting one
+                                      (wts_autotune tries both when the workspace allows).
+                                      anomaly_score_noalloc always counts inside the DP. */
+    int32_t reserved[4];
 } wts_options;
 
 /* Values of wts_options.cost_kind. */

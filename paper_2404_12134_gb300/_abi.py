@@ -54,7 +54,8 @@ class wts_options(ctypes.Structure):
         ("fault_skip_handoff", ctypes.c_int32),
         ("band", ctypes.c_double),
         ("cost_kind", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("score_via_codes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

@@ -58,11 +58,14 @@ class Batch:
 
 
 def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0, dir_mode=0,
-            ckpt_bands=0, spin_limit=0, fault_skip_handoff=0, band=0.0, cost_kind=0) -> wts_options:
+            ckpt_bands=0, spin_limit=0, fault_skip_handoff=0, band=0.0, cost_kind=0,
+            score_via_codes=0) -> wts_options:
     """Launch and method options (see wts_options in include/wetsand.h); band > 0
     is the Sakoe-Chiba width (Table I) for the DTW operations; cost_kind 1 takes
-    the l2 norm as the local cost instead of its square (Sec. 3.2)."""
+    the l2 norm as the local cost instead of its square (Sec. 3.2);
+    score_via_codes 1 makes anomaly_score walk stored codes for |pi|."""
     o = wts_options()
+    o.score_via_codes = score_via_codes
     o.band = float(band)
     o.cost_kind = cost_kind
     o.rows_per_thread = rows_per_thread
@@ -366,12 +369,13 @@ def dba_iterate(B_in: torch.Tensor, batch: Batch, opts=None, ws: Workspace | Non
 
 def autotune(op: int, B: torch.Tensor, batch: Batch, ws: Workspace | None = None):
     """Time the candidate launch options of the wavefront for ``op`` on this
-    batch and return (options, wavefront ms).  The workspace is sized for the
-    largest candidate."""
+    batch and return (options, ms).  The workspace is sized for the largest
+    candidate (for the score: also the form that walks stored codes)."""
     B = _check_B(B, batch.d)
     M = B.shape[0]
-    need = max(workspace_size(op, M, batch, options(rows_per_thread=r))
-               for r in ((8, 16, 32) if batch.d <= 3 else (8, 16)))
+    forms = (0, 1) if op == _abi.OP_ANOMALY_SCORE else (0,)
+    need = max(workspace_size(op, M, batch, options(rows_per_thread=r, score_via_codes=f))
+               for r in ((8, 16, 32) if batch.d <= 3 else (8, 16)) for f in forms)
     buf = _ws(ws, need)
     best = wts_options()
     ms = ctypes.c_float(0)

@@ -128,6 +128,7 @@ int check_opt(const wts_options* opt, int D)
     if (!(opt->band >= 0.0) || opt->band > 1e6) return fail(WTS_EINVAL, "band must be a finite value >= 0");
     if (opt->cost_kind != WTS_COST_SQEUCLID && opt->cost_kind != WTS_COST_L2)
         return fail(WTS_EINVAL, "cost_kind must be 0 (squared l2) or 1 (l2 norm), got %d", opt->cost_kind);
+    if (opt->score_via_codes != 0 && opt->score_via_codes != 1) return fail(WTS_EINVAL, "score_via_codes must be 0 or 1");
     return WTS_OK;
 }
 
@@ -142,6 +143,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     if (op != kOpPairwise && (M < 1 || M > (int64_t)1 << 30)) return fail(WTS_EINVAL, "M=%lld out of range", (long long)M);
     if (op == kOpPairwise && Y->T < 2) return fail(WTS_EINVAL, "pairwise DTW needs T >= 2");
     if (op == kOpPairwise && Y->T > 4096) return fail(WTS_EINVAL, "pairwise DTW limited to T <= 4096");
+    // the score through stored codes: dtw_align's layout (codes, walk state,
+    // ranges, costs) plus |pi| per cycle
+    const bool via_codes = op == kOpScore && opt && opt->score_via_codes;
+    if (via_codes) op = kOpDba;
     *L = Layout{};
     L->op = op;
     L->T = Y->T;
@@ -254,6 +259,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         L->off_ebuf = take(L->ebuf_bytes);
         L->off_pcost = take((size_t)L->T * sizeof(float));
     }
+    if (via_codes) L->off_plen = take((size_t)L->T * sizeof(int32_t));
     L->total = off;
     return WTS_OK;
 }
@@ -633,6 +639,22 @@ int anomaly_score(const float* B, int64_t M, const wts_batch* Y, const wts_optio
     if ((rc = check_ws(L, workspace, workspace_bytes))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
+    if (opt && opt->score_via_codes) {
+        // codes + walk: the same DTW cost, |pi| from the walked ranges, the
+        // same FP32 division
+        float* c = cost ? cost : reinterpret_cast<float*>(ws + L.off_costs);
+        int32_t* pl = plen ? plen : reinterpret_cast<int32_t*>(ws + L.off_plen);
+        if ((rc = align_into(L, ws, B, Y, opt, st, c, pl, reinterpret_cast<int32_t*>(ws + L.off_jlo),
+                             reinterpret_cast<int32_t*>(ws + L.off_jhi))))
+            return rc;
+        cudaError_t e;
+        {
+            Prof pr("score_divide", st);
+            e = launch_score_divide(c, pl, score, L.T, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "score division launch");
+        return ok();
+    }
     if ((rc = prepare(L, ws, B, Y, opt, st))) return rc;
     DPParams p = base_params(L, ws, opt);
     p.cost_out = cost;
@@ -1139,9 +1161,17 @@ int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* wo
     if (rc) return rc;
     if (!B) return fail(WTS_EINVAL, "B is NULL");
     int64_t sumN = Y->offsets_host[Y->T];
+    // for the score: does the workspace hold the codes (the result depends on it)
+    int codes_fit = 0;
+    if (kop == kOpScore) {
+        wts_options o{};
+        o.score_via_codes = 1;
+        Layout Lc;
+        codes_fit = compute_layout(kop, M, Y, &o, &Lc) == WTS_OK && check_ws(Lc, workspace, workspace_bytes) == WTS_OK;
+    }
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int64_t, int, int64_t>, std::pair<wts_options, float>> cache;
-    const auto key = std::make_tuple(kop, Y->d, M, (int)Y->T, sumN);
+    static std::map<std::tuple<int, int, int64_t, int, int64_t, int>, std::pair<wts_options, float>> cache;
+    const auto key = std::make_tuple(kop, Y->d, M, (int)Y->T, sumN, codes_fit);
     {
         std::lock_guard<std::mutex> g(mu);
         auto it = cache.find(key);
@@ -1164,23 +1194,49 @@ int wts_autotune(int op, const float* B, int64_t M, const wts_batch* Y, void* wo
             cands.push_back(o);
         }
     }
+    // the score through stored codes and the walk (when the workspace holds
+    // the codes): the two row counts of the code-writing DP, 4 warps per block
+    if (kop == kOpScore)
+        for (int R : {D <= 2 ? 32 : 16, D <= 2 ? 16 : 32}) {
+            if (R == 32 && D > 3) continue;
+            wts_options o{};
+            o.rows_per_thread = R;
+            o.warps_per_block = 4;
+            o.score_via_codes = 1;
+            cands.push_back(o);
+        }
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
         return fail(WTS_ECUDA, "cudaEventCreate");
     float best_t = 1e30f;
     wts_options best_o{};
     int tried = 0;
+    // one run of a candidate: the DP (after its preparation), or for the score
+    // through codes the whole call (DP, walk, division; in place in the workspace)
+    auto run_once = [&](const wts_options& o, const Layout& L) -> int {
+        char* ws = (char*)workspace;
+        if (kop == kOpScore && o.score_via_codes) {
+            float* c = reinterpret_cast<float*>(ws + L.off_costs);
+            int32_t* pl = reinterpret_cast<int32_t*>(ws + L.off_plen);
+            int r = align_into(L, ws, B, Y, &o, st, c, pl, reinterpret_cast<int32_t*>(ws + L.off_jlo),
+                               reinterpret_cast<int32_t*>(ws + L.off_jhi));
+            if (r) return r;
+            const cudaError_t e = launch_score_divide(c, pl, c, L.T, st);
+            return e == cudaSuccess ? WTS_OK : cuda_fail(e, "score division launch");
+        }
+        int r = prepare(L, ws, B, Y, &o, st);
+        if (r) return r;
+        DPParams p = base_params(L, ws, &o);
+        return launch_dp(mode, L, p, &o, st);
+    };
     for (const wts_options& o : cands) {
         Layout L;
         if (compute_layout(kop, M, Y, &o, &L) != WTS_OK) continue;
         if (check_ws(L, workspace, workspace_bytes) != WTS_OK) continue;
-        char* ws = (char*)workspace;
         float t_min = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {             // first run warms up, best of two
-            if ((rc = prepare(L, ws, B, Y, &o, st))) break;
-            DPParams p = base_params(L, ws, &o);
             cudaEventRecord(a, st);
-            if ((rc = launch_dp(mode, L, p, &o, st))) break;
+            if ((rc = run_once(o, L))) break;
             cudaEventRecord(b, st);
             if (cudaEventSynchronize(b) != cudaSuccess) { rc = fail(WTS_ECUDA, "autotune run failed"); break; }
             float ms = 0.f;
@@ -1346,6 +1402,10 @@ extern "C" int anomaly_score_noalloc(const float* B, int64_t M, const wts_batch*
                                      void* stream, float* score, float* cost, int32_t* plen)
 {
     using namespace wts;
+    // the fixed scratch serves the count inside the DP only
+    wts_options o = opt ? *opt : wts_options{};
+    o.score_via_codes = 0;
+    opt = &o;
     Layout L;
     int rc = compute_layout(kOpScore, M, Y, opt, &L);
     if (rc) return rc;

@@ -351,6 +351,16 @@ __global__ void __launch_bounds__(256) dba_average_kernel(const float* __restric
     }
 }
 
+__global__ void score_divide_kernel(const float* __restrict__ cost, const int32_t* __restrict__ plen,
+                                    float* __restrict__ score, int T)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < T) {
+        const int32_t c = plen[k];
+        score[k] = c > 0 ? __fdiv_rn(cost[k], (float)c) : __int_as_float(0x7fc00000);
+    }
+}
+
 // Linear resampling: p = m (N-1)/(M-1), i = floor(p), x_i + (p - i)(x_{i+1} - x_i),
 // in double with every operation rounded separately, then rounded to float.
 __device__ __forceinline__ float resample_at(const float* x, int64_t N, int d, int c, int64_t m, int64_t M)
@@ -437,6 +447,12 @@ cudaError_t launch_dba_average(const float* data, const int64_t* offsets, int T,
     const int64_t n = M * d;
     const int grid = (int)((n + block - 1) / block);
     dba_average_kernel<<<grid, block, 0, st>>>(data, offsets, T, d, M, jlo, jhi, costs, B_out, counts, cost_before);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_divide(const float* cost, const int32_t* plen, float* score, int T, cudaStream_t st)
+{
+    score_divide_kernel<<<(T + 255) / 256, 256, 0, st>>>(cost, plen, score, T);
     return cudaGetLastError();
 }
 

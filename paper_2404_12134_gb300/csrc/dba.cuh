@@ -56,6 +56,9 @@ cudaError_t launch_dba_average(const float* data, const int64_t* offsets, int T,
                                const int32_t* jlo, const int32_t* jhi, const float* costs,
                                float* B_out, int32_t* counts, double* cost_before, cudaStream_t st);
 
+// score[k] = cost[k] / plen[k] (one FP32 division, Eq. 8); NaN where the walk failed.
+cudaError_t launch_score_divide(const float* cost, const int32_t* plen, float* score, int T, cudaStream_t st);
+
 cudaError_t launch_resample(const float* x, int64_t N, int d, float* out, int64_t M, cudaStream_t st);
 cudaError_t launch_euclid_mean(const float* data, const int64_t* offsets, int T, int d, int64_t M,
                                float* out, cudaStream_t st);

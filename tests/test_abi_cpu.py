@@ -211,3 +211,19 @@ def test_cost_kind_option_layout_and_validation(lib):
     n16b = ctypes.c_size_t(0)
     assert lib.wts_segment_workspace_size(600, 3, ctypes.byref(o16), ctypes.byref(n16b)) == 0
     assert n16.value == n16b.value
+
+
+def test_score_via_codes_workspace(lib):
+    """The score through stored codes needs the code store of dtw_align plus
+    the walk's ranges; the count inside the DP needs neither."""
+    b, offs = _batch([3000, 2500, 777], d=3)
+    o = _abi.wts_options()
+    o.score_via_codes = 1
+    rc, via = _size(lib, _abi.OP_ANOMALY_SCORE, 2600, b, o)
+    rc2, fused = _size(lib, _abi.OP_ANOMALY_SCORE, 2600, b)
+    rc3, align = _size(lib, _abi.OP_DTW_ALIGN, 2600, b)
+    assert rc == rc2 == rc3 == 0
+    assert via > align > fused
+    o.score_via_codes = 2
+    rc, _ = _size(lib, _abi.OP_ANOMALY_SCORE, 2600, b, o)
+    assert rc == _abi.WTS_EINVAL

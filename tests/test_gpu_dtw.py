@@ -316,3 +316,56 @@ def test_segmented_walk_any_guess(wts):
         Bo, cnt_o, cb_o, _ = oracle.dba_iterate(Bc, data, offs, "f32")
         assert (Bn.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all() and float(cb) == cb_o
         Bc = Bo
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_score_via_codes_bit_exact(wts, case):
+    """anomaly_score through stored codes and the walk (score_via_codes = 1)
+    gives the FP32 mirror's cost, |pi| and score, bit for bit, as the count
+    inside the DP does."""
+    _, B, cyc = case
+    data, offs = _pack(cyc)
+    gb = _gb(wts, data, offs)
+    ws = wts.Workspace()
+    score, cost, plen = wts.anomaly_score(torch.from_numpy(B).cuda(), gb, wts.options(score_via_codes=1), ws=ws)
+    assert wts.read_status(ws.buf) == 0
+    s32, c32, L32 = oracle.score(B, data, offs, "f32")
+    assert (cost.cpu().numpy() == c32).all()
+    assert (plen.cpu().numpy() == L32).all()
+    assert (score.cpu().numpy() == s32).all()
+
+
+@pytest.mark.parametrize("rows,dir_mode", [(16, 0), (32, 0), (8, 0), (16, 1)])
+def test_score_via_codes_long_prototype(wts, rows, dir_mode):
+    """Several 2,048-row segments of the walk (M = 5,000) and checkpointed
+    codes: the codes form equals the count inside the DP and the FP32 mirror."""
+    b = synth.config_batch(3, scale=0.25, T=6)
+    B = synth.clean_prototype(b, 5000)
+    gb = _gb(wts, b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    ws = wts.Workspace()
+    ref = wts.anomaly_score(Bt, gb, ws=ws)
+    got = wts.anomaly_score(Bt, gb, wts.options(rows_per_thread=rows, dir_mode=dir_mode, ckpt_bands=3,
+                                                 score_via_codes=1), ws=ws)
+    assert wts.read_status(ws.buf) == 0
+    for x, y in zip(got, ref):
+        assert torch.equal(x, y)
+    s32, c32, L32 = oracle.score(B, b.data, b.offsets, "f32")
+    assert (got[2].cpu().numpy() == L32).all() and (got[1].cpu().numpy() == c32).all()
+
+
+def test_autotune_score_forms(wts):
+    """With a workspace that holds the codes, the score's autotuner also times
+    the codes form; whatever it picks gives the same scores."""
+    from paper_2404_12134_gb300 import _abi
+    b = synth.config_batch(3, scale=0.2, T=12)
+    B = synth.clean_prototype(b, 4000)
+    gb = _gb(wts, b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    ws = wts.Workspace()
+    best, ms = wts.autotune(_abi.OP_ANOMALY_SCORE, Bt, gb, ws)
+    assert ms > 0 and best.score_via_codes in (0, 1)
+    got = wts.anomaly_score(Bt, gb, best, ws=ws)
+    ref = wts.anomaly_score(Bt, gb, ws=ws)
+    for x, y in zip(got, ref):
+        assert torch.equal(x, y)
