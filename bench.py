@@ -342,6 +342,7 @@ def scoring_leg(api, torch, dev, barrier, T: int | None = None, per_pair: bool =
                     "speedup_vs_per_pair_eager": pp_ms / batched_ms})
         del g1, ws1
     del g, ws
+    torch.cuda.empty_cache()
     return res
 
 
@@ -357,18 +358,20 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
     cells = M * int(b.lengths.sum())
     sub = b.subset(np.arange(8))
     gsub = api.Batch.from_numpy(sub.data, sub.offsets, device=dev)
-    idx, _ = api.medoid(api.pairwise_dtw(gsub))
+    idx, _ = api.medoid(api.pairwise_dtw(gsub, ws=api.Workspace(dev)))
     k = int(idx)
     B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M)
     res = {"workload": "32 cycles x 3 ch FP32, pre-gap N ~ U(100k,120k), 2% gaps, M=110000", "cells_per_iter": cells}
     outs = {}
     from paper_2404_12134_gb300 import _abi
-    tuned, _ = api.autotune(_abi.OP_DBA_ITERATE, B0, gb)
+    ws = api.Workspace(dev)
+    tuned, _ = api.autotune(_abi.OP_DBA_ITERATE, B0, gb, ws)
     res["options"] = {"rows_per_thread": tuned.rows_per_thread, "warps_per_block": tuned.warps_per_block}
     for name, mode in (("stored", 0), ("checkpoint", 1)):
         opt = api.options(rows_per_thread=tuned.rows_per_thread, warps_per_block=tuned.warps_per_block,
                           dir_mode=mode, ckpt_bands=16)
-        ws = api.Workspace(dev)
+        if ws is None:
+            ws = api.Workspace(dev)
         B = B0.clone()
         Bn, cnt, cb, _ = api.dba_iterate(B, gb, opt, ws=ws)          # warm-up
         barrier()
@@ -382,8 +385,9 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
         ms = e0.elapsed_time(e1) / iters
         outs[name] = B.clone()
         res[name] = {"s_per_dba_iter": ms * 1e-3, "gcups": cells / (ms * 1e-3) / 1e9,
-                     "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf)}
-        del ws
+                     "workspace_gb": api.workspace_size(_abi.OP_DBA_ITERATE, M, gb, opt) / 1e9,
+                     "device_status": api.read_status(ws.buf)}
+        ws = None
         torch.cuda.empty_cache()
     res["checkpoint_prototype_identical"] = bool(torch.equal(outs["stored"], outs["checkpoint"]))
     # soft-DTW forward + backward, 8 pairs, checkpointed (64 bands of R per group)
@@ -811,7 +815,7 @@ def run_gpu(args):
     # initial prototype (untimed): medoid of a seeded 16-cycle subset, resampled to M
     sub = b.subset(subset)
     gsub = api.Batch.from_numpy(sub.data, sub.offsets, device=dev)
-    C = api.pairwise_dtw(gsub)
+    C = api.pairwise_dtw(gsub, ws=api.Workspace(dev))
     idx, _ = api.medoid(C)
     k = int(idx)
     B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M_PROTO)

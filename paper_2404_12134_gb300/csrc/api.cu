@@ -216,10 +216,14 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             dw += pair_dir_words(G > 0 ? (G < nb ? G : nb) : nb, Np, L->R);
         }
         if (op == kOpSoft) {
-            // checkpoint mode: two buffers of G bands (one group's R is read
-            // while the next group's is recomputed)
+            // checkpoint mode: column checkpoints of every band (no band), or
+            // two buffers of G bands (with a band: one group's R is read while
+            // the next group's is recomputed)
             const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
-            rs += pair_rstore_floats(G > 0 ? (2 * G < nb ? 2 * G : nb) : nb, Np, L->R);
+            if (G > 0 && !(opt->band > 0))
+                rs += nb * band_ckcol_floats(Np, L->R);
+            else
+                rs += pair_rstore_floats(G > 0 ? (2 * G < nb ? 2 * G : nb) : nb, Np, L->R);
         }
     }
     if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
@@ -254,6 +258,7 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     }
     if (op == kOpSoft) {
         if (opt && opt->dir_mode == 1) L->group_bands = opt->ckpt_bands ? opt->ckpt_bands : 16;
+        L->soft_fused = L->group_bands > 0 && !L->banded;
         L->off_rstore = take((size_t)rs * sizeof(float));
         L->off_gpart = take((size_t)L->T * M * D * sizeof(float));
         L->off_ebuf = take(L->ebuf_bytes);
@@ -492,6 +497,10 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     p.gpart = reinterpret_cast<float*>(ws + L.off_gpart);
     p.banded = L.banded;
     p.cost_kind = L.cost_kind;
+    if (L.soft_fused) {                   // the checkpoint area holds column checkpoints
+        p.ckcol = reinterpret_cast<float*>(ws + L.off_rstore);
+        p.fused = 1;
+    }
     return p;
 }
 
@@ -503,7 +512,7 @@ int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, 
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind);
+    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind, L.soft_fused);
     if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;
@@ -1023,7 +1032,9 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward hand-off rows)");
     SoftParams p = soft_params(L, ws, gamma, opt);
     int grid = 0, block = 0;
-    if (L.group_bands == 0) {
+    if (L.group_bands == 0 || L.soft_fused) {
+        // R stored, or (checkpoint mode without a band) recomputed inside
+        // each band's warp from the column checkpoints: one launch
         if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;
         {
             Prof pr("softdtw_bwd", st);

@@ -79,8 +79,10 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
             h = pair_hbuf_slots(nb, N);
             if (sp.op == kOpAlign || sp.op == kOpDba || sp.op == kOpSubdtw)
                 dw = pair_dir_words(sp.group_bands > 0 ? min((int64_t)sp.group_bands, nb) : nb, N, sp.R);
-            if (sp.op == kOpSoft)      // checkpoint mode: two buffers of group_bands bands
-                rs = pair_rstore_floats(sp.group_bands > 0 ? min(2 * (int64_t)sp.group_bands, nb) : nb, N, sp.R);
+            if (sp.op == kOpSoft)      // checkpoint mode: column checkpoints, or (band) two R buffers of groups
+                rs = sp.group_bands <= 0 ? pair_rstore_floats(nb, N, sp.R)
+                     : sp.band > 0       ? pair_rstore_floats(min(2 * (int64_t)sp.group_bands, nb), N, sp.R)
+                                         : nb * band_ckcol_floats(N, sp.R);
         }
         int64_t eh, ed, er;
         int64_t th = block_exclusive_scan(h, &eh);

@@ -40,6 +40,11 @@ __host__ __device__ inline int64_t band_dir_words(int64_t N, int R)
 }
 __host__ __device__ inline int64_t pair_dir_words(int64_t nb, int64_t N, int R) { return nb * band_dir_words(N, R); }
 __host__ __device__ inline int64_t pair_rstore_floats(int64_t nb, int64_t N, int R) { return nb * (N + 31) * 32 * R; }
+// Soft-DTW column checkpoints (checkpoint mode without a band): every kCk
+// forward steps, each lane's R values of its last column and the value above
+// its first row; per band [ceil((N + 31) / kCk)][R + 1][32] floats
+constexpr int kCk = 16;
+__host__ __device__ inline int64_t band_ckcol_floats(int64_t N, int R) { return ((N + 31 + kCk - 1) / kCk) * (R + 1) * 32; }
 
 struct Layout {
     int op = 0;
@@ -56,6 +61,7 @@ struct Layout {
     int banded = 0;       // a Sakoe-Chiba band applies (the banded kernels run with R = 16)
     int cost_kind = 0;    // local cost: 0 squared l2, 1 the l2 norm (DTW kernels with R = 16)
     int nseg = 0;         // segments of the segmented backtrack (codes stored, not Sub-DTW)
+    int soft_fused = 0;   // soft-DTW checkpoint mode without a band: column checkpoints, fused backward
     size_t off_seg = 0;
 
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;

@@ -78,8 +78,6 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Backward steps whose R blocks are in flight at once (shared-memory ring per warp)
 constexpr int kRPre = 8;
-template <int R>
-constexpr size_t rring_bytes(int block) { return (size_t)(block / 32) * kRPre * (R / 4) * 32 * sizeof(float4); }
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -110,6 +108,29 @@ __device__ __forceinline__ float local_cost(const float* bk, const float* y, flo
 
 // One band of the forward pass; rslot: the band's slot in the R store (when
 // store_r), recompute: start from the stored top row and write no hand-off row.
+// One cell of the forward recursion: r = delta + min^gamma(dg, up, lf), the
+// soft minimum taken relative to min(dg, lf) (see the file comment);
+// kk = log2(e) / gamma, gl = gamma ln 2.
+template <int D, int COST>
+__device__ __forceinline__ float soft_cell(const float* bk, const float* y, float dg, float up, float lf, float kk,
+                                           float gl)
+{
+    float t[D];
+    const float delta = local_cost<D, COST>(bk, y, t);
+    // off the serial path (dg, lf known): m2 and S2
+    const float m2 = fminf(dg, lf);
+    const float S2 = __fadd_rn(1.f, ex2a(__fmul_rn(-fabsf(__fsub_rn(dg, lf)), kk)));
+    const float du = __fsub_rn(up, m2);
+    const float z = ex2a(__fmul_rn(-fabsf(du), kk));
+    const float S = du >= 0.f ? __fadd_rn(S2, z) : __fmaf_rn(S2, z, 1.f);
+    return __fmaf_rn(-gl, lg2a(S), __fadd_rn(delta, fminf(m2, up)));
+}
+
+// Column checkpoints (kCk, band_ckcol_floats: plan.cuh): chunk c of a band
+// holds its lanes' state after forward step c kCk - 1 - the R rows of the
+// lane's last column and r of the row above at the column before - so that
+// the backward can recompute any kCk steps of the band on its own.
+
 template <int D, int R, bool BANDED, int COST>
 __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, int rslot,
                                          bool recompute, bool store_r)
@@ -168,8 +189,18 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     load_y(s_begin + lane);
     if (!top && s_begin + lane < N) tnext = __ldcv(hprev + s_begin + lane);
 
+    // column checkpoints of this band (full forward in checkpoint mode)
+    float* ckb = (!BANDED && p.ckcol && !recompute) ? p.ckcol + pd.aux_off + (int64_t)band * band_ckcol_floats(N, R)
+                                                    : nullptr;
+
 #pragma unroll 2
     for (int s = s_begin; s < s_end; ++s) {
+        if (ckb != nullptr && s > 0 && (s % kCk) == 0) {
+            float* ck = ckb + (int64_t)(s / kCk) * (R + 1) * 32 + lane;
+#pragma unroll
+            for (int k = 0; k < R; ++k) ck[k * 32] = col[k];
+            ck[R * 32] = prev_up;
+        }
         if ((s & 31) == 0 && s <= jhi) {
             const int jj = s + lane;
 #pragma unroll
@@ -212,15 +243,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const float lf = col[k];
-                float t[D];
-                const float delta = local_cost<D, COST>(b[k], y, t);
-                // off the serial path (dg, lf known): m2 and S2
-                const float m2 = fminf(dg, lf);
-                const float S2 = __fadd_rn(1.f, ex2a(__fmul_rn(-fabsf(__fsub_rn(dg, lf)), kk)));
-                const float du = __fsub_rn(up, m2);
-                const float z = ex2a(__fmul_rn(-fabsf(du), kk));
-                const float S = du >= 0.f ? __fadd_rn(S2, z) : __fmaf_rn(S2, z, 1.f);
-                float r = __fmaf_rn(-gl, lg2a(S), __fadd_rn(delta, fminf(m2, up)));
+                float r = soft_cell<D, COST>(b[k], y, dg, up, lf, kk, gl);
                 if (MASK && (k < klo || k > khi)) r = INF;      // outside the band
                 dg = lf;
                 up = r;
@@ -257,7 +280,11 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     }
 }
 
-template <int D, int R, bool BANDED, int COST>
+// FUSED (checkpoint mode without a band): R is not stored; every kCk
+// backward steps the warp recomputes the kCk forward steps they read from the
+// band's column checkpoint into `ring` (kCk blocks of R/4 x 32 float4: each
+// lane writes and later reads only its own rows, so no synchronisation).
+template <int D, int R, bool BANDED, int COST, bool FUSED>
 __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring,
                                          int rslot)
 {
@@ -293,7 +320,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // words {r, delta k} and {e, 0}, each NaN until written
     const u64* enext = last ? nullptr : reinterpret_cast<const u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)band * N);
     u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
-    const float* rs = p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R;
+    const float* rs = FUSED ? nullptr : p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R;
 
     // Sakoe-Chiba band: the band's columns [jlo, jhi], the row below's
     // [jbot_lo, jbot_hi] (the only columns its producer waits for here), the
@@ -318,6 +345,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // use (one commit group per step, empty past the end), so that a step's
     // wait covers the copies issued kRPre steps earlier
     auto issue_r = [&](int ss) {
+        if (FUSED) return;
         const int jj = N - 1 - ss + (31 - lane);
         if (ss < steps && jj >= jlo && jj <= jhi) {
             const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - ss) * 32 * R);
@@ -327,8 +355,70 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         }
         cp_async_commit();
     };
+    if (!FUSED)
 #pragma unroll 1
-    for (int ss = s_begin; ss < s_begin + kRPre; ++ss) issue_r(ss);
+        for (int ss = s_begin; ss < s_begin + kRPre; ++ss) issue_r(ss);
+
+    // FUSED: recompute forward steps [f0, f1) of this band into `ring` from
+    // the column checkpoint (the same cell arithmetic and inputs as the full
+    // forward, so R is bit-identical); the band's top row comes from the
+    // forward's hand-off rows, all written before this launch
+    const float* ckb = FUSED ? p.ckcol + pd.aux_off + (int64_t)band * band_ckcol_floats(N, R) : nullptr;
+    const float* hprev = (FUSED && !top) ? p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N : nullptr;
+    auto recompute = [&](int f0, int f1) {
+        const float FINF = 1e30f;                  // the forward's finite sentinel
+        const float gl = p.gamma * kLn2;
+        float fcol[R];
+        float fprev;
+        if (f0 == 0) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) fcol[k] = FINF;
+            fprev = (top && lane == 0) ? 0.f : FINF;
+        } else {
+            const float* ck = ckb + (int64_t)(f0 / kCk) * (R + 1) * 32 + lane;
+#pragma unroll
+            for (int k = 0; k < R; ++k) fcol[k] = __ldg(ck + k * 32);
+            fprev = __ldg(ck + R * 32);
+        }
+        float fy[D], fyb[D];
+        const int jy = f0 - 1 - lane, fb = f0 & ~31;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            fy[c] = (jy >= 0 && jy < N && c < d) ? __ldg(pd.Y + (int64_t)jy * d + c) : 0.f;
+            fyb[c] = (fb + lane < N && c < d) ? __ldg(pd.Y + (int64_t)(fb + lane) * d + c) : 0.f;
+        }
+        const float ftop = (top || fb + lane >= N) ? FINF : __ldcg(hprev + fb + lane);
+        for (int ff = f0; ff < f1; ++ff) {
+            const int src = ff & 31;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const float fresh = __shfl_sync(FULL, fyb[c], src);
+                const float moved = __shfl_up_sync(FULL, fy[c], 1);
+                fy[c] = lane == 0 ? fresh : moved;
+            }
+            const float above = __shfl_up_sync(FULL, fcol[R - 1], 1);
+            const float tv = __shfl_sync(FULL, ftop, src);
+            const float up_in = lane == 0 ? (top ? FINF : tv) : above;
+            const float dg_in = fprev;
+            fprev = up_in;
+            const int jf = ff - lane;
+            if (jf >= 0 && jf < N) {
+                float dg = dg_in, up = up_in;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const float lf = fcol[k];
+                    const float r = soft_cell<D, COST>(b[k], fy, dg, up, lf, kk, gl);
+                    dg = lf;
+                    up = r;
+                    fcol[k] = r;
+                }
+            }
+            float4* dst = ring + (ff - f0) * (R / 4) * 32;
+#pragma unroll
+            for (int k4 = 0; k4 < R / 4; ++k4)
+                dst[k4 * 32 + lane] = make_float4(fcol[4 * k4], fcol[4 * k4 + 1], fcol[4 * k4 + 2], fcol[4 * k4 + 3]);
+        }
+    };
     // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l
     float ynext[D];
     u64 wa = 0, wb = 0;
@@ -345,9 +435,19 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 #pragma unroll 1
     for (int s = s_begin; s < steps; ++s) {
         float4 rcur[R / 4];
-        cp_async_wait<kRPre - 1>();
+        if (FUSED) {
+            // forward step f of this backward step; a new chunk of kCk forward
+            // steps (read backwards) starts at its last step
+            const int f = N + 30 - s;
+            const int fr = f % kCk;
+            if (s == s_begin || fr == kCk - 1) recompute(f - fr, min(f - fr + kCk, N + 31));
 #pragma unroll
-        for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[(s & (kRPre - 1)) * (R / 4) * 32 + k4 * 32 + lane];
+            for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[fr * (R / 4) * 32 + k4 * 32 + lane];
+        } else {
+            cp_async_wait<kRPre - 1>();
+#pragma unroll
+            for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[(s & (kRPre - 1)) * (R / 4) * 32 + k4 * 32 + lane];
+        }
         if ((s & 31) == 0 && s < N) {
             const int jj = N - 1 - s - lane;
 #pragma unroll
@@ -474,7 +574,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 }
 
 // The persistent item loop shared by the kernels below.
-template <int D, int R, bool BWD, bool BANDED, int COST>
+template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED>
 __device__ __forceinline__ void soft_items(const SoftParams& p)
 {
     extern __shared__ float4 rring_all[];
@@ -512,8 +612,9 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
             const int band = p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k;
-            bwd_band<D, R, BANDED, COST>(p, pd, band, lane, rring_all + (threadIdx.x >> 5) * kRPre * (R / 4) * 32,
-                                         band - p.band_lo + p.rbuf_band0);
+            bwd_band<D, R, BANDED, COST, FUSED>(p, pd, band, lane,
+                                                rring_all + (threadIdx.x >> 5) * (FUSED ? kCk : kRPre) * (R / 4) * 32,
+                                                band - p.band_lo + p.rbuf_band0);
         } else {
             const int band = p.band_cnt > 0 ? p.band_lo + k : k;
             fwd_band<D, R, BANDED, COST>(p, pd, band, lane, band - p.band_lo + p.rbuf_band0, p.recompute != 0,
@@ -525,30 +626,38 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
 // g == null: Eq. 7's weights lambda_k / m_k with lambda_k = 1, i.e. 1 / N_k
 // (N_k from the offsets), rounded to FP32 as a caller's FP32 weights would be.
 // Blocks of at most 4 warps.
-template <int D, int R, bool BWD, bool BANDED, int COST>
+template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED>
 __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
 {
-    soft_items<D, R, BWD, BANDED, COST>(p);
+    soft_items<D, R, BWD, BANDED, COST, FUSED>(p);
 }
 
 // The backward for one channel, held to 96 registers so that five
 // blocks of 4 warps fit per SM (3,040 warps on the GPU): the 2,560 (pair,
 // band) items of 64 pairs of 10k then all run at once, instead of the last
 // pairs waiting for the longest ones to finish.
-template <int D, int R, bool BANDED, int COST>
+template <int D, int R, bool BANDED, int COST, bool FUSED>
 __global__ void __launch_bounds__(128, 5) softdtw_bwd_narrow_kernel(SoftParams p)
 {
-    soft_items<D, R, true, BANDED, COST>(p);
+    soft_items<D, R, true, BANDED, COST, FUSED>(p);
 }
 
-// the kernel that runs (D, BWD)
-template <int D, int R, bool BWD, bool BANDED, int COST>
+// the kernel that runs (D, BWD, FUSED)
+template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED>
 constexpr auto soft_kernel()
 {
     if constexpr (BWD && D == 1)
-        return softdtw_bwd_narrow_kernel<D, R, BANDED, COST>;
+        return softdtw_bwd_narrow_kernel<D, R, BANDED, COST, FUSED>;
     else
-        return softdtw_kernel<D, R, BWD, BANDED, COST>;
+        return softdtw_kernel<D, R, BWD, BANDED, COST, FUSED>;
+}
+
+// dynamic shared memory per block: the backward's R ring (or, FUSED, its
+// kCk-step buffer of recomputed R)
+template <int R>
+constexpr size_t soft_smem(bool bwd, bool fused, int block)
+{
+    return bwd ? (size_t)(block / 32) * (fused ? kCk : kRPre) * (R / 4) * 32 * sizeof(float4) : 0;
 }
 
 __global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g,
@@ -582,12 +691,12 @@ __global__ void adam_kernel(float* x, const float* grad, float* m, float* v, int
     x[i] = __fsub_rn(x[i], __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(sqrtf(vh), eps)));
 }
 
-template <int D, bool BWD, bool BANDED, int COST>
+template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
 cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
-    const size_t smem = BWD ? rring_bytes<R>(block) : 0;
-    auto kern = soft_kernel<D, R, BWD, BANDED, COST>();
+    const size_t smem = soft_smem<R>(BWD, FUSED, block);
+    auto kern = soft_kernel<D, R, BWD, BANDED, COST, FUSED>();
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
@@ -596,6 +705,9 @@ cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 template <int D, bool BWD>
 cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
+    if (BWD && p.fused && !p.banded)
+        return p.cost_kind == kCostL2 ? launch_db<D, BWD, false, kCostL2, BWD>(p, grid, block, st)
+                                      : launch_db<D, BWD, false, kCostSqEuclid, BWD>(p, grid, block, st);
     if (p.cost_kind == kCostL2)
         return p.banded ? launch_db<D, BWD, true, kCostL2>(p, grid, block, st)
                         : launch_db<D, BWD, false, kCostL2>(p, grid, block, st);
@@ -603,21 +715,24 @@ cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
                     : launch_db<D, BWD, false, kCostSqEuclid>(p, grid, block, st);
 }
 
-template <int D, bool BWD, bool BANDED, int COST>
+template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
 int occ_db(int block)
 {
     constexpr int R = 8;
-    const size_t smem = BWD ? rring_bytes<R>(block) : 0;
+    const size_t smem = soft_smem<R>(BWD, FUSED, block);
     int n = 0;
-    auto kern = soft_kernel<D, R, BWD, BANDED, COST>();
+    auto kern = soft_kernel<D, R, BWD, BANDED, COST, FUSED>();
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, smem);
     return n;
 }
 
 template <int D, bool BWD>
-int occ_d(int block, int banded, int cost_kind)
+int occ_d(int block, int banded, int cost_kind, int fused)
 {
+    if (BWD && fused && !banded)
+        return cost_kind == kCostL2 ? occ_db<D, BWD, false, kCostL2, BWD>(block)
+                                    : occ_db<D, BWD, false, kCostSqEuclid, BWD>(block);
     if (cost_kind == kCostL2)
         return banded ? occ_db<D, BWD, true, kCostL2>(block) : occ_db<D, BWD, false, kCostL2>(block);
     return banded ? occ_db<D, BWD, true, kCostSqEuclid>(block) : occ_db<D, BWD, false, kCostSqEuclid>(block);
@@ -648,12 +763,12 @@ cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, 
     return cudaErrorInvalidValue;
 }
 
-int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded, int cost_kind)
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded, int cost_kind, int fused)
 {
     if (backward) {
-        WTS_SOFT_DISPATCH(occ_d, true, block, banded, cost_kind)
+        WTS_SOFT_DISPATCH(occ_d, true, block, banded, cost_kind, fused)
     } else {
-        WTS_SOFT_DISPATCH(occ_d, false, block, banded, cost_kind)
+        WTS_SOFT_DISPATCH(occ_d, false, block, banded, cost_kind, fused)
     }
     return 0;
 }

@@ -35,6 +35,11 @@ struct SoftParams {
     // rec_band_cnt), into slots from rec_rbuf_band0) while the backward items
     // run; they read only the stored hand-off rows, so they never wait
     int n_rec, rec_band_lo, rec_band_cnt, rec_rbuf_band0;
+    // checkpoint mode without a band: column checkpoints instead of R groups.
+    // The full forward writes them (ckcol != null), and the backward (fused = 1)
+    // recomputes R a few steps at a time inside each band's warp
+    float* ckcol;
+    int fused;
     long long spin_limit;    // polls before a wait gives up
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
@@ -47,7 +52,7 @@ inline int soft_rows(int /*D*/) { return 8; }
 
 cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
-int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0, int cost_kind = 0);
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0, int cost_kind = 0, int fused = 0);
 
 // grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending); g == null
 // takes g[k] = 1 / N_k (Eq. 7 with lambda_k = 1) from the cycle offsets
