@@ -59,8 +59,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the score / soft-DTW side metrics")
     ap.add_argument("--soft-ckpt", action="store_true",
                     help="soft leg in checkpoint mode (R recomputed in the backward; for profiling)")
-    ap.add_argument("--leg", default="all", choices=["all", "dba", "soft", "score", "long", "bary", "table", "segment"],
-                    help="soft / score: only that leg (soft: with --T cycles of its workload); for profiling")
+    ap.add_argument("--leg", default="all",
+                    choices=["all", "dba", "soft", "score", "long", "bary", "table", "segment", "softckpt"],
+                    help="only that leg (soft: --T cycles of its workload, lengths times --scale; softckpt: the "
+                         "very-long workload's checkpointed soft-DTW on --T pairs, lengths times --scale); "
+                         "for profiling")
+    ap.add_argument("--scale", type=float, default=1.0, help="length scale of the soft / softckpt legs' cycles")
     return ap.parse_args()
 
 
@@ -193,14 +197,14 @@ def hbm_peak_gbs() -> float:
 
 
 def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None, ckpt: bool = False,
-                band: float = 0.0, per_pair: bool = False, peaks: dict | None = None):
+                band: float = 0.0, per_pair: bool = False, peaks: dict | None = None, scale: float = 1.0):
     """Soft-DTW forward + backward on the single-channel barycenter workload:
     64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB), the
     Eq. 7 weights 1 / N_k (the library's default);
     band > 0: with the Sakoe-Chiba band (GCUPS then also over the cells in
     the band); per_pair: also the plain form, one forward + backward call per
     cycle; peaks (measured ex2 / lg2 rates): a roofline for each kernel."""
-    sb = synth.config_batch(2, T=T)
+    sb = synth.config_batch(2, T=T, scale=scale)
     M = synth.PROTO_LEN[2]
     gb = api.Batch.from_numpy(sb.data, sb.offsets, device=dev)
     B = api.euclid_mean(gb, M)
@@ -431,6 +435,38 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
         res["cpu_oracle_subset"] = {"sample": f"{n} cycles cut to their first 2,000 samples against the full "
                                               f"{M}-row prototype, DTW + |pi| (FP64), one cycle per thread",
                                     "s": dt, "gcups": c / dt / 1e9, "threads": n, "cells": c}
+    return res
+
+
+def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma: float = 0.1):
+    """The very-long workload's checkpointed soft-DTW alone: T pairs of its
+    cycles (lengths times scale) against a prototype of 110,000 x scale
+    samples (the clean base; untimed), forward + backward with recomputation,
+    one warm-up then one timed pass."""
+    b = synth.config_batch(4, T=T, scale=scale)
+    M = int(round(synth.PROTO_LEN[4] * scale))
+    gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
+    B0 = torch.from_numpy(synth.clean_prototype(b, M)).to(dev)
+    opt = api.options(dir_mode=1, ckpt_bands=64)
+    ws = api.Workspace(dev)
+    api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
+    api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
+    e1.record()
+    api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
+    e2.record()
+    barrier()
+    cells = M * int(b.lengths.sum())
+    f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    res = {"pairs": b.T, "M": M, "gamma": gamma, "cells": cells, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
+           "fwd_bwd_gcups": cells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": ws.buf.numel() / 1e9,
+           "device_status": api.read_status(ws.buf)}
+    del ws
+    torch.cuda.empty_cache()
     return res
 
 
@@ -800,10 +836,18 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"leg": "segment", "segmentation": res}), flush=True)
         return 0
+    if args.leg == "softckpt":
+        def sync():
+            torch.cuda.synchronize()
+        res = softckpt_leg(api, torch, dev, sync, T=min(args.T, 32), scale=args.scale)
+        if rank == 0:
+            print(json.dumps({"leg": "softckpt", "softdtw_checkpoint": res}), flush=True)
+        return 0
     if args.leg == "soft":
         def sync():
             torch.cuda.synchronize()
-        res = softdtw_leg(api, torch, dev, torch.cuda.current_stream(), sync, T=min(args.T, 64), ckpt=args.soft_ckpt)
+        res = softdtw_leg(api, torch, dev, torch.cuda.current_stream(), sync, T=min(args.T, 64), ckpt=args.soft_ckpt,
+                          scale=args.scale)
         if rank == 0:
             print(json.dumps({"leg": "soft", "softdtw": res}), flush=True)
         return 0

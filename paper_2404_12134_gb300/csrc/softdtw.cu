@@ -160,7 +160,11 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 
     const float* hprev = top ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N;
     float* hcur = (last || recompute || p.skip_handoff) ? nullptr : p.hbuf + pd.hbuf_off + (int64_t)band * N;
-    float* rs = store_r ? p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R : nullptr;
+    // what the band keeps: every step's R (store_r), or every kCk steps its
+    // lanes' state (the full forward in checkpoint mode without a band)
+    const bool ck_mode = !BANDED && !store_r && p.ckcol != nullptr && !recompute;
+    float* rs = store_r   ? p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R
+                : ck_mode ? p.ckcol + pd.aux_off + (int64_t)band * band_ckcol_floats(N, R) : nullptr;
 
     // Sakoe-Chiba band (as in the hard-min wavefront): the band's columns
     // [jlo, jhi], the row above's [jtop_lo, jtop_hi] (the only columns its
@@ -189,14 +193,10 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     load_y(s_begin + lane);
     if (!top && s_begin + lane < N) tnext = __ldcv(hprev + s_begin + lane);
 
-    // column checkpoints of this band (full forward in checkpoint mode)
-    float* ckb = (!BANDED && p.ckcol && !recompute) ? p.ckcol + pd.aux_off + (int64_t)band * band_ckcol_floats(N, R)
-                                                    : nullptr;
-
 #pragma unroll 2
     for (int s = s_begin; s < s_end; ++s) {
-        if (ckb != nullptr && s > 0 && (s % kCk) == 0) {
-            float* ck = ckb + (int64_t)(s / kCk) * (R + 1) * 32 + lane;
+        if (ck_mode && s > 0 && (s % kCk) == 0) {
+            float* ck = rs + (int64_t)(s / kCk) * (R + 1) * 32 + lane;
 #pragma unroll
             for (int k = 0; k < R; ++k) ck[k * 32] = col[k];
             ck[R * 32] = prev_up;
@@ -259,7 +259,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
             // stored as -inf: a slot is NaN only while it is unwritten
             if (hcur != nullptr && lane == 31) __stcg(hcur + j, fmaxf(col[R - 1], -inf_f()));
         }
-        if (rs != nullptr) {
+        if (store_r) {
             float4* dst = reinterpret_cast<float4*>(rs + (int64_t)s * 32 * R);
 #pragma unroll
             for (int k4 = 0; k4 < R / 4; ++k4)
@@ -535,8 +535,8 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 #pragma unroll
                             for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(e, t[c], g[k][c]);
                         } else {
-                            // d delta / d b = t / delta (0 where delta = 0)
-                            const float w = delta > 0.f ? __fdividef(e, delta) : 0.f;
+                            // d delta / d b = t / delta (0 where delta = 0), an IEEE division
+                            const float w = delta > 0.f ? __fdiv_rn(e, delta) : 0.f;
 #pragma unroll
                             for (int c = 0; c < D; ++c) g[k][c] = __fmaf_rn(w, t[c], g[k][c]);
                         }
