@@ -964,7 +964,7 @@ def run_gpu(args):
     d_data = torch.empty_like(gb.data)
     gb_e2e = api.Batch(d_data, gb.offsets, gb.offsets_host)
     d_B = torch.empty_like(B)
-    n_e2e = max(2, min(args.steps, 3))
+    n_e2e = max(2, min(args.steps, 10))
 
     def e2e_step():
         d_data.copy_(h_data, non_blocking=True)

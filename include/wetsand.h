@@ -89,8 +89,9 @@ typedef struct wts_options {
                                       recompute the codes of ckpt_bands bands at a time during the backtrack
                                       (one extra forward pass, bit-identical paths) */
     int32_t ckpt_bands;            /* bands (of 32*rows_per_thread prototype rows) recomputed per group; 0 = 16.
-                                      Soft-DTW keeps two groups' R (the backward of one group runs beside the
-                                      recompute of the next), DTW one group's codes */
+                                      DTW keeps one group's codes; soft-DTW with a band keeps two groups' R (the
+                                      backward of one group runs beside the recompute of the next); soft-DTW
+                                      without a band uses column checkpoints instead and ignores it */
     int32_t spin_limit;            /* polls before an in-kernel wait gives up (each ~0.1-1 us); 0 = 2^27 */
     int32_t fault_skip_handoff;    /* fault injection for tests: 1 = producers skip their hand-off rows, so
                                       consumers wait until spin_limit and the call ends with WTS_ETIMEOUT in
@@ -347,11 +348,15 @@ int dba_iterate(const float* B_in, float* B_out, int64_t M, const wts_batch* Y, 
  *     m - gamma ln(sum_i exp(-(a_i - m)/gamma)),  m = min_i a_i,
  * with the hardware ex2 / lg2 approximations (flush-to-zero), in FP32.  Every r(i,j) is kept
  * in the workspace for softdtw_backward (4 bytes per cell plus a skew
- * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)); with opt->dir_mode = 1
- * only the band hand-off rows are kept and softdtw_backward recomputes R for
- * ckpt_bands bands at a time (one extra forward pass; the recompute of the
- * next group overlaps the backward of the current one, so R of two groups is
- * kept).
+ * margin: wts_workspace_size(WTS_OP_SOFTDTW, ...)).  With opt->dir_mode = 1
+ * R is not kept: without a band, every band keeps its lanes' state every 16
+ * steps (column checkpoints, about R/14 of R's size) besides the band hand-off
+ * rows, and softdtw_backward recomputes R 16 steps at a time inside each
+ * band's warp (one extra forward pass, all bands in flight at once); with a
+ * band, only the hand-off rows are kept and R is recomputed for ckpt_bands
+ * bands at a time (the recompute of the next group overlaps the backward of
+ * the current one, so R of two groups is kept).  Values and gradients are
+ * bit-identical to the stored mode.
  *   B [M][d] (d <= 8), gamma > 0 (gamma = 0 is DTW: use anomaly_score),
  *   value [T] out.
  */
