@@ -183,14 +183,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     const int s_begin = BANDED ? max(0, (jlo - 1) & ~31) : 0;
     const int s_end = BANDED ? jhi + 32 : N + 31;
 
-    // Cycle samples: lane l holds column s0 + l of the current 32-column block
-    // (s0 = s rounded down to 32), loaded one block ahead.  The band above's
-    // bottom row (NaN until written): lane l holds column s0 + l as well, but
-    // the lanes of each quarter (8 lanes) check their value only at step
-    // s0 + 8q, having loaded it 4 steps before; lane l's value is read at step
-    // s0 + l.  So this band needs the band above only 39 + a few steps ahead
-    // (its lane 31 writes column j at step j + 31), where checking a whole
-    // block at once, prefetched a block earlier, held the bands ~94 steps apart.
+    // lane-0 feeds one chunk of 32 columns ahead (the top row is NaN until written)
     float ynext[D];
     float tnext = INF;
     auto load_y = [&](int jj) {
@@ -209,25 +202,19 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
             ck[R * 32] = prev_up;
         }
         if ((s & 31) == 0 && s <= jhi) {
+            const int jj = s + lane;
 #pragma unroll
             for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
-            load_y(s + lane + 32);
-        }
-        if (!top && (s & 7) == 0 && (s & ~31) <= jhi) {
-            // the quarter due now: its lanes' values must be written
-            const int jj = (s & ~31) + lane;
-            const bool mine = (lane >> 3) == ((s & 31) >> 3);
-            const bool need = mine && jj >= jtop_lo && jj <= jtop_hi;
-            float t = tnext;
-            const bool ok = wait_filled(need && isnan(t), [&]() { t = __ldcv(hprev + jj); return isnan(t); },
-                                        p.hdr, 3, p.spin_limit);
-            if (!ok) return;
-            if (mine) topv = need ? t : INF;
-        }
-        if (!top && (s & 7) == 4 && ((s + 4) & ~31) <= jhi && (lane >> 3) == (((s + 4) & 31) >> 3)) {
-            // the quarter due at s + 4 loads its values
-            const int jj = ((s + 4) & ~31) + lane;
-            tnext = jj < N ? __ldcv(hprev + jj) : INF;
+            if (!top) {
+                const bool need = jj >= jtop_lo && jj <= jtop_hi;
+                float t = tnext;
+                const bool ok = wait_filled(need && isnan(t), [&]() { t = __ldcv(hprev + jj); return isnan(t); },
+                                            p.hdr, 3, p.spin_limit);
+                if (!ok) return;
+                topv = need ? t : INF;
+                tnext = jj + 32 < N ? __ldcv(hprev + jj + 32) : INF;
+            }
+            load_y(jj + 32);
         }
         const int src = s & 31;
 #pragma unroll
@@ -432,11 +419,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 dst[k4 * 32 + lane] = make_float4(fcol[4 * k4], fcol[4 * k4 + 1], fcol[4 * k4 + 2], fcol[4 * k4 + 3]);
         }
     };
-    // lane l holds column N-1-s0-l of the current 32-step block (s0 = s
-    // rounded down to 32): cycle samples loaded a block ahead; the row below's
-    // {r, delta k, e} checked per quarter of 8 lanes at step s0 + 8q, loaded
-    // 4 steps before (as in the forward: the band below needs to be only ~40
-    // steps ahead)
+    // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l
     float ynext[D];
     u64 wa = 0, wb = 0;
     auto load_y = [&](int jj) {
@@ -466,24 +449,19 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
             for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[(s & (kRPre - 1)) * (R / 4) * 32 + k4 * 32 + lane];
         }
         if ((s & 31) == 0 && s < N) {
+            const int jj = N - 1 - s - lane;
 #pragma unroll
             for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
-            load_y(N - 1 - s - lane - 32);
-        }
-        if (!last && (s & 7) == 0 && (s & ~31) < N) {
-            // the quarter due now; only the row below's columns inside the band
-            // are written (and waited for)
-            const int jj = N - 1 - (s & ~31) - lane;
-            const bool mine = (lane >> 3) == ((s & 31) >> 3);
-            const bool need = mine && jj >= jbot_lo && jj <= jbot_hi;
-            const bool ok = wait_filled(need && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
-                                        [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
-                                        p.hdr, 4, p.spin_limit);
-            if (!ok) {
-                cp_async_wait<0>();
-                return;
-            }
-            if (mine) {
+            if (!last) {
+                // only the row below's columns inside the band are written (and waited for)
+                const bool need = jj >= jbot_lo && jj <= jbot_hi;
+                const bool ok = wait_filled(need && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
+                                            [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
+                                            p.hdr, 4, p.spin_limit);
+                if (!ok) {
+                    cp_async_wait<0>();
+                    return;
+                }
                 if (need) {
                     cr = __uint_as_float((uint32_t)wa);
                     cd = __uint_as_float((uint32_t)(wa >> 32));
@@ -491,10 +469,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 } else {
                     cr = NINF; cd = 0.f; ce = 0.f;
                 }
+                load_e(jj - 32);
             }
+            load_y(jj - 32);
         }
-        if (!last && (s & 7) == 4 && ((s + 4) & ~31) < N && (lane >> 3) == (((s + 4) & 31) >> 3))
-            load_e(N - 1 - ((s + 4) & ~31) - lane);     // the quarter due at s + 4 loads its values
         const int src = s & 31;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -654,7 +632,7 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
     soft_items<D, R, BWD, BANDED, COST, FUSED>(p);
 }
 
-// The backward for one channel, held to 96 registers so that five
+// The backward for one channel without a band, held to 96 registers so that five
 // blocks of 4 warps fit per SM (3,040 warps on the GPU): the 2,560 (pair,
 // band) items of 64 pairs of 10k then all run at once, instead of the last
 // pairs waiting for the longest ones to finish.
@@ -668,7 +646,7 @@ __global__ void __launch_bounds__(128, 5) softdtw_bwd_narrow_kernel(SoftParams p
 template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED>
 constexpr auto soft_kernel()
 {
-    if constexpr (BWD && D == 1)
+    if constexpr (BWD && D == 1 && !BANDED)
         return softdtw_bwd_narrow_kernel<D, R, BANDED, COST, FUSED>;
     else
         return softdtw_kernel<D, R, BWD, BANDED, COST, FUSED>;

@@ -95,6 +95,8 @@ def test_segment_full_size(wts):
     segs = wts.segment(Xt, Yt, int(0.15 * M))
     assert segs[0][:2] == (r["a"], r["b"]) and segs[0][2] == float(r["cost"])
     pieces_match_cycles(segs, bounds, len(bounds) - 1)
+    # the library's default alpha is Sec. 3.2's 0.15 M (rounded down)
+    assert wts.segment(Xt, Yt) == segs
 
 
 def test_subdtw_rejects_unsupported_options(wts):
