@@ -48,6 +48,31 @@ WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1582 + 5.6421) * 1e9 / 2.2029e10
 # hand-off rows, in proportion to cells; the skew margin, 2.5 % of a band at
 # that length, is 0.3 % at full length).
 SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0150 + 3.2692 + 3.3059 + 0.0593) * 1e9 / 7.9029e8
+# Warp instructions per cell of the checkpointed soft-DTW passes (column
+# checkpoints, recompute fused into the backward), from one ncu capture
+# (smsp__inst_executed.sum) of the same build on the very-long workload's
+# 8 pairs cut to a quarter (5.842e9 cells): forward 5.0907e9, backward
+# 1.2110e10.  Both passes are bound by the issue rate (one warp instruction
+# per scheduler per cycle), not by a pipe or by DRAM.
+SOFT_CKPT_FWD_INSTR_PER_CELL = 5.0907e9 / 5.842045e9
+SOFT_CKPT_BWD_INSTR_PER_CELL = 1.2110e10 / 5.842045e9
+
+
+def softckpt_roofline(cells: int, fwd_ms: float, bwd_ms: float, sms: int, ex2: float | None, lg2: float | None):
+    """Issue-rate roofline of the checkpointed soft-DTW passes (and their MUFU
+    fraction when the measured ex2 / lg2 rates are given)."""
+    peak = sms * 4 * 2.070e9                         # warp instructions per second
+    out = {}
+    for name, ms, ipc, mufu in (("fwd", fwd_ms, SOFT_CKPT_FWD_INSTR_PER_CELL, (2, 1)),
+                                ("bwd", bwd_ms, SOFT_CKPT_BWD_INSTR_PER_CELL, (5, 1))):
+        t = ms * 1e-3
+        r = {"bound": "issue", "achieved": cells * ipc / t, "peak": peak, "unit": "warp-instructions/s",
+             "frac": cells * ipc / t / peak, "instructions_per_cell": ipc,
+             "peak_note": f"{sms} SMs x 4 schedulers x 2070 MHz; instructions per cell from one ncu capture"}
+        if ex2 and lg2:
+            r["mufu_frac"] = cells * (mufu[0] / ex2 + mufu[1] / lg2) / t
+        out[name] = r
+    return out
 
 
 def parse():
@@ -352,7 +377,8 @@ def scoring_leg(api, torch, dev, barrier, T: int | None = None, per_pair: bool =
     return res
 
 
-def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
+def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, ex2: float | None = None,
+             lg2: float | None = None):
     """Very long cycles: 32 cycles x 3 ch, pre-gap N ~ U(100k, 120k), M =
     110,000 (medoid of a seeded 8-cycle subset, resampled; untimed).  DBA with
     every code stored (~95 GB) against checkpoint mode (band rows kept, codes
@@ -398,7 +424,7 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
     res["checkpoint_prototype_identical"] = bool(torch.equal(outs["stored"], outs["checkpoint"]))
     # soft-DTW forward + backward, 8 pairs, checkpointed (64 bands of R per group)
     gamma = 0.1
-    opt = api.options(dir_mode=1, ckpt_bands=64)
+    opt = api.options(dir_mode=1)
     ws = api.Workspace(dev)
     w = None                                   # Eq. 7's 1 / N_k (the library's default)
     api.softdtw_forward(B0, gsub, gamma, opt, ws=ws)
@@ -413,9 +439,12 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True):
     barrier()
     scells = M * int(sub.lengths.sum())
     f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    res["softdtw_checkpoint"] = {"pairs": 8, "gamma": gamma, "ckpt_bands": 64, "cells": scells, "fwd_ms": f_ms,
-                                 "bwd_incl_recompute_ms": b_ms, "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
-                                 "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf)}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    res["softdtw_checkpoint"] = {"pairs": 8, "gamma": gamma, "checkpoints": "every 16 steps per band", "cells": scells,
+                                 "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
+                                 "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
+                                 "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf),
+                                 "roofline": softckpt_roofline(scells, f_ms, b_ms, sms, ex2, lg2)}
     del ws
     torch.cuda.empty_cache()
     if cpu_sample:
@@ -449,7 +478,7 @@ def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma
     M = int(round(synth.PROTO_LEN[4] * scale))
     gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
     B0 = torch.from_numpy(synth.clean_prototype(b, M)).to(dev)
-    opt = api.options(dir_mode=1, ckpt_bands=64)
+    opt = api.options(dir_mode=1)
     ws = api.Workspace(dev)
     api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
     api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
@@ -466,7 +495,9 @@ def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma
     f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
     res = {"pairs": b.T, "M": M, "gamma": gamma, "cells": cells, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
            "fwd_bwd_gcups": cells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": ws.buf.numel() / 1e9,
-           "device_status": api.read_status(ws.buf)}
+           "device_status": api.read_status(ws.buf),
+           "roofline": softckpt_roofline(cells, f_ms, b_ms, torch.cuda.get_device_properties(dev).multi_processor_count,
+                                         None, None)}
     del ws
     torch.cuda.empty_cache()
     return res
@@ -1050,7 +1081,7 @@ def run_gpu(args):
         out["small_dba"] = small_dba_leg(api, torch, dev, barrier, cpu_sample=rank == 0)
         del ws
         torch.cuda.empty_cache()
-        out["long"] = long_leg(api, torch, dev, barrier, cpu_sample=rank == 0)
+        out["long"] = long_leg(api, torch, dev, barrier, cpu_sample=rank == 0, ex2=ex2, lg2=lg2)
         sd = out["softdtw"]
         cells_s = sd["cells"]
         t_mufu = cells_s * (2 / ex2 + 1 / lg2) + cells_s * 3 / ex2          # fwd: 2 ex2 + 1 lg2, bwd: 3 ex2
