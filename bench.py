@@ -224,7 +224,8 @@ def hbm_peak_gbs() -> float:
 
 
 def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None = None, ckpt: bool = False,
-                band: float = 0.0, per_pair: bool = False, peaks: dict | None = None, scale: float = 1.0):
+                band: float = 0.0, per_pair: bool = False, peaks: dict | None = None, scale: float = 1.0,
+                wpb: int = 0):
     """Soft-DTW forward + backward on the single-channel barycenter workload:
     64 cycles, pre-gap N ~ U(8k, 12k), M = 10,000 (R stored: ~26 GB), the
     Eq. 7 weights 1 / N_k (the library's default);
@@ -238,7 +239,8 @@ def softdtw_leg(api, torch, dev, st, barrier, gamma: float = 1.0, T: int | None 
     w = None
     ws = api.Workspace(dev)
     grad = torch.empty_like(B)
-    opt = api.options(dir_mode=1, ckpt_bands=1 << 20, band=band) if ckpt else (api.options(band=band) if band else None)
+    opt = api.options(dir_mode=1, ckpt_bands=1 << 20, band=band, warps_per_block=wpb) if ckpt else \
+        api.options(band=band, warps_per_block=wpb)
     for _ in range(2):
         api.softdtw_forward(B, gb, gamma, opt, ws=ws)
         api.softdtw_backward(B, gb, gamma, w, opt, ws=ws, grad_B=grad)
@@ -469,7 +471,7 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     return res
 
 
-def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma: float = 0.1):
+def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma: float = 0.1, wpb: int = 0):
     """The very-long workload's checkpointed soft-DTW alone: T pairs of its
     cycles (lengths times scale) against a prototype of 110,000 x scale
     samples (the clean base; untimed), forward + backward with recomputation,
@@ -478,7 +480,7 @@ def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma
     M = int(round(synth.PROTO_LEN[4] * scale))
     gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
     B0 = torch.from_numpy(synth.clean_prototype(b, M)).to(dev)
-    opt = api.options(dir_mode=1)
+    opt = api.options(dir_mode=1, warps_per_block=wpb)
     ws = api.Workspace(dev)
     api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
     api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
