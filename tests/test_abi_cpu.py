@@ -227,3 +227,20 @@ def test_score_via_codes_workspace(lib):
     o.score_via_codes = 2
     rc, _ = _size(lib, _abi.OP_ANOMALY_SCORE, 2600, b, o)
     assert rc == _abi.WTS_EINVAL
+
+
+def test_softdtw_checkpoint_workspace(lib):
+    """Soft-DTW checkpoint mode without a band keeps column checkpoints (R/14
+    of the stored R's size), with a band two groups of R."""
+    b, offs = _batch([9000, 11000], d=1)
+    rc, stored = _size(lib, _abi.OP_SOFTDTW, 10000, b)
+    o = _abi.wts_options()
+    o.dir_mode = 1
+    rc2, ck = _size(lib, _abi.OP_SOFTDTW, 10000, b, o)
+    o.band = 0.6
+    o.ckpt_bands = 4
+    rc3, banded = _size(lib, _abi.OP_SOFTDTW, 10000, b, o)
+    assert rc == rc2 == rc3 == 0
+    cells = 10000 * 20000
+    assert stored >= 4 * cells and ck < stored / 10 and ck > 4 * cells * 9 / (8 * 16) * 0.9
+    assert banded < stored / 4

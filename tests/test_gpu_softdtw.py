@@ -263,3 +263,51 @@ def test_banded_lbfgs_barycenter(wts):
     _, fg, _ = oracle.softdtw_batch(Bg.cpu().numpy(), b.data, b.offsets, 1.0, weights=w, prec="f64", band=0.6)
     Bo, fo, ito, evo, whyo = oracle.softdtw_barycenter_lbfgs(b.data, b.offsets, B0.cpu().numpy(), 1.0, band=0.6)
     assert abs(fg - fo) <= 1e-3 * abs(fo), (fg, fo)
+
+
+def test_adam_barycenter_checkpoint_mode_identical(wts):
+    """The library's Adam loop with R recomputed from column checkpoints
+    (dir_mode = 1) reaches the same barycenter, bit for bit, as with R stored."""
+    b = synth.config_batch(2, scale=0.06, T=5)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M = 700
+    B0 = wts.euclid_mean(gb, M)
+    Bs, hs = wts.softdtw_barycenter(gb, M, 0.1, steps=5, lr=2e-2, init=B0)
+    Bc, hc = wts.softdtw_barycenter(gb, M, 0.1, steps=5, lr=2e-2, init=B0, opts=wts.options(dir_mode=1))
+    assert torch.equal(Bs, Bc) and torch.equal(hs, hc)
+
+
+def test_lbfgs_barycenter_reports_nonfinite_sample(wts):
+    """A NaN sample stops the L-BFGS driver at its first evaluation with
+    WTS_EINVAL (the device-side input scan), not with a wrong objective."""
+    from paper_2404_12134_gb300._abi import WTS_EINVAL, WtsError
+    b = synth.config_batch(2, scale=0.03, T=4)
+    data = b.data.copy()
+    data[17, 0] = np.nan
+    gb = wts.Batch.from_numpy(data, b.offsets)
+    with pytest.raises(WtsError) as ei:
+        wts.softdtw_barycenter_lbfgs(gb, 200, 0.1, init=torch.zeros((200, 1), device="cuda"))
+    assert ei.value.code == WTS_EINVAL
+
+
+def test_lbfgs_first_step_matches_oracle(wts):
+    """One L-BFGS iteration (max_iter = 1) from the same start: the step the
+    library takes (GPU objective and gradient in FP32, the driver in double on
+    the host) equals the oracle's (FP64) within the gradient's bar: twice a
+    plain FP32 evaluation's error plus 1e-5, relative to the step's size (a
+    first iteration is steepest descent, x1 = x0 - t g, with the same
+    backtracking on both sides)."""
+    b = synth.config_batch(2, scale=0.008, T=5)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M, gamma = 60, 1.0
+    B0 = wts.euclid_mean(gb, M)
+    B0h = B0.cpu().numpy()
+    Bg, f, it, ev, why = wts.softdtw_barycenter_lbfgs(gb, M, gamma, init=B0, params=wts.lbfgs_params(max_iter=1))
+    Bo, fo, ito, evo, whyo = oracle.softdtw_barycenter_lbfgs(b.data, b.offsets, B0h, gamma, max_iter=1)
+    assert it == ito == 1 and ev == evo
+    w = (1.0 / b.lengths).astype(np.float32)
+    _, _, go = oracle.softdtw_batch(B0h, b.data, b.offsets, gamma, weights=w.astype(np.float64))
+    bar = _grad_bar(B0h, b, gamma, w.astype(np.float64), go)
+    dg = Bg.cpu().numpy().astype(np.float64) - B0h
+    do = np.asarray(Bo, dtype=np.float64).reshape(B0h.shape) - B0h
+    assert np.abs(dg - do).max() <= 2.0 * bar * np.abs(do).max() + 1e-7, (np.abs(dg - do).max(), np.abs(do).max())
