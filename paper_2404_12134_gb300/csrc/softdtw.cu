@@ -182,6 +182,9 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
     // the row above one column before the band starts)
     const int s_begin = BANDED ? max(0, (jlo - 1) & ~31) : 0;
     const int s_end = BANDED ? jhi + 32 : N + 31;
+    // the lane's rows inside the band at its column s - lane, kept step by step
+    BandRows brow{};
+    if (BANDED) brow.init(s_begin - lane, bnd, M, N);
 
     // lane-0 feeds one chunk of 32 columns ahead (the top row is NaN until written)
     float ynext[D];
@@ -233,12 +236,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
         // the lane's column; MASK: only rows k in [klo, khi] lie in the band
         auto column = [&](auto mask) {
             constexpr bool MASK = decltype(mask)::value;
-            int klo = 0, khi = R - 1;
-            if (MASK) {
-                const int64_t jm = (int64_t)j * M;
-                klo = (int)max((int64_t)-1, ceil_div64(jm - bnd, N) - i0);
-                khi = (int)min((int64_t)R, floor_div64(jm + bnd, N) - i0);
-            }
+            const int klo = MASK ? brow.qa - i0 : 0, khi = MASK ? brow.qb - i0 : R - 1;
             float dg = dg_in, up = up_in;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -265,6 +263,7 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
             for (int k4 = 0; k4 < R / 4; ++k4)
                 dst[k4 * 32 + lane] = make_float4(col[4 * k4], col[4 * k4 + 1], col[4 * k4 + 2], col[4 * k4 + 3]);
         }
+        if (BANDED) brow.next(N);
     }
 
     if (last && !recompute) {
@@ -339,6 +338,9 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     }
     const int s_begin = BANDED ? max(0, (N - 2 - jhi) & ~31) : 0;
     const int steps = BANDED ? N + 31 - jlo : N + 31;
+    // the lane's rows inside the band at its column N-1-s+(31-lane)
+    BandRows brow{};
+    if (BANDED) brow.init(N - 1 - s_begin + (31 - lane), bnd, M, N);
 
     // R of this lane's rows at the column of step ss (written by forward step
     // N+30-ss) is copied into ring slot ss mod kRPre kRPre steps ahead of its
@@ -501,12 +503,8 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         auto column = [&](auto checked) {
             constexpr bool CHECKED = decltype(checked)::value;
             // checked with a band: only rows k in [klo, khi] lie in the band
-            int klo = 0, khi = R - 1;
-            if (CHECKED && BANDED) {
-                const int64_t jm = (int64_t)j * M;
-                klo = (int)max((int64_t)-1, ceil_div64(jm - bnd, N) - i0);
-                khi = (int)min((int64_t)R, floor_div64(jm + bnd, N) - i0);
-            }
+            const int klo = CHECKED && BANDED ? brow.qa - i0 : 0;
+            const int khi = CHECKED && BANDED ? brow.qb - i0 : R - 1;
             float nr = br, nd = bd, ne = be;       // below, column j
 #pragma unroll
             for (int k4 = R / 4 - 1; k4 >= 0; --k4) {
@@ -561,6 +559,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         }
         // the slot just read (its values are consumed) takes step s + kRPre
         issue_r(s + kRPre);
+        if (BANDED) brow.prev(N);
     }
     cp_async_wait<0>();
 

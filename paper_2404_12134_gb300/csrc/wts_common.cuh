@@ -109,6 +109,43 @@ __device__ __forceinline__ int band_hi(int64_t i, int64_t bnd, int M, int N)
     return (int)min((int64_t)N - 1, floor_div64(i * N + bnd, M));
 }
 
+// The rows inside the band at a column j that moves by one a step, without a
+// division per step: row i is in the band at column j iff
+// ceil((jM - bnd) / N) <= i <= floor((jM + bnd) / N).  qa and qb are those two
+// quotients, ra = qa N - (jM - bnd) and rb = (jM + bnd) - qb N their
+// remainders in [0, N); dq, dr = M / N, M % N.  |bnd| <= MN keeps every field
+// within 32 bits.
+struct BandRows {
+    int qa, ra, qb, rb, dq, dr;
+    __device__ __forceinline__ void init(int64_t j, int64_t bnd, int M, int N)
+    {
+        const int64_t A = j * M - bnd, B = j * M + bnd;
+        const int64_t a = ceil_div64(A, N), b = floor_div64(B, N);
+        qa = (int)a;
+        ra = (int)(a * N - A);
+        qb = (int)b;
+        rb = (int)(B - b * N);
+        dq = M / N;
+        dr = M % N;
+    }
+    __device__ __forceinline__ void next(int N)      // j + 1
+    {
+        const bool ca = dr > ra, cb = rb + dr >= N;
+        qa += dq + (int)ca;
+        ra += ca ? N - dr : -dr;
+        qb += dq + (int)cb;
+        rb += cb ? dr - N : dr;
+    }
+    __device__ __forceinline__ void prev(int N)      // j - 1
+    {
+        const bool ca = ra + dr >= N, cb = rb < dr;
+        qa -= dq + (int)ca;
+        ra += ca ? dr - N : dr;
+        qb -= dq + (int)cb;
+        rb += cb ? N - dr : -dr;
+    }
+};
+
 // Work list: items are (pair, band) in the order pairs[order[0]], bands 0..,
 // pairs[order[1]], ...; prefix[q] = first item of the q-th pair in that order.
 __device__ __forceinline__ int find_slot(const int32_t* prefix, int n, int item)
