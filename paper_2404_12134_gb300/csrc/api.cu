@@ -497,6 +497,7 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     p.gpart = reinterpret_cast<float*>(ws + L.off_gpart);
     p.banded = L.banded;
     p.cost_kind = L.cost_kind;
+    p.m_aligned = (L.M % L.R) == 0 ? 1 : 0;
     if (L.soft_fused) {                   // the checkpoint area holds column checkpoints
         p.ckcol = reinterpret_cast<float*>(ws + L.off_rstore);
         p.fused = 1;

@@ -106,24 +106,34 @@ __device__ __forceinline__ float local_cost(const float* bk, const float* y, flo
     return COST == kCostL2 ? __fsqrt_rn(acc) : acc;
 }
 
-// One band of the forward pass; rslot: the band's slot in the R store (when
-// store_r), recompute: start from the stored top row and write no hand-off row.
 // One cell of the forward recursion: r = delta + min^gamma(dg, up, lf), the
 // soft minimum taken relative to min(dg, lf) (see the file comment);
-// kk = log2(e) / gamma, gl = gamma ln 2.
+// kk = log2(e) / gamma, gl = gamma ln 2.  It is split in two: soft_pre takes
+// what does not depend on r of the row above (delta, m2 = min(dg, lf) and
+// S2 = 1 + 2^(-|dg - lf| kk)), soft_chain the rest.  A lane's rows form a
+// serial chain through `up` within a step; computing every row's soft_pre
+// before the chain keeps that work out of the chain's latency.
+struct SoftPre {
+    float delta, m2, S2;
+};
+
 template <int D, int COST>
-__device__ __forceinline__ float soft_cell(const float* bk, const float* y, float dg, float up, float lf, float kk,
-                                           float gl)
+__device__ __forceinline__ SoftPre soft_pre(const float* bk, const float* y, float dg, float lf, float kk)
 {
     float t[D];
-    const float delta = local_cost<D, COST>(bk, y, t);
-    // off the serial path (dg, lf known): m2 and S2
-    const float m2 = fminf(dg, lf);
-    const float S2 = __fadd_rn(1.f, ex2a(__fmul_rn(-fabsf(__fsub_rn(dg, lf)), kk)));
-    const float du = __fsub_rn(up, m2);
+    SoftPre q;
+    q.delta = local_cost<D, COST>(bk, y, t);
+    q.m2 = fminf(dg, lf);
+    q.S2 = __fadd_rn(1.f, ex2a(__fmul_rn(-fabsf(__fsub_rn(dg, lf)), kk)));
+    return q;
+}
+
+__device__ __forceinline__ float soft_chain(const SoftPre& q, float up, float kk, float gl)
+{
+    const float du = __fsub_rn(up, q.m2);
     const float z = ex2a(__fmul_rn(-fabsf(du), kk));
-    const float S = du >= 0.f ? __fadd_rn(S2, z) : __fmaf_rn(S2, z, 1.f);
-    return __fmaf_rn(-gl, lg2a(S), __fadd_rn(delta, fminf(m2, up)));
+    const float S = du >= 0.f ? __fadd_rn(q.S2, z) : __fmaf_rn(q.S2, z, 1.f);
+    return __fmaf_rn(-gl, lg2a(S), __fadd_rn(q.delta, fminf(q.m2, up)));
 }
 
 // Column checkpoints (kCk, band_ckcol_floats: plan.cuh): chunk c of a band
@@ -131,6 +141,8 @@ __device__ __forceinline__ float soft_cell(const float* bk, const float* y, floa
 // lane's last column and r of the row above at the column before - so that
 // the backward can recompute any kCk steps of the band on its own.
 
+// One band of the forward pass; rslot: the band's slot in the R store (when
+// store_r), recompute: start from the stored top row and write no hand-off row.
 template <int D, int R, bool BANDED, int COST>
 __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, int rslot,
                                          bool recompute, bool store_r)
@@ -237,13 +249,14 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
         auto column = [&](auto mask) {
             constexpr bool MASK = decltype(mask)::value;
             const int klo = MASK ? brow.qa - i0 : 0, khi = MASK ? brow.qb - i0 : R - 1;
-            float dg = dg_in, up = up_in;
+            SoftPre q[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) q[k] = soft_pre<D, COST>(b[k], y, k == 0 ? dg_in : col[k - 1], col[k], kk);
+            float up = up_in;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                const float lf = col[k];
-                float r = soft_cell<D, COST>(b[k], y, dg, up, lf, kk, gl);
+                float r = soft_chain(q[k], up, kk, gl);
                 if (MASK && (k < klo || k > khi)) r = INF;      // outside the band
-                dg = lf;
                 up = r;
                 col[k] = r;
             }
@@ -283,7 +296,13 @@ __device__ __forceinline__ void fwd_band(const SoftParams& p, const PairDesc& pd
 // backward steps the warp recomputes the kCk forward steps they read from the
 // band's column checkpoint into `ring` (kCk blocks of R/4 x 32 float4: each
 // lane writes and later reads only its own rows, so no synchronisation).
-template <int D, int R, bool BANDED, int COST, bool FUSED>
+// ALIGNED (no band, M a multiple of R): a lane's rows lie all inside the
+// matrix or all past it, so every column runs unchecked: the lanes past the
+// matrix skip their columns (their state stays (-inf, 0, 0), what the lane
+// above must see below the last row), and the seed e(M-1, N-1) = 1 enters as
+// a diagonal successor with r(M-1, N-1), delta 0 and e = 1 (its weight
+// 2^0 = 1): the same e, bit for bit, without the checked column's registers.
+template <int D, int R, bool BANDED, int COST, bool FUSED, bool ALIGNED = false>
 __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd, int band, int lane, float4* ring,
                                          int rslot)
 {
@@ -297,8 +316,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 
     float b[R][D];
     load_rows<D, R>(b, pd.X, i0, M, d);
-    // lanes whose rows reach the matrix's last row (or pass it)
+    // lanes whose rows reach the matrix's last row (or pass it); ALIGNED: the
+    // lane whose last row is the matrix's
     const bool edge = last && i0 + R >= M;
+    const bool seed_lane = last && i0 + R == M;
     // state of each row at the column to the right (r, delta k, e) with
     // k = log2(e) / gamma; beyond the matrix: (-inf, 0, 0)
     float rp[R], dp[R], ep[R];
@@ -405,12 +426,14 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
             fprev = up_in;
             const int jf = ff - lane;
             if (jf >= 0 && jf < N) {
-                float dg = dg_in, up = up_in;
+                SoftPre q[R];
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    q[k] = soft_pre<D, COST>(b[k], fy, k == 0 ? dg_in : fcol[k - 1], fcol[k], kk);
+                float up = up_in;
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    const float lf = fcol[k];
-                    const float r = soft_cell<D, COST>(b[k], fy, dg, up, lf, kk, gl);
-                    dg = lf;
+                    const float r = soft_chain(q[k], up, kk, gl);
                     up = r;
                     fcol[k] = r;
                 }
@@ -495,6 +518,11 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         }
         float xr = pbr, xd = pbd, xe = pbe;        // below, column j+1
         pbr = br; pbd = bd; pbe = be;
+        if (ALIGNED && seed_lane && s == 31 - lane) {  // this lane's first column, j = N-1
+            xr = rcur[R / 4 - 1].w;
+            xd = 0.f;
+            xe = 1.f;
+        }
 
         const int j = N - 1 - s + (31 - lane);
         // one column of the lane's rows, bottom to top; CHECKED: rows past the
@@ -546,8 +574,10 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 }
             }
         };
-        if (j >= jlo && j <= jhi) {
-            if ((edge && (i0 + R > M || j == N - 1)) || (BANDED && (j < full_lo || j > full_hi)))
+        if (j >= jlo && j <= jhi && (!ALIGNED || i0 < M)) {
+            if (ALIGNED)
+                column(std::false_type{});
+            else if ((edge && (i0 + R > M || j == N - 1)) || (BANDED && (j < full_lo || j > full_hi)))
                 column(std::true_type{});
             else
                 column(std::false_type{});
@@ -573,7 +603,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 }
 
 // The persistent item loop shared by the kernels below.
-template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED>
+template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED, bool ALIGNED = false>
 __device__ __forceinline__ void soft_items(const SoftParams& p)
 {
     extern __shared__ float4 rring_all[];
@@ -611,7 +641,7 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
             const int band = p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k;
-            bwd_band<D, R, BANDED, COST, FUSED>(p, pd, band, lane,
+            bwd_band<D, R, BANDED, COST, FUSED, ALIGNED>(p, pd, band, lane,
                                                 rring_all + (threadIdx.x >> 5) * (FUSED ? kCk : kRPre) * (R / 4) * 32,
                                                 band - p.band_lo + p.rbuf_band0);
         } else {
@@ -634,11 +664,12 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
 // The backward for one channel without a band, held to 96 registers so that five
 // blocks of 4 warps fit per SM (3,040 warps on the GPU): the 2,560 (pair,
 // band) items of 64 pairs of 10k then all run at once, instead of the last
-// pairs waiting for the longest ones to finish.
-template <int D, int R, bool BANDED, int COST, bool FUSED>
+// pairs waiting for the longest ones to finish.  ALIGNED (M a multiple of R)
+// needs no checked columns: at 96 registers it spills nothing.
+template <int D, int R, bool BANDED, int COST, bool FUSED, bool ALIGNED = false>
 __global__ void __launch_bounds__(128, 5) softdtw_bwd_narrow_kernel(SoftParams p)
 {
-    soft_items<D, R, true, BANDED, COST, FUSED>(p);
+    soft_items<D, R, true, BANDED, COST, FUSED, ALIGNED>(p);
 }
 
 // the kernel that runs (D, BWD, FUSED)
@@ -695,10 +726,15 @@ cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
     const size_t smem = soft_smem<R>(BWD, FUSED, block);
-    auto kern = soft_kernel<D, R, BWD, BANDED, COST, FUSED>();
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, block, smem, st>>>(p);
-    return cudaGetLastError();
+    auto run = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, block, smem, st>>>(p);
+        return cudaGetLastError();
+    };
+    if constexpr (BWD && D == 1 && !BANDED) {
+        if (p.m_aligned) return run(softdtw_bwd_narrow_kernel<D, R, BANDED, COST, FUSED, true>);
+    }
+    return run(soft_kernel<D, R, BWD, BANDED, COST, FUSED>());
 }
 
 template <int D, bool BWD>

@@ -44,6 +44,8 @@ struct SoftParams {
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
     int cost_kind;           // LocalCost
+    int m_aligned;           // the prototype's M is a multiple of the rows per lane (every lane's rows
+                             // lie all inside the matrix or all past it)
 };
 
 // Rows held per lane by the soft-DTW kernels (8 for every padded channel

@@ -184,6 +184,34 @@ def test_checkpoint_mode_identical(wts, G):
     assert s_ck <= s_st and (G > 1 or s_ck < s_st)
 
 
+@pytest.mark.parametrize("dir_mode", [0, 1])
+@pytest.mark.parametrize("M", [8, 256, 776, 1000, 1024])
+def test_aligned_rows_backward_identical_to_checked(wts, M, dir_mode):
+    """With one channel, no band and M a multiple of the 8 rows per lane, the
+    backward runs no checked column: lanes past the matrix skip their columns
+    and the seed e(M-1, N-1) = 1 enters as a diagonal successor of weight 1.
+    Values and gradients equal, bit for bit, those of the checked backward,
+    run here through a second channel of zeros (the same arithmetic in
+    another kernel); with R stored and with column checkpoints."""
+    B, b = _case(40 + M, M, [M, 1, 31, 300, M + 45, 2 * M + 3], 1)
+    B2 = np.concatenate([B, np.zeros_like(B)], axis=1)
+    c2 = [np.concatenate([b.cycle(k), np.zeros_like(b.cycle(k))], axis=1) for k in range(b.T)]
+    b2 = synth.pack(c2)
+    opt = wts.options(dir_mode=dir_mode, ckpt_bands=1 << 20) if dir_mode else None
+    out = []
+    for Bx, bx in ((B, b), (B2, b2)):
+        gb = wts.Batch.from_numpy(bx.data, bx.offsets)
+        Bt = torch.from_numpy(Bx).cuda()
+        ws = wts.Workspace()
+        v = wts.softdtw_forward(Bt, gb, 0.2, opt, ws=ws)
+        g = wts.softdtw_backward(Bt, gb, 0.2, None, opt, ws=ws)
+        assert wts.read_status(ws.buf) == 0
+        out.append((v.cpu().numpy(), g.cpu().numpy()))
+    (v1, g1), (v2, g2) = out
+    assert (v1 == v2).all()
+    assert (g1[:, 0] == g2[:, 0]).all() and (g2[:, 1] == 0).all()
+
+
 def test_full_size_pair_value(wts):
     """The soft-DTW workload at full size (64 cycles of 8k-12k, M = 10,000,
     the benchmark's launch): two sampled pairs' values against the FP64
