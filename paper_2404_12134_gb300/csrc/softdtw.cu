@@ -72,12 +72,26 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
                  :: "r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
 // Backward steps whose R blocks are in flight at once (shared-memory ring per warp)
 constexpr int kRPre = 8;
+
+// float4 words of shared memory per backward warp: the R ring, or (fused
+// checkpoint mode) the kCk-step buffer and the staged inputs of the next
+// recompute chunk (R + 2 + 2D floats per lane)
+template <int D, int R>
+__host__ __device__ constexpr int soft_warp_f4(bool fused)
+{
+    return fused ? kCk * (R / 4) * 32 + (R + 2 + 2 * D) * 8 : kRPre * (R / 4) * 32;
+}
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -388,29 +402,50 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // forward's hand-off rows, all written before this launch
     const float* ckb = FUSED ? p.ckcol + pd.aux_off + (int64_t)band * band_ckcol_floats(N, R) : nullptr;
     const float* hprev = (FUSED && !top) ? p.hbuf + pd.hbuf_off + (int64_t)(band - 1) * N : nullptr;
-    auto recompute = [&](int f0, int f1) {
-        const float FINF = 1e30f;                  // the forward's finite sentinel
-        const float gl = p.gamma * kLn2;
-        float fcol[R];
-        float fprev;
+    const float FINF = 1e30f;                      // the forward's finite sentinel
+    // A chunk's inputs (the checkpoint's R + 1 values, the samples of its first
+    // column and of its 32-column block, the top row's value) are staged in
+    // shared memory by asynchronous copies one chunk ahead, after the kCk-step
+    // buffer: kStage floats per lane, [value][lane]
+    float* stage = FUSED ? reinterpret_cast<float*>(ring + kCk * (R / 4) * 32) + lane : nullptr;
+    auto stage_chunk = [&](int f0) {
         if (f0 == 0) {
 #pragma unroll
-            for (int k = 0; k < R; ++k) fcol[k] = FINF;
-            fprev = (top && lane == 0) ? 0.f : FINF;
+            for (int k = 0; k < R; ++k) stage[k * 32] = FINF;
+            stage[R * 32] = (top && lane == 0) ? 0.f : FINF;
         } else {
             const float* ck = ckb + (int64_t)(f0 / kCk) * (R + 1) * 32 + lane;
 #pragma unroll
-            for (int k = 0; k < R; ++k) fcol[k] = __ldg(ck + k * 32);
-            fprev = __ldg(ck + R * 32);
+            for (int k = 0; k <= R; ++k) cp_async4(stage + k * 32, ck + k * 32);
         }
-        float fy[D], fyb[D];
         const int jy = f0 - 1 - lane, fb = f0 & ~31;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            fy[c] = (jy >= 0 && jy < N && c < d) ? __ldg(pd.Y + (int64_t)jy * d + c) : 0.f;
-            fyb[c] = (fb + lane < N && c < d) ? __ldg(pd.Y + (int64_t)(fb + lane) * d + c) : 0.f;
+            float* a = stage + (R + 1 + c) * 32;
+            float* bq = stage + (R + 1 + D + c) * 32;
+            if (jy >= 0 && jy < N && c < d) cp_async4(a, pd.Y + (int64_t)jy * d + c); else *a = 0.f;
+            if (fb + lane < N && c < d) cp_async4(bq, pd.Y + (int64_t)(fb + lane) * d + c); else *bq = 0.f;
         }
-        const float ftop = (top || fb + lane >= N) ? FINF : __ldcg(hprev + fb + lane);
+        float* tq = stage + (R + 1 + 2 * D) * 32;
+        if (top || fb + lane >= N) *tq = FINF; else cp_async4(tq, hprev + fb + lane);
+        cp_async_commit();
+    };
+    auto recompute = [&](int f0, int f1, bool first) {
+        const float gl = p.gamma * kLn2;
+        if (first) stage_chunk(f0);
+        cp_async_wait<0>();
+        float fcol[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) fcol[k] = stage[k * 32];
+        float fprev = stage[R * 32];
+        float fy[D], fyb[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            fy[c] = stage[(R + 1 + c) * 32];
+            fyb[c] = stage[(R + 1 + D + c) * 32];
+        }
+        const float ftop = stage[(R + 1 + 2 * D) * 32];
+        if (f0 >= kCk) stage_chunk(f0 - kCk);        // the next chunk down, while this one runs
         for (int ff = f0; ff < f1; ++ff) {
             const int src = ff & 31;
 #pragma unroll
@@ -465,7 +500,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
             // steps (read backwards) starts at its last step
             const int f = N + 30 - s;
             const int fr = f % kCk;
-            if (s == s_begin || fr == kCk - 1) recompute(f - fr, min(f - fr + kCk, N + 31));
+            if (s == s_begin || fr == kCk - 1) recompute(f - fr, min(f - fr + kCk, N + 31), s == s_begin);
 #pragma unroll
             for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[fr * (R / 4) * 32 + k4 * 32 + lane];
         } else {
@@ -642,8 +677,8 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
             // bands bottom-up: the whole pair, or the range's last band first
             const int band = p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k;
             bwd_band<D, R, BANDED, COST, FUSED, ALIGNED>(p, pd, band, lane,
-                                                rring_all + (threadIdx.x >> 5) * (FUSED ? kCk : kRPre) * (R / 4) * 32,
-                                                band - p.band_lo + p.rbuf_band0);
+                                                         rring_all + (threadIdx.x >> 5) * soft_warp_f4<D, R>(FUSED),
+                                                         band - p.band_lo + p.rbuf_band0);
         } else {
             const int band = p.band_cnt > 0 ? p.band_lo + k : k;
             fwd_band<D, R, BANDED, COST>(p, pd, band, lane, band - p.band_lo + p.rbuf_band0, p.recompute != 0,
@@ -683,11 +718,11 @@ constexpr auto soft_kernel()
 }
 
 // dynamic shared memory per block: the backward's R ring (or, FUSED, its
-// kCk-step buffer of recomputed R)
-template <int R>
+// kCk-step buffer of recomputed R and the staged inputs of the next chunk)
+template <int D, int R>
 constexpr size_t soft_smem(bool bwd, bool fused, int block)
 {
-    return bwd ? (size_t)(block / 32) * (fused ? kCk : kRPre) * (R / 4) * 32 * sizeof(float4) : 0;
+    return bwd ? (size_t)(block / 32) * soft_warp_f4<D, R>(fused) * sizeof(float4) : 0;
 }
 
 __global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g,
@@ -725,7 +760,7 @@ template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
 cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
-    const size_t smem = soft_smem<R>(BWD, FUSED, block);
+    const size_t smem = soft_smem<D, R>(BWD, FUSED, block);
     auto run = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, block, smem, st>>>(p);
@@ -754,7 +789,7 @@ template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
 int occ_db(int block)
 {
     constexpr int R = 8;
-    const size_t smem = soft_smem<R>(BWD, FUSED, block);
+    const size_t smem = soft_smem<D, R>(BWD, FUSED, block);
     int n = 0;
     auto kern = soft_kernel<D, R, BWD, BANDED, COST, FUSED>();
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
