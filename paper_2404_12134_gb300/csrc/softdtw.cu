@@ -353,7 +353,8 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // boundary slot b holds the top row of band b+1: per column two 8-byte
     // words {r, delta k} and {e, 0}, each NaN until written
     const u64* enext = last ? nullptr : reinterpret_cast<const u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)band * N);
-    u64* emine = top ? nullptr : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
+    u64* emine = (top || p.skip_handoff) ? nullptr
+                                         : reinterpret_cast<u64*>(p.ebuf) + 2 * (pd.hbuf_off + (int64_t)(band - 1) * N);
     const float* rs = FUSED ? nullptr : p.rstore + pd.aux_off + (int64_t)rslot * (N + 31) * 32 * R;
 
     // Sakoe-Chiba band: the band's columns [jlo, jhi], the row below's
@@ -381,14 +382,29 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
     // N+30-ss) is copied into ring slot ss mod kRPre kRPre steps ahead of its
     // use (one commit group per step, empty past the end), so that a step's
     // wait covers the copies issued kRPre steps earlier
+    // (without a band every lane's slot of every step exists, as the forward
+    // stores all N + 31 steps: no range check, and the source walks down one
+    // step of R per call)
+    const float4* rsrc = (FUSED || BANDED)
+                             ? nullptr
+                             : reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - s_begin) * 32 * R) + lane;
     auto issue_r = [&](int ss) {
         if (FUSED) return;
-        const int jj = N - 1 - ss + (31 - lane);
-        if (ss < steps && jj >= jlo && jj <= jhi) {
-            const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - ss) * 32 * R);
-            float4* dst = ring + (ss & (kRPre - 1)) * (R / 4) * 32;
+        if (!BANDED) {
+            if (ss < steps) {
+                float4* dst = ring + (ss & (kRPre - 1)) * (R / 4) * 32 + lane;
 #pragma unroll
-            for (int k4 = 0; k4 < R / 4; ++k4) cp_async16(dst + k4 * 32 + lane, src4 + k4 * 32 + lane);
+                for (int k4 = 0; k4 < R / 4; ++k4) cp_async16(dst + k4 * 32, rsrc + k4 * 32);
+            }
+            rsrc -= (R / 4) * 32;
+        } else {
+            const int jj = N - 1 - ss + (31 - lane);
+            if (ss < steps && jj >= jlo && jj <= jhi) {
+                const float4* src4 = reinterpret_cast<const float4*>(rs + (int64_t)(N + 30 - ss) * 32 * R);
+                float4* dst = ring + (ss & (kRPre - 1)) * (R / 4) * 32;
+#pragma unroll
+                for (int k4 = 0; k4 < R / 4; ++k4) cp_async16(dst + k4 * 32 + lane, src4 + k4 * 32 + lane);
+            }
         }
         cp_async_commit();
     };
@@ -616,7 +632,7 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 column(std::true_type{});
             else
                 column(std::false_type{});
-            if (emine != nullptr && lane == 0 && !p.skip_handoff) {
+            if (emine != nullptr && lane == 0) {
                 // (NaN from overflowing samples stored as -inf, as in the forward)
                 __stcg(emine + 2 * j, pack2(fmaxf(rp[0], NINF), dp[0]));
                 __stcg(emine + 2 * j + 1, pack2(fmaxf(ep[0], NINF), 0.f));
