@@ -51,11 +51,11 @@ SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0152 + 3.2689 + 3.3682 + 0.0534) * 1e9 / 7
 # Warp instructions per cell of the checkpointed soft-DTW passes (column
 # checkpoints, recompute fused into the backward), from one ncu capture
 # (smsp__inst_executed.sum) of the same build on the very-long workload's
-# 8 pairs cut to a quarter (5.842e9 cells): forward 5.0907e9, backward
-# 1.2110e10.  Both passes are bound by the issue rate (one warp instruction
+# 8 pairs cut to a quarter (5.842e9 cells): forward 4.9542e9, backward
+# 1.21216e10.  Both passes are bound by the issue rate (one warp instruction
 # per scheduler per cycle), not by a pipe or by DRAM.
-SOFT_CKPT_FWD_INSTR_PER_CELL = 5.0907e9 / 5.842045e9
-SOFT_CKPT_BWD_INSTR_PER_CELL = 1.2110e10 / 5.842045e9
+SOFT_CKPT_FWD_INSTR_PER_CELL = 4.9542e9 / 5.842045e9
+SOFT_CKPT_BWD_INSTR_PER_CELL = 1.21216e10 / 5.842045e9
 
 
 def softckpt_roofline(cells: int, fwd_ms: float, bwd_ms: float, sms: int, ex2: float | None, lg2: float | None):
