@@ -84,13 +84,14 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Backward steps whose R blocks are in flight at once (shared-memory ring per warp)
 constexpr int kRPre = 8;
 
-// float4 words of shared memory per backward warp: the R ring, or (fused
-// checkpoint mode) the kCk-step buffer and the staged inputs of the next
-// recompute chunk (R + 2 + 2D floats per lane)
+// float4 words of shared memory per backward warp: the R ring (without a
+// band followed by two chunks of hand-off slots and samples, 2 x (16 + 4D)
+// bytes per lane), or (fused checkpoint mode) the kCk-step buffer and the
+// staged inputs of the next recompute chunk (R + 2 + 2D floats per lane)
 template <int D, int R>
-__host__ __device__ constexpr int soft_warp_f4(bool fused)
+__host__ __device__ constexpr int soft_warp_f4(bool fused, bool banded)
 {
-    return fused ? kCk * (R / 4) * 32 + (R + 2 + 2 * D) * 8 : kRPre * (R / 4) * 32;
+    return fused ? kCk * (R / 4) * 32 + (R + 2 + 2 * D) * 8 : kRPre * (R / 4) * 32 + (banded ? 0 : 64 + 16 * D);
 }
 
 constexpr float kLog2e = 1.4426950408889634f;
@@ -408,9 +409,6 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
         }
         cp_async_commit();
     };
-    if (!FUSED)
-#pragma unroll 1
-        for (int ss = s_begin; ss < s_begin + kRPre; ++ss) issue_r(ss);
 
     // FUSED: recompute forward steps [f0, f1) of this band into `ring` from
     // the column checkpoint (the same cell arithmetic and inputs as the full
@@ -495,20 +493,53 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 dst[k4 * 32 + lane] = make_float4(fcol[4 * k4], fcol[4 * k4 + 1], fcol[4 * k4 + 2], fcol[4 * k4 + 3]);
         }
     };
-    // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l
+    // lane-31 feeds one chunk ahead: lane l holds column N-1-s-l.  With R
+    // stored and no band, each chunk's hand-off slots (16 B: r, delta k, e) and samples are
+    // copied by cp.async, one chunk ahead and in the step's commit group, into
+    // one of two shared-memory buffers after the R ring, and read there every
+    // step by lane 31 (the ring's wait seven groups behind has them complete
+    // long before their chunk starts); no register holds a chunk, which lets
+    // the one-channel loop without a band be unrolled by two within 96
+    // registers (the column state then alternates registers instead of being
+    // copied each step).  Fused or banded, the chunks are loaded into registers
+    // and broadcast by shuffles.
+    constexpr bool SPF = !FUSED && !BANDED;
+    float4* ech = SPF ? ring + kRPre * (R / 4) * 32 : nullptr;           // [2][32]
+    float* ych = SPF ? reinterpret_cast<float*>(ech + 64) : nullptr;    // [2][D][32]
     float ynext[D];
     u64 wa = 0, wb = 0;
-    auto load_y = [&](int jj) {
+    auto load_y = [&](int jj, int buf) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) ynext[c] = (jj >= 0 && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+        for (int c = 0; c < D; ++c) {
+            if (SPF) {
+                float* dst = ych + (buf * D + c) * 32 + lane;
+                if (jj >= 0 && c < d) cp_async4(dst, pd.Y + (int64_t)jj * d + c);
+                else *dst = 0.f;
+            } else {
+                ynext[c] = (jj >= 0 && c < d) ? __ldg(pd.Y + (int64_t)jj * d + c) : 0.f;
+            }
+        }
     };
-    auto load_e = [&](int jj) {
-        if (jj >= 0) { wa = __ldcv(enext + 2 * jj); wb = __ldcv(enext + 2 * jj + 1); }
+    auto load_e = [&](int jj, int buf) {
+        if (jj >= 0) {
+            if (SPF) {
+                cp_async16(ech + buf * 32 + lane, enext + 2 * jj);
+            } else {
+                wa = __ldcv(enext + 2 * jj);
+                wb = __ldcv(enext + 2 * jj + 1);
+            }
+        }
     };
-    load_y(N - 1 - s_begin - lane);
-    if (!last) load_e(N - 1 - s_begin - lane);
-
+    load_y(N - 1 - s_begin - lane, (s_begin >> 5) & 1);
+    if (!last) load_e(N - 1 - s_begin - lane, (s_begin >> 5) & 1);
+    // the first chunk's group, then the ring's first kRPre steps: the first
+    // step's wait (all but the newest kRPre - 1 groups) covers both
+    if (SPF) cp_async_commit();
+    if (!FUSED)
 #pragma unroll 1
+        for (int ss = s_begin; ss < s_begin + kRPre; ++ss) issue_r(ss);
+
+#pragma unroll(D == 1 && !BANDED && !FUSED ? 2 : 1)
     for (int s = s_begin; s < steps; ++s) {
         float4 rcur[R / 4];
         if (FUSED) {
@@ -524,15 +555,30 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
 #pragma unroll
             for (int k4 = 0; k4 < R / 4; ++k4) rcur[k4] = ring[(s & (kRPre - 1)) * (R / 4) * 32 + k4 * 32 + lane];
         }
+        const int cbuf = (s >> 5) & 1;
         if ((s & 31) == 0 && s < N) {
             const int jj = N - 1 - s - lane;
+            if (!SPF) {
 #pragma unroll
-            for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
+                for (int c = 0; c < D; ++c) ybuf[c] = ynext[c];
+            }
             if (!last) {
-                // only the row below's columns inside the band are written (and waited for)
+                // only the row below's columns inside the band are written (and
+                // waited for); a slot found unwritten is polled from global memory
                 const bool need = jj >= jbot_lo && jj <= jbot_hi;
+                if (SPF && need) {
+                    const float4 v = ech[cbuf * 32 + lane];
+                    wa = pack2(v.x, v.y);
+                    wb = pack2(v.z, v.w);
+                }
+                bool polled = false;
                 const bool ok = wait_filled(need && (is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb)),
-                                            [&]() { load_e(jj); return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb); },
+                                            [&]() {
+                                                wa = __ldcv(enext + 2 * jj);
+                                                wb = __ldcv(enext + 2 * jj + 1);
+                                                polled = true;
+                                                return is_nan_bits((uint32_t)wa) || is_nan_bits((uint32_t)wb);
+                                            },
                                             p.hdr, 4, p.spin_limit);
                 if (!ok) {
                     cp_async_wait<0>();
@@ -545,23 +591,37 @@ __device__ __forceinline__ void bwd_band(const SoftParams& p, const PairDesc& pd
                 } else {
                     cr = NINF; cd = 0.f; ce = 0.f;
                 }
-                load_e(jj - 32);
+                if (SPF && (polled || !need)) ech[cbuf * 32 + lane] = make_float4(cr, cd, ce, 0.f);
             }
-            load_y(jj - 32);
+            if (SPF) {
+                // this chunk's slots visible to lane 31, the other buffer's last
+                // chunk read by every lane, before the next chunk's copies
+                __syncwarp();
+                if (!last) load_e(jj - 32, cbuf ^ 1);
+            } else if (!last) {
+                load_e(jj - 32, 0);
+            }
+            load_y(jj - 32, cbuf ^ 1);
         }
         const int src = s & 31;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const float fresh = __shfl_sync(FULL, ybuf[c], src);
+            const float fresh = SPF ? ych[(cbuf * D + c) * 32 + src] : __shfl_sync(FULL, ybuf[c], src);
             const float moved = __shfl_down_sync(FULL, y[c], 1);
             y[c] = lane == 31 ? fresh : moved;
         }
         float br = __shfl_down_sync(FULL, rp[0], 1);
         float bd = __shfl_down_sync(FULL, dp[0], 1);
         float be = __shfl_down_sync(FULL, ep[0], 1);
-        const float fr = __shfl_sync(FULL, cr, src);
-        const float fd = __shfl_sync(FULL, cd, src);
-        const float fe = __shfl_sync(FULL, ce, src);
+        float fr, fd, fe;
+        if (SPF) {
+            const float4 v = last ? make_float4(NINF, 0.f, 0.f, 0.f) : ech[cbuf * 32 + src];
+            fr = v.x; fd = v.y; fe = v.z;
+        } else {
+            fr = __shfl_sync(FULL, cr, src);
+            fd = __shfl_sync(FULL, cd, src);
+            fe = __shfl_sync(FULL, ce, src);
+        }
         if (lane == 31) {
             br = last ? NINF : fr;
             bd = last ? 0.f : fd;
@@ -693,7 +753,7 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
             // bands bottom-up: the whole pair, or the range's last band first
             const int band = p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k;
             bwd_band<D, R, BANDED, COST, FUSED, ALIGNED>(p, pd, band, lane,
-                                                         rring_all + (threadIdx.x >> 5) * soft_warp_f4<D, R>(FUSED),
+                                                         rring_all + (threadIdx.x >> 5) * soft_warp_f4<D, R>(FUSED, BANDED),
                                                          band - p.band_lo + p.rbuf_band0);
         } else {
             const int band = p.band_cnt > 0 ? p.band_lo + k : k;
@@ -712,13 +772,14 @@ __global__ void __launch_bounds__(256) softdtw_kernel(SoftParams p)
     soft_items<D, R, BWD, BANDED, COST, FUSED>(p);
 }
 
-// The backward for one channel without a band, held to 96 registers so that five
-// blocks of 4 warps fit per SM (3,040 warps on the GPU): the 2,560 (pair,
-// band) items of 64 pairs of 10k then all run at once, instead of the last
-// pairs waiting for the longest ones to finish.  ALIGNED (M a multiple of R)
-// needs no checked columns: at 96 registers it spills nothing.
+// The backward for one channel without a band, its step loop unrolled by two,
+// held to 128 registers: four blocks of 4 warps per SM (2,432 warps on the
+// GPU; the 2,560 (pair, band) items of 64 pairs of 10k then almost all run at
+// once).  Held to 96 registers (five blocks, every item at once) it ran 1.5 %
+// slower on that workload, the unrolled loop at the edge of its registers.
+// ALIGNED (M a multiple of R) needs no checked columns.
 template <int D, int R, bool BANDED, int COST, bool FUSED, bool ALIGNED = false>
-__global__ void __launch_bounds__(128, 5) softdtw_bwd_narrow_kernel(SoftParams p)
+__global__ void __launch_bounds__(128, 4) softdtw_bwd_narrow_kernel(SoftParams p)
 {
     soft_items<D, R, true, BANDED, COST, FUSED, ALIGNED>(p);
 }
@@ -736,9 +797,9 @@ constexpr auto soft_kernel()
 // dynamic shared memory per block: the backward's R ring (or, FUSED, its
 // kCk-step buffer of recomputed R and the staged inputs of the next chunk)
 template <int D, int R>
-constexpr size_t soft_smem(bool bwd, bool fused, int block)
+constexpr size_t soft_smem(bool bwd, bool fused, bool banded, int block)
 {
-    return bwd ? (size_t)(block / 32) * soft_warp_f4<D, R>(fused) * sizeof(float4) : 0;
+    return bwd ? (size_t)(block / 32) * soft_warp_f4<D, R>(fused, banded) * sizeof(float4) : 0;
 }
 
 __global__ void grad_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ g,
@@ -776,7 +837,7 @@ template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
 cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
     constexpr int R = 8;
-    const size_t smem = soft_smem<D, R>(BWD, FUSED, block);
+    const size_t smem = soft_smem<D, R>(BWD, FUSED, BANDED, block);
     auto run = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, block, smem, st>>>(p);
@@ -805,7 +866,7 @@ template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
 int occ_db(int block)
 {
     constexpr int R = 8;
-    const size_t smem = soft_smem<D, R>(BWD, FUSED, block);
+    const size_t smem = soft_smem<D, R>(BWD, FUSED, BANDED, block);
     int n = 0;
     auto kern = soft_kernel<D, R, BWD, BANDED, COST, FUSED>();
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
