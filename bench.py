@@ -44,10 +44,10 @@ WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1582 + 5.6421) * 1e9 / 2.2029e10
 # DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
 # ncu capture of both kernels (the same build) on the soft-DTW workload with
 # its cycles cut to an eighth (64 pairs, the benchmark's occupancy):
-# (0.0152 + 3.2689 + 3.3682 + 0.0534)e9 bytes / 7.9029e8 cells (stored R plus
+# (0.0163 + 3.2686 + 3.3679 + 0.0536)e9 bytes / 7.9029e8 cells (stored R plus
 # hand-off rows, in proportion to cells; the skew margin, 2.5 % of a band at
 # that length, is 0.3 % at full length).
-SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0152 + 3.2689 + 3.3682 + 0.0534) * 1e9 / 7.9029e8
+SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0163 + 3.2686 + 3.3679 + 0.0536) * 1e9 / 7.9029e8
 # Warp instructions per cell of the checkpointed soft-DTW passes (column
 # checkpoints, recompute fused into the backward), from one ncu capture
 # (smsp__inst_executed.sum) of the same build on the very-long workload's
