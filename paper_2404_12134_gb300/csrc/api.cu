@@ -383,11 +383,21 @@ DPParams base_params(const Layout& L, char* ws, const wts_options* opt = nullptr
     return p;
 }
 
-int launch_dp(int mode, const Layout& L, const DPParams& p, const wts_options* opt, cudaStream_t st)
+int launch_dp(int mode, const Layout& L, const DPParams& p0, const wts_options* opt, cudaStream_t st)
 {
     int grid = 0, block = 0;
-    int rc = grid_for(mode, L, opt, &grid, &block, p.n_items);
+    int rc = grid_for(mode, L, opt, &grid, &block, p0.n_items);
     if (rc) return rc;
+    DPParams p = p0;
+    // Every pair of a shared-prototype launch has the same bands: take the
+    // pairs in groups whose items about fill the resident warps once,
+    // band-major within a group (measured: batched DBA, 200 x 25k x 6 ch,
+    // wavefront 74.1 -> 70.7 ms against pair after pair)
+    if (L.op != kOpPairwise && !p.recompute && !p.banded && L.M > 0) {
+        const int64_t nb = cdiv(L.M, L.BR);
+        const int64_t warps = (int64_t)grid * (block / 32);
+        p.group_pairs = (int)std::max<int64_t>(1, std::min<int64_t>(L.P, warps / nb));
+    }
     cudaError_t e;
     {
         Prof pr(p.recompute ? "wavefront_recompute" : "wavefront", st);

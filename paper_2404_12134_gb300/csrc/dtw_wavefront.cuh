@@ -41,6 +41,8 @@ struct DPParams {
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); R = 16 only;
                              // items then run band-major (every pair's band 0, then band 1, ...)
     int cost_kind;           // LocalCost; kCostL2 runs with R = 16 only
+    int group_pairs;         // > 0 (every pair with the same bands): the work list takes pairs in
+                             // groups of this many, band-major within a group; 0: pair after pair
 };
 
 // Launch the persistent wavefront for D (padded channels) and R (rows/lane);

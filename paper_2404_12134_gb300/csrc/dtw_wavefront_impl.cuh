@@ -496,6 +496,18 @@ __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(
             // Every pair has the same number of bands (one prototype).
             q = item % p.P;
             band = item / p.P;
+        } else if (p.group_pairs > 0) {
+            // groups of G pairs (in the work list's order), band-major within
+            // a group: a group's bands start in the order their producers
+            // do, and its items about fill the resident warps once.  Band
+            // b - 1 of a pair is earlier in the list (no deadlock).
+            const int nb = p.prefix[1] - p.prefix[0];
+            const int G = p.group_pairs;
+            const int g = item / (G * nb), q0 = g * G;
+            const int Gg = min(G, p.P - q0);
+            const int r = item - q0 * nb;
+            band = r / Gg;
+            q = q0 + r % Gg;
         } else {
             q = find_slot(p.prefix, p.P, item);
             band = item - p.prefix[q];
