@@ -37,10 +37,10 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per cell of the code-writing wavefront, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel build on 36 cycles of this workload: (0.1582 + 5.6421)e9 bytes /
+# kernel build on 36 cycles of this workload: (0.1479 + 5.6418)e9 bytes /
 # 2.2029e10 cells.  Traffic grows in proportion to the cells (codes +
 # hand-off rows).
-WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1582 + 5.6421) * 1e9 / 2.2029e10
+WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1479 + 5.6418) * 1e9 / 2.2029e10
 # DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
 # ncu capture of both kernels (the same build) on the soft-DTW workload with
 # its cycles cut to an eighth (64 pairs, the benchmark's occupancy):
