@@ -392,11 +392,12 @@ int launch_dp(int mode, const Layout& L, const DPParams& p0, const wts_options* 
     // Every pair of a shared-prototype launch has the same bands: take the
     // pairs in groups whose items about fill the resident warps once,
     // band-major within a group (measured: batched DBA, 200 x 25k x 6 ch,
-    // wavefront 74.1 -> 70.7 ms against pair after pair)
-    if (L.op != kOpPairwise && !p.recompute && !p.banded && L.M > 0) {
-        const int64_t nb = cdiv(L.M, L.BR);
+    // wavefront 74.1 -> 70.7 ms against pair after pair).  Under a band
+    // every pair's band b comes before any band b + 1 (one group).
+    if (L.op != kOpPairwise && L.M > 0) {
+        const int64_t nb = p.recompute ? p.band_cnt : cdiv(L.M, L.BR);
         const int64_t warps = (int64_t)grid * (block / 32);
-        p.group_pairs = (int)std::max<int64_t>(1, std::min<int64_t>(L.P, warps / nb));
+        p.group_pairs = p.banded ? L.P : (int)std::max<int64_t>(1, std::min<int64_t>(L.P, warps / nb));
     }
     cudaError_t e;
     {

@@ -481,33 +481,25 @@ __global__ void __launch_bounds__(128, min_blocks<D, R>()) dtw_wavefront_kernel(
         if (item >= p.n_items) break;
         if (ld_volatile(&p.hdr->abort)) break;
         int q, band;
-        if (p.recompute && BANDED) {
-            q = item % p.P;
-            band = p.band_lo + item / p.P;
-        } else if (p.recompute) {
-            q = item / p.band_cnt;
-            band = p.band_lo + item % p.band_cnt;
-        } else if (BANDED) {
-            // band-major: under a band, row band b of a pair starts only once
-            // the band above has covered the diagonal drift of b's first
-            // column, so a pair has few bands ready at a time; taking every
-            // pair's band b before any band b + 1 keeps warps on ready work.
-            // Band b - 1 of a pair is always earlier in the list (no deadlock).
-            // Every pair has the same number of bands (one prototype).
-            q = item % p.P;
-            band = item / p.P;
-        } else if (p.group_pairs > 0) {
+        if (p.group_pairs > 0) {
             // groups of G pairs (in the work list's order), band-major within
             // a group: a group's bands start in the order their producers
-            // do, and its items about fill the resident warps once.  Band
-            // b - 1 of a pair is earlier in the list (no deadlock).
-            const int nb = p.prefix[1] - p.prefix[0];
+            // do, and its items about fill the resident warps once (G = P:
+            // every pair's band b before any band b + 1, as under a band,
+            // where a pair has few bands ready at a time).  Every pair has the
+            // same bands here (one prototype); recompute runs the range
+            // [band_lo, band_lo + band_cnt) of each.  Band b - 1 of a pair is
+            // earlier in the list (no deadlock).
+            const int nb = p.recompute ? p.band_cnt : p.prefix[1] - p.prefix[0];
             const int G = p.group_pairs;
             const int g = item / (G * nb), q0 = g * G;
             const int Gg = min(G, p.P - q0);
             const int r = item - q0 * nb;
-            band = r / Gg;
             q = q0 + r % Gg;
+            band = (p.recompute ? p.band_lo : 0) + r / Gg;
+        } else if (p.recompute) {
+            q = item / p.band_cnt;
+            band = p.band_lo + item % p.band_cnt;
         } else {
             q = find_slot(p.prefix, p.P, item);
             band = item - p.prefix[q];
