@@ -106,3 +106,24 @@ def test_segmented_dba_iteration_in_a_graph(wts):
         Bo, cnt_o, cb_o, _ = oracle.dba_iterate(Bo, b.data, b.offsets, "f32")
         assert (Bout.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all() and float(cb) == cb_o, it
         Bin.copy_(Bout)
+
+
+@pytest.mark.parametrize("wpb,max_blocks,rows", [(1, 1, 8), (1, 2, 16), (4, 3, 8), (2, 5, 16), (4, 0, 32)])
+def test_grouped_work_list_any_group_size(wts, wpb, max_blocks, rows):
+    """The work list takes the pairs in groups of about (resident warps /
+    bands per pair), band-major within a group: with a grid cut to a few
+    warps the groups have 1 to a few pairs and the last group is ragged (one
+    warp alone runs every item in turn).  Scores, costs, |pi|, paths and the
+    DBA prototype stay bit-exact against the FP32 mirror."""
+    b, B = _uneven(seed=33, T=13)
+    M = 700                                  # 3 bands of 256 rows, 2 of 512 or 1 of 1,024
+    B = synth.clean_prototype(b, M)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    opt = wts.options(rows_per_thread=rows, warps_per_block=wpb, max_blocks=max_blocks)
+    s, c, L = wts.anomaly_score(Bt, gb, opt)
+    s32, c32, L32 = oracle.score(B, b.data, b.offsets, "f32")
+    assert (c.cpu().numpy() == c32).all() and (L.cpu().numpy() == L32).all() and (s.cpu().numpy() == s32).all()
+    Bn, cnt, cb, ck = wts.dba_iterate(Bt, gb, opt)
+    Bo, cnt_o, cb_o, ck_o = oracle.dba_iterate(B, b.data, b.offsets, "f32")
+    assert (Bn.cpu().numpy() == Bo).all() and (cnt.cpu().numpy() == cnt_o).all() and (ck.cpu().numpy() == ck_o).all()
