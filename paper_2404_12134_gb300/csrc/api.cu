@@ -172,6 +172,8 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             if (opt->rows_per_thread && opt->rows_per_thread != 16)
                 return fail(WTS_EINVAL, "with a band, rows_per_thread must be 0 or 16 (got %d)", opt->rows_per_thread);
             L->R = 16;
+        } else if (opt->band < kSoftNarrowBand) {
+            L->R = 4;
         }
         L->banded = 1;
     }
@@ -508,6 +510,7 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     p.gpart = reinterpret_cast<float*>(ws + L.off_gpart);
     p.banded = L.banded;
     p.cost_kind = L.cost_kind;
+    p.rows = L.R;
     p.m_aligned = (L.M % L.R) == 0 ? 1 : 0;
     if (L.soft_fused) {                   // the checkpoint area holds column checkpoints
         p.ckcol = reinterpret_cast<float*>(ws + L.off_rstore);
@@ -524,7 +527,7 @@ int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, 
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind, L.soft_fused);
+    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind, L.soft_fused, L.R);
     if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;

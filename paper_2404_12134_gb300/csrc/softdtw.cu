@@ -833,10 +833,9 @@ __global__ void adam_kernel(float* x, const float* grad, float* m, float* v, int
     x[i] = __fsub_rn(x[i], __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(sqrtf(vh), eps)));
 }
 
-template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
-cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
+template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED = false>
+cudaError_t launch_dbr(const SoftParams& p, int grid, int block, cudaStream_t st)
 {
-    constexpr int R = 8;
     const size_t smem = soft_smem<D, R>(BWD, FUSED, BANDED, block);
     auto run = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -847,6 +846,16 @@ cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
         if (p.m_aligned) return run(softdtw_bwd_narrow_kernel<D, R, BANDED, COST, FUSED, true>);
     }
     return run(soft_kernel<D, R, BWD, BANDED, COST, FUSED>());
+}
+
+// 8 rows per lane, or 4 under a narrow band (kSoftNarrowBand)
+template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
+cudaError_t launch_db(const SoftParams& p, int grid, int block, cudaStream_t st)
+{
+    if constexpr (BANDED) {
+        if (p.rows == 4) return launch_dbr<D, 4, BWD, BANDED, COST, FUSED>(p, grid, block, st);
+    }
+    return launch_dbr<D, 8, BWD, BANDED, COST, FUSED>(p, grid, block, st);
 }
 
 template <int D, bool BWD>
@@ -862,10 +871,9 @@ cudaError_t launch_d(const SoftParams& p, int grid, int block, cudaStream_t st)
                     : launch_db<D, BWD, false, kCostSqEuclid>(p, grid, block, st);
 }
 
-template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
-int occ_db(int block)
+template <int D, int R, bool BWD, bool BANDED, int COST, bool FUSED = false>
+int occ_dbr(int block)
 {
-    constexpr int R = 8;
     const size_t smem = soft_smem<D, R>(BWD, FUSED, BANDED, block);
     int n = 0;
     auto kern = soft_kernel<D, R, BWD, BANDED, COST, FUSED>();
@@ -874,15 +882,25 @@ int occ_db(int block)
     return n;
 }
 
+template <int D, bool BWD, bool BANDED, int COST, bool FUSED = false>
+int occ_db(int block, int rows)
+{
+    if constexpr (BANDED) {
+        if (rows == 4) return occ_dbr<D, 4, BWD, BANDED, COST, FUSED>(block);
+    }
+    return occ_dbr<D, 8, BWD, BANDED, COST, FUSED>(block);
+}
+
 template <int D, bool BWD>
-int occ_d(int block, int banded, int cost_kind, int fused)
+int occ_d(int block, int banded, int cost_kind, int fused, int rows)
 {
     if (BWD && fused && !banded)
-        return cost_kind == kCostL2 ? occ_db<D, BWD, false, kCostL2, BWD>(block)
-                                    : occ_db<D, BWD, false, kCostSqEuclid, BWD>(block);
+        return cost_kind == kCostL2 ? occ_db<D, BWD, false, kCostL2, BWD>(block, rows)
+                                    : occ_db<D, BWD, false, kCostSqEuclid, BWD>(block, rows);
     if (cost_kind == kCostL2)
-        return banded ? occ_db<D, BWD, true, kCostL2>(block) : occ_db<D, BWD, false, kCostL2>(block);
-    return banded ? occ_db<D, BWD, true, kCostSqEuclid>(block) : occ_db<D, BWD, false, kCostSqEuclid>(block);
+        return banded ? occ_db<D, BWD, true, kCostL2>(block, rows) : occ_db<D, BWD, false, kCostL2>(block, rows);
+    return banded ? occ_db<D, BWD, true, kCostSqEuclid>(block, rows)
+                  : occ_db<D, BWD, false, kCostSqEuclid>(block, rows);
 }
 
 }  // namespace
@@ -910,12 +928,12 @@ cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, 
     return cudaErrorInvalidValue;
 }
 
-int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded, int cost_kind, int fused)
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded, int cost_kind, int fused, int rows)
 {
     if (backward) {
-        WTS_SOFT_DISPATCH(occ_d, true, block, banded, cost_kind, fused)
+        WTS_SOFT_DISPATCH(occ_d, true, block, banded, cost_kind, fused, rows)
     } else {
-        WTS_SOFT_DISPATCH(occ_d, false, block, banded, cost_kind, fused)
+        WTS_SOFT_DISPATCH(occ_d, false, block, banded, cost_kind, fused, rows)
     }
     return 0;
 }

@@ -44,6 +44,7 @@ struct SoftParams {
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
     int cost_kind;           // LocalCost
+    int rows;                // rows per lane R: 8, or 4 under a narrow band
     int m_aligned;           // the prototype's M is a multiple of the rows per lane (every lane's rows
                              // lie all inside the matrix or all past it)
 };
@@ -51,10 +52,19 @@ struct SoftParams {
 // Rows held per lane by the soft-DTW kernels (8 for every padded channel
 // count: measured best against 4 and 16).
 inline int soft_rows(int /*D*/) { return 8; }
+// Under a Sakoe-Chiba band narrower than this fraction the soft-DTW passes
+// run 4 rows per lane: the band's lower edge is a chain of row bands, each
+// starting when the one above has covered its first 32 R + 62 columns, so
+// the time barely falls with the band's width at 8 rows; at 4 the chain's
+// steps are half as long (64 pairs of 10k, forward + backward: w = 0.3
+// 18.5 -> 15.8 ms, w = 0.1 18.0 -> 14.0 ms; at w = 0.6 8 rows stay faster,
+// 18.1 against 19.8 ms).
+constexpr double kSoftNarrowBand = 0.45;
 
 cudaError_t launch_softdtw_fwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
 cudaError_t launch_softdtw_bwd(int D, const SoftParams& p, int grid, int block, cudaStream_t st);
-int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0, int cost_kind = 0, int fused = 0);
+int softdtw_max_blocks_per_sm(int D, int backward, int block, int banded = 0, int cost_kind = 0, int fused = 0,
+                              int rows = 8);
 
 // grad_B[i][c] = sum_k g[k] * gpart[k][i][c] (FP64 sum, k ascending); g == null
 // takes g[k] = 1 / N_k (Eq. 7 with lambda_k = 1) from the cycle offsets
