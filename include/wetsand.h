@@ -80,7 +80,8 @@ typedef struct wts_batch {
 /* Launch options; a zeroed struct (or NULL) selects the defaults. */
 typedef struct wts_options {
     int32_t rows_per_thread;       /* prototype rows held per lane: 0 = default (32 if d <= 2, else 16); 8, 16 or 32 (32 needs d <= 3);
-                                      4 for Sub-DTW only */
+                                      4 for Sub-DTW only.  Soft-DTW does not use it: 8 rows per lane, 4 under a
+                                      band narrower than 0.45 */
     int32_t warps_per_block;       /* 0 = 4; 1..4 */
     int32_t max_blocks;            /* 0 = as many as are resident at once (persistent grid); else a cap */
     int32_t keep_batch_order;      /* 0 = schedule the longest pairs first; 1 = batch order */
