@@ -92,6 +92,7 @@ def parse():
                          "very-long workload's checkpointed soft-DTW on --T pairs, lengths times --scale); "
                          "for profiling")
     ap.add_argument("--scale", type=float, default=1.0, help="length scale of the soft / softckpt legs' cycles")
+    ap.add_argument("--store-pairs", type=int, default=0, help="softckpt leg: pairs that keep R beside the checkpoints")
     return ap.parse_args()
 
 
@@ -424,30 +425,36 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
         ws = None
         torch.cuda.empty_cache()
     res["checkpoint_prototype_identical"] = bool(torch.equal(outs["stored"], outs["checkpoint"]))
-    # soft-DTW forward + backward, 8 pairs, checkpointed (64 bands of R per group)
+    # soft-DTW forward + backward, 8 pairs, column checkpoints (stored R would
+    # take ~390 GB); then with as many pairs keeping R as the free memory holds
     gamma = 0.1
-    opt = api.options(dir_mode=1)
-    ws = api.Workspace(dev)
-    w = None                                   # Eq. 7's 1 / N_k (the library's default)
-    api.softdtw_forward(B0, gsub, gamma, opt, ws=ws)
-    api.softdtw_backward(B0, gsub, gamma, w, opt, ws=ws)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True); e2 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    api.softdtw_forward(B0, gsub, gamma, opt, ws=ws)
-    e1.record()
-    api.softdtw_backward(B0, gsub, gamma, w, opt, ws=ws)
-    e2.record()
-    barrier()
     scells = M * int(sub.lengths.sum())
-    f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_ms, b_ms, wgb, st, v_ck, g_ck = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma, api.options(dir_mode=1))
     res["softdtw_checkpoint"] = {"pairs": 8, "gamma": gamma, "checkpoints": "every 16 steps per band", "cells": scells,
                                  "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
                                  "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
-                                 "workspace_gb": ws.buf.numel() / 1e9, "device_status": api.read_status(ws.buf),
+                                 "workspace_gb": wgb, "device_status": st,
                                  "roofline": softckpt_roofline(scells, f_ms, b_ms, sms, ex2, lg2)}
-    del ws
+    # the most pairs whose R fits, and two fewer: the backward runs the stored
+    # pairs' items and the checkpointed pairs' items in two launches, fastest
+    # when each launch's items are resident at once
+    S, _ = store_pairs_that_fit(api, torch, dev, M, gsub)
+    runs = []
+    for s in range(S, max(0, S - 3), -1):
+        f_ms, b_ms, wgb, st, v_h, g_h = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma,
+                                                     api.options(dir_mode=1, store_pairs=s))
+        runs.append({"store_pairs": s, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
+                     "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": wgb,
+                     "device_status": st,
+                     "identical_to_checkpointed": bool(torch.equal(v_h, v_ck) and torch.equal(g_h, g_ck))})
+        del v_h, g_h
+    if runs:
+        best = max(runs, key=lambda r: r["fwd_bwd_gcups"])
+        res["softdtw_checkpoint"]["store_pairs"] = dict(
+            best, note="the longest pairs keep R in HBM (store_pairs), the others column checkpoints; "
+                       "best of the runs listed", runs=runs)
+    del v_ck, g_ck
     torch.cuda.empty_cache()
     if cpu_sample:
         # the oracle (FP64) on a bounded sample: a full pair keeps a 1-byte
@@ -471,7 +478,45 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     return res
 
 
-def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma: float = 0.1, wpb: int = 0):
+def soft_fwd_bwd(api, torch, dev, barrier, B0, gb, gamma, opt):
+    """One warm-up and one timed soft-DTW forward + backward (Eq. 7's default
+    weights 1 / N_k); returns (fwd ms, bwd ms, workspace GB, status, values,
+    gradient).  The workspace is freed before returning."""
+    ws = api.Workspace(dev)
+    api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
+    api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    v = api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
+    e1.record()
+    g = api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
+    e2.record()
+    barrier()
+    out = (e0.elapsed_time(e1), e1.elapsed_time(e2), ws.buf.numel() / 1e9, api.read_status(ws.buf), v, g)
+    del ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def store_pairs_that_fit(api, torch, dev, M, gb, margin_gb: float = 16.0):
+    """The most pairs that can keep R (soft-DTW checkpoint mode's store_pairs)
+    with the workspace inside the device's free memory less a margin."""
+    from paper_2404_12134_gb300 import _abi
+    torch.cuda.empty_cache()
+    free = torch.cuda.mem_get_info(dev)[0] - margin_gb * 1e9
+    best, need = 0, 0
+    for s in range(1, gb.T + 1):
+        n = api.workspace_size(_abi.OP_SOFTDTW, M, gb, api.options(dir_mode=1, store_pairs=s))
+        if n > free:
+            break
+        best, need = s, n
+    return best, need
+
+
+def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma: float = 0.1, wpb: int = 0,
+                 store_pairs: int = 0):
     """The very-long workload's checkpointed soft-DTW alone: T pairs of its
     cycles (lengths times scale) against a prototype of 110,000 x scale
     samples (the clean base; untimed), forward + backward with recomputation,
@@ -480,27 +525,14 @@ def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma
     M = int(round(synth.PROTO_LEN[4] * scale))
     gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
     B0 = torch.from_numpy(synth.clean_prototype(b, M)).to(dev)
-    opt = api.options(dir_mode=1, warps_per_block=wpb)
-    ws = api.Workspace(dev)
-    api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
-    api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    api.softdtw_forward(B0, gb, gamma, opt, ws=ws)
-    e1.record()
-    api.softdtw_backward(B0, gb, gamma, None, opt, ws=ws)
-    e2.record()
-    barrier()
+    opt = api.options(dir_mode=1, warps_per_block=wpb, store_pairs=store_pairs)
+    f_ms, b_ms, wgb, st, _, _ = soft_fwd_bwd(api, torch, dev, barrier, B0, gb, gamma, opt)
     cells = M * int(b.lengths.sum())
-    f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    res = {"pairs": b.T, "M": M, "gamma": gamma, "cells": cells, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
-           "fwd_bwd_gcups": cells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": ws.buf.numel() / 1e9,
-           "device_status": api.read_status(ws.buf),
+    res = {"pairs": b.T, "M": M, "gamma": gamma, "cells": cells, "store_pairs": store_pairs, "fwd_ms": f_ms,
+           "bwd_incl_recompute_ms": b_ms, "fwd_bwd_gcups": cells / ((f_ms + b_ms) * 1e-3) / 1e9,
+           "workspace_gb": wgb, "device_status": st,
            "roofline": softckpt_roofline(cells, f_ms, b_ms, torch.cuda.get_device_properties(dev).multi_processor_count,
                                          None, None)}
-    del ws
     torch.cuda.empty_cache()
     return res
 
@@ -892,7 +924,7 @@ def run_gpu(args):
     if args.leg == "softckpt":
         def sync():
             torch.cuda.synchronize()
-        res = softckpt_leg(api, torch, dev, sync, T=min(args.T, 32), scale=args.scale)
+        res = softckpt_leg(api, torch, dev, sync, T=min(args.T, 32), scale=args.scale, store_pairs=args.store_pairs)
         if rank == 0:
             print(json.dumps({"leg": "softckpt", "softdtw_checkpoint": res}), flush=True)
         return 0

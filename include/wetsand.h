@@ -119,7 +119,18 @@ typedef struct wts_options {
                                       workspace; faster where the code-writing DP outruns the counting one
                                       (wts_autotune tries both when the workspace allows).
                                       anomaly_score_noalloc always counts inside the DP. */
-    int32_t reserved[4];
+    int32_t store_pairs;           /* soft-DTW with dir_mode = 1 and no band (column checkpoints): the first
+                                      store_pairs pairs of the longest-first order keep every R value in the
+                                      workspace, as dir_mode = 0 does, and only the others keep column
+                                      checkpoints, so the backward recomputes R for those pairs only.  0 = none;
+                                      values >= T store every pair.  Values, gradients and the workspace's
+                                      other parts are the same bit for bit; the workspace grows by
+                                      (R - checkpoint) bytes of the stored pairs (wts_workspace_size).  For
+                                      batches whose whole R (4 bytes per cell) exceeds the device's memory:
+                                      the checkpoints take about 0.3 bytes per cell, and the memory left
+                                      can hold R of some pairs instead of recomputing it.  Non-zero with
+                                      any other operation or mode is WTS_EINVAL. */
+    int32_t reserved[3];
 } wts_options;
 
 /* Values of wts_options.cost_kind. */

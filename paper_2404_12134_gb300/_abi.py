@@ -55,7 +55,8 @@ class wts_options(ctypes.Structure):
         ("band", ctypes.c_double),
         ("cost_kind", ctypes.c_int32),
         ("score_via_codes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("store_pairs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

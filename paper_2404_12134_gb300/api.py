@@ -59,12 +59,14 @@ class Batch:
 
 def options(rows_per_thread=0, warps_per_block=0, max_blocks=0, keep_batch_order=0, dir_mode=0,
             ckpt_bands=0, spin_limit=0, fault_skip_handoff=0, band=0.0, cost_kind=0,
-            score_via_codes=0) -> wts_options:
+            score_via_codes=0, store_pairs=0) -> wts_options:
     """Launch and method options (see wts_options in include/wetsand.h); band > 0
     is the Sakoe-Chiba width (Table I) for the DTW operations; cost_kind 1 takes
     the l2 norm as the local cost instead of its square (Sec. 3.2);
-    score_via_codes 1 makes anomaly_score walk stored codes for |pi|."""
+    score_via_codes 1 makes anomaly_score walk stored codes for |pi|;
+    store_pairs keeps R of the longest pairs in soft-DTW's checkpoint mode."""
     o = wts_options()
+    o.store_pairs = store_pairs
     o.score_via_codes = score_via_codes
     o.band = float(band)
     o.cost_kind = cost_kind

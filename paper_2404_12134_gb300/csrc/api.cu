@@ -129,6 +129,7 @@ int check_opt(const wts_options* opt, int D)
     if (opt->cost_kind != WTS_COST_SQEUCLID && opt->cost_kind != WTS_COST_L2)
         return fail(WTS_EINVAL, "cost_kind must be 0 (squared l2) or 1 (l2 norm), got %d", opt->cost_kind);
     if (opt->score_via_codes != 0 && opt->score_via_codes != 1) return fail(WTS_EINVAL, "score_via_codes must be 0 or 1");
+    if (opt->store_pairs < 0) return fail(WTS_EINVAL, "store_pairs must be >= 0");
     return WTS_OK;
 }
 
@@ -189,6 +190,21 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->BR = 32 * L->R;
     L->M = M;
     const int64_t* o = Y->offsets_host;
+    // soft-DTW column checkpoints: the first store_pairs pairs of the
+    // longest-first order keep R (the setup kernel takes the same ranks)
+    std::vector<char> keep_r;
+    if (opt && opt->store_pairs) {
+        if (op != kOpSoft || opt->dir_mode != 1 || opt->band > 0)
+            return fail(WTS_EINVAL, "store_pairs applies to soft-DTW with dir_mode = 1 and no band");
+        L->store_pairs = opt->store_pairs < L->P ? opt->store_pairs : L->P;
+        std::vector<int> idx(L->P);
+        for (int p = 0; p < L->P; ++p) idx[p] = p;
+        std::sort(idx.begin(), idx.end(), [&](int q, int p) {
+            return longer_first(M * (o[q + 1] - o[q]), q, M * (o[p + 1] - o[p]), p);
+        });
+        keep_r.assign(L->P, 0);
+        for (int r = 0; r < L->store_pairs; ++r) keep_r[idx[r]] = 1;
+    }
     int64_t items = 0, h = 0, dw = 0, rs = 0;
     for (int p = 0; p < L->P; ++p) {
         int64_t Mp, Np;
@@ -222,10 +238,11 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
             // two buffers of G bands (with a band: one group's R is read while
             // the next group's is recomputed)
             const int64_t G = (opt && opt->dir_mode == 1) ? (opt->ckpt_bands ? opt->ckpt_bands : 16) : 0;
-            if (G > 0 && !(opt->band > 0))
+            if (G > 0 && !(opt->band > 0) && !(L->store_pairs && keep_r[p]))
                 rs += nb * band_ckcol_floats(Np, L->R);
             else
-                rs += pair_rstore_floats(G > 0 ? (2 * G < nb ? 2 * G : nb) : nb, Np, L->R);
+                rs += pair_rstore_floats(G > 0 && !(L->store_pairs && keep_r[p]) ? (2 * G < nb ? 2 * G : nb) : nb,
+                                         Np, L->R);
         }
     }
     if (items >= ((int64_t)1 << 31)) return fail(WTS_EINVAL, "too many work items");
@@ -333,6 +350,7 @@ int prepare(const Layout& L, char* ws, const float* B, const wts_batch* Y, const
     sp.sort = (opt && opt->keep_batch_order) ? 0 : 1;
     sp.group_bands = L.group_bands;
     sp.band = opt ? opt->band : 0.0;
+    sp.store_pairs = L.store_pairs;
     {
         Prof pr("setup", st);
         launch_setup(sp, st);
@@ -519,15 +537,17 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     return p;
 }
 
-int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block, int64_t n_items = -1)
+int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block, int64_t n_items = -1,
+              int fused = -1)
 {
     if (n_items < 0) n_items = L.n_items;
+    if (fused < 0) fused = L.soft_fused;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
     const int wpb = (opt && opt->warps_per_block) ? opt->warps_per_block : 4;
     *block = 32 * wpb;
-    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind, L.soft_fused, L.R);
+    const int occ = softdtw_max_blocks_per_sm(L.D, backward, *block, L.banded, L.cost_kind, fused, L.R);
     if (occ < 1) return fail(WTS_ECUDA, "no resident soft-DTW block for D=%d block=%d", L.D, *block);
     int64_t g = (int64_t)occ * di.sms;
     const int64_t need = (n_items + wpb - 1) / wpb;
@@ -1047,7 +1067,37 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward hand-off rows)");
     SoftParams p = soft_params(L, ws, gamma, opt);
     int grid = 0, block = 0;
-    if (L.group_bands == 0 || L.soft_fused) {
+    if (L.soft_fused && L.store_pairs > 0) {
+        // column checkpoints with the first store_pairs pairs of the order
+        // keeping R: their items (the first of the work list; every pair has
+        // the same bands) run the backward that reads R, then the others the
+        // fused backward that recomputes it
+        const int64_t nb = cdiv(M, L.BR);
+        const int64_t k = (int64_t)L.store_pairs * nb;
+        SoftParams a = p;
+        a.fused = 0;
+        a.n_items = (int)k;
+        a.item_base = 0;
+        if ((rc = soft_grid(L, 1, opt, &grid, &block, k, 0))) return rc;
+        {
+            Prof pr("softdtw_bwd", st);
+            e = launch_softdtw_bwd(L.D, a, grid, block, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
+        if (k < L.n_items) {
+            SoftParams b = p;
+            b.n_items = (int)(L.n_items - k);
+            b.item_base = (int)k;
+            e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
+            if ((rc = soft_grid(L, 1, opt, &grid, &block, b.n_items))) return rc;
+            {
+                Prof pr("softdtw_bwd", st);
+                e = launch_softdtw_bwd(L.D, b, grid, block, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
+        }
+    } else if (L.group_bands == 0 || L.soft_fused) {
         // R stored, or (checkpoint mode without a band) recomputed inside
         // each band's warp from the column checkpoints: one launch
         if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;

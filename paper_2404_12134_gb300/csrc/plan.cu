@@ -79,10 +79,19 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
             h = pair_hbuf_slots(nb, N);
             if (sp.op == kOpAlign || sp.op == kOpDba || sp.op == kOpSubdtw)
                 dw = pair_dir_words(sp.group_bands > 0 ? min((int64_t)sp.group_bands, nb) : nb, N, sp.R);
-            if (sp.op == kOpSoft)      // checkpoint mode: column checkpoints, or (band) two R buffers of groups
-                rs = sp.group_bands <= 0 ? pair_rstore_floats(nb, N, sp.R)
-                     : sp.band > 0       ? pair_rstore_floats(min(2 * (int64_t)sp.group_bands, nb), N, sp.R)
-                                         : nb * band_ckcol_floats(N, sp.R);
+            if (sp.op == kOpSoft) {    // checkpoint mode: column checkpoints, or (band) two R buffers of groups
+                if (sp.store_pairs > 0) {
+                    // column checkpoints, but the first store_pairs pairs of the
+                    // longest-first order keep R (the rank as in pass 2)
+                    int rank = 0;
+                    for (int q = 0; q < P; ++q)
+                        rank += longer_first(M * (sp.offsets[q + 1] - sp.offsets[q]), q, M * N, p);
+                    pd.keep_r = rank < sp.store_pairs ? 1 : 0;
+                }
+                rs = sp.group_bands <= 0 || pd.keep_r ? pair_rstore_floats(nb, N, sp.R)
+                     : sp.band > 0                    ? pair_rstore_floats(min(2 * (int64_t)sp.group_bands, nb), N, sp.R)
+                                                      : nb * band_ckcol_floats(N, sp.R);
+            }
         }
         int64_t eh, ed, er;
         int64_t th = block_exclusive_scan(h, &eh);
@@ -102,10 +111,7 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
         if (!sp.sort) { sp.order[p] = p; continue; }
         const int64_t cp = (int64_t)sp.pairs[p].M * sp.pairs[p].N;
         int rank = 0;
-        for (int q = 0; q < P; ++q) {
-            const int64_t cq = (int64_t)sp.pairs[q].M * sp.pairs[q].N;
-            rank += (cq > cp) || (cq == cp && q < p);
-        }
+        for (int q = 0; q < P; ++q) rank += longer_first((int64_t)sp.pairs[q].M * sp.pairs[q].N, q, cp, p);
         sp.order[rank] = p;
     }
     __syncthreads();

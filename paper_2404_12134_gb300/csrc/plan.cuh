@@ -62,6 +62,7 @@ struct Layout {
     int cost_kind = 0;    // local cost: 0 squared l2, 1 the l2 norm (DTW kernels with R = 16)
     int nseg = 0;         // segments of the segmented backtrack (codes stored, not Sub-DTW)
     int soft_fused = 0;   // soft-DTW checkpoint mode without a band: column checkpoints, fused backward
+    int store_pairs = 0;  // soft_fused: the first store_pairs pairs of the longest-first order keep R
     size_t off_seg = 0;
 
     size_t off_plen = 0, off_rstore = 0, off_gpart = 0, off_ebuf = 0, off_pcost = 0;
@@ -82,7 +83,15 @@ struct SetupParams {
     int sort;                  // 1: order longest-first, 0: identity
     int group_bands;           // > 0: directions for only this many bands per pair (checkpoint mode)
     double band;               // Sakoe-Chiba width (0 = none): band_bound = floor(band * M * N)
+    int store_pairs;           // soft-DTW column checkpoints: pairs of rank < store_pairs keep R instead
 };
+
+// Rank of pair p in the longest-first order (cells descending, ties by index),
+// the order of the work list.
+__host__ __device__ inline bool longer_first(int64_t cells_q, int q, int64_t cells_p, int p)
+{
+    return cells_q > cells_p || (cells_q == cells_p && q < p);
+}
 
 // floor(band * M * N) in double, as the host validation and the oracle take it
 __host__ __device__ inline int64_t band_bound_of(double band, int64_t M, int64_t N)

@@ -726,9 +726,10 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
         item = __shfl_sync(FULL, item, 0);
         if (item >= n_all) break;
         if (ld_volatile(&p.hdr->abort)) break;
-        if (BWD && item >= p.n_items) {
+        item += p.item_base;
+        if (BWD && item >= p.item_base + p.n_items) {
             // recompute of the next group up, beside this group's backward
-            const int r = item - p.n_items;
+            const int r = item - p.item_base - p.n_items;
             const int qr = r / p.rec_band_cnt, kr = r % p.rec_band_cnt;
             const PairDesc pr = p.pairs[p.order[qr]];
             fwd_band<D, R, BANDED, COST>(p, pr, p.rec_band_lo + kr, lane, p.rec_rbuf_band0 + kr, true, true);
@@ -758,7 +759,7 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
         } else {
             const int band = p.band_cnt > 0 ? p.band_lo + k : k;
             fwd_band<D, R, BANDED, COST>(p, pd, band, lane, band - p.band_lo + p.rbuf_band0, p.recompute != 0,
-                                         p.store_r != 0);
+                                         p.store_r != 0 || pd.keep_r != 0);
         }
     }
 }

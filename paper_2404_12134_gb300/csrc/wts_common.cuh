@@ -38,6 +38,8 @@ struct PairDesc {
     int64_t hbuf_off;    // first slot of this pair's hand-off rows ((nbands-1) * N slots)
     int64_t aux_off;     // first element of per-pair auxiliary storage (R store)
     int64_t band_bound;  // Sakoe-Chiba band: cell (i, j) kept when |i N - j M| <= band_bound; -1 = no band
+    int32_t keep_r;      // soft-DTW checkpoint mode: this pair's R is stored (not column checkpoints)
+    int32_t spare;
 };
 
 // Header at the start of every workspace.

@@ -244,3 +244,45 @@ def test_softdtw_checkpoint_workspace(lib):
     cells = 10000 * 20000
     assert stored >= 4 * cells and ck < stored / 10 and ck > 4 * cells * 9 / (8 * 16) * 0.9
     assert banded < stored / 4
+
+
+def test_softdtw_store_pairs_workspace(lib):
+    """store_pairs (column checkpoints, no band): the first pairs of the
+    longest-first order keep R; the workspace grows by exactly their R minus
+    their checkpoints, from dir_mode = 1's size (none kept) to dir_mode = 0's
+    (all kept); any other use is rejected."""
+    lengths = [9000, 11000, 5000]
+    M = 10000
+    b, offs = _batch(lengths, d=1)
+    rc, stored = _size(lib, _abi.OP_SOFTDTW, M, b)
+    o = _abi.wts_options()
+    o.dir_mode = 1
+    rc1, ck = _size(lib, _abi.OP_SOFTDTW, M, b, o)
+    assert rc == rc1 == 0
+    nb = -(-M // 256)                                  # bands of 32 lanes x 8 rows
+
+    def extra(n):                                      # floats: R minus column checkpoints of one pair
+        return nb * (n + 31) * 32 * 8 - nb * (-(-(n + 31) // 16)) * 9 * 32
+
+    want = {0: 0, 1: extra(11000), 2: extra(11000) + extra(9000), 3: sum(extra(n) for n in lengths)}
+    for S, dx in want.items():
+        o.store_pairs = S
+        rc, sz = _size(lib, _abi.OP_SOFTDTW, M, b, o)
+        assert rc == 0
+        assert abs(sz - ck - 4 * dx) < 256, (S, sz - ck, 4 * dx)
+    assert sz == stored
+    o.store_pairs = 7                                  # more than T: every pair
+    assert _size(lib, _abi.OP_SOFTDTW, M, b, o) == (0, stored)
+    # the Adam and L-BFGS drivers take the same option
+    assert _size(lib, _abi.OP_SOFTDTW_ADAM, M, b, o)[0] == 0
+    o.store_pairs = -1
+    assert _size(lib, _abi.OP_SOFTDTW, M, b, o)[0] == _abi.WTS_EINVAL
+    o.store_pairs = 1
+    o.dir_mode = 0
+    assert _size(lib, _abi.OP_SOFTDTW, M, b, o)[0] == _abi.WTS_EINVAL
+    o.dir_mode = 1
+    o.band = 0.6
+    assert _size(lib, _abi.OP_SOFTDTW, M, b, o)[0] == _abi.WTS_EINVAL
+    o.band = 0.0
+    assert _size(lib, _abi.OP_DTW_ALIGN, M, b, o)[0] == _abi.WTS_EINVAL
+    assert b"store_pairs" in lib.wts_last_error()

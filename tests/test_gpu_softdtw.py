@@ -184,6 +184,45 @@ def test_checkpoint_mode_identical(wts, G):
     assert s_ck <= s_st and (G > 1 or s_ck < s_st)
 
 
+@pytest.mark.parametrize("M,d,cost", [(1100, 1, 0), (1024, 1, 0), (700, 3, 0), (520, 2, 1)])
+def test_store_pairs_identical(wts, M, d, cost):
+    """Column checkpoints with the longest pairs keeping R (store_pairs): the
+    stored pairs run the backward that reads R, the others the fused one that
+    recomputes it, in two launches.  Values and gradients equal, bit for bit,
+    those with every R stored and with every pair checkpointed; with one
+    channel and M a multiple of 8 (1024) the first launch is the one-channel
+    backward without checked columns."""
+    B, b = _case(70 + M, M, [900, 1300, 77, 1300, 31], d)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    Bt = torch.from_numpy(B).cuda()
+    w = torch.from_numpy((1.0 / b.lengths).astype(np.float32)).cuda()
+    res = []
+    for opt in (wts.options(cost_kind=cost), wts.options(dir_mode=1, cost_kind=cost),
+                wts.options(dir_mode=1, cost_kind=cost, store_pairs=1),
+                wts.options(dir_mode=1, cost_kind=cost, store_pairs=3),
+                wts.options(dir_mode=1, cost_kind=cost, store_pairs=5)):
+        ws = wts.Workspace()
+        v = wts.softdtw_forward(Bt, gb, 0.1, opt, ws=ws)
+        g = wts.softdtw_backward(Bt, gb, 0.1, w, opt, ws=ws)
+        assert wts.read_status(ws.buf) == 0
+        res.append((v, g))
+    for v, g in res[1:]:
+        assert torch.equal(v, res[0][0]) and torch.equal(g, res[0][1])
+
+
+def test_adam_barycenter_store_pairs_identical(wts):
+    """The library's Adam loop with two of five pairs keeping R beside column
+    checkpoints reaches the barycenter of the stored mode, bit for bit."""
+    b = synth.config_batch(2, scale=0.06, T=5)
+    gb = wts.Batch.from_numpy(b.data, b.offsets)
+    M = 700
+    B0 = wts.euclid_mean(gb, M)
+    Bs, hs = wts.softdtw_barycenter(gb, M, 0.1, steps=5, lr=2e-2, init=B0)
+    Bh, hh = wts.softdtw_barycenter(gb, M, 0.1, steps=5, lr=2e-2, init=B0,
+                                    opts=wts.options(dir_mode=1, store_pairs=2))
+    assert torch.equal(Bs, Bh) and torch.equal(hs, hh)
+
+
 @pytest.mark.parametrize("dir_mode", [0, 1])
 @pytest.mark.parametrize("M", [8, 256, 776, 1000, 1024])
 def test_aligned_rows_backward_identical_to_checked(wts, M, dir_mode):
