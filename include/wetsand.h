@@ -120,7 +120,8 @@ typedef struct wts_options {
                                       (wts_autotune tries both when the workspace allows).
                                       anomaly_score_noalloc always counts inside the DP. */
     int32_t store_pairs;           /* soft-DTW with dir_mode = 1 and no band (column checkpoints): the first
-                                      store_pairs pairs of the longest-first order keep every R value in the
+                                      store_pairs pairs of the work list (longest first, or the batch order
+                                      with keep_batch_order) keep every R value in the
                                       workspace, as dir_mode = 0 does, and only the others keep column
                                       checkpoints, so the backward recomputes R for those pairs only.  0 = none;
                                       values >= T store every pair.  Values, gradients and the workspace's

@@ -190,8 +190,9 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
     L->BR = 32 * L->R;
     L->M = M;
     const int64_t* o = Y->offsets_host;
-    // soft-DTW column checkpoints: the first store_pairs pairs of the
-    // longest-first order keep R (the setup kernel takes the same ranks)
+    // soft-DTW column checkpoints: the first store_pairs pairs of the work
+    // list's order (longest first, or the batch order) keep R; the setup
+    // kernel takes the same ranks
     std::vector<char> keep_r;
     if (opt && opt->store_pairs) {
         if (op != kOpSoft || opt->dir_mode != 1 || opt->band > 0)
@@ -199,9 +200,10 @@ int compute_layout(int op, int64_t M, const wts_batch* Y, const wts_options* opt
         L->store_pairs = opt->store_pairs < L->P ? opt->store_pairs : L->P;
         std::vector<int> idx(L->P);
         for (int p = 0; p < L->P; ++p) idx[p] = p;
-        std::sort(idx.begin(), idx.end(), [&](int q, int p) {
-            return longer_first(M * (o[q + 1] - o[q]), q, M * (o[p + 1] - o[p]), p);
-        });
+        if (!opt->keep_batch_order)
+            std::sort(idx.begin(), idx.end(), [&](int q, int p) {
+                return longer_first(M * (o[q + 1] - o[q]), q, M * (o[p + 1] - o[p]), p);
+            });
         keep_r.assign(L->P, 0);
         for (int r = 0; r < L->store_pairs; ++r) keep_r[idx[r]] = 1;
     }

@@ -82,10 +82,13 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams sp)
             if (sp.op == kOpSoft) {    // checkpoint mode: column checkpoints, or (band) two R buffers of groups
                 if (sp.store_pairs > 0) {
                     // column checkpoints, but the first store_pairs pairs of the
-                    // longest-first order keep R (the rank as in pass 2)
-                    int rank = 0;
-                    for (int q = 0; q < P; ++q)
-                        rank += longer_first(M * (sp.offsets[q + 1] - sp.offsets[q]), q, M * N, p);
+                    // work list's order keep R (the rank as in pass 2)
+                    int rank = p;
+                    if (sp.sort) {
+                        rank = 0;
+                        for (int q = 0; q < P; ++q)
+                            rank += longer_first(M * (sp.offsets[q + 1] - sp.offsets[q]), q, M * N, p);
+                    }
                     pd.keep_r = rank < sp.store_pairs ? 1 : 0;
                 }
                 rs = sp.group_bands <= 0 || pd.keep_r ? pair_rstore_floats(nb, N, sp.R)

@@ -273,6 +273,12 @@ def test_softdtw_store_pairs_workspace(lib):
     assert sz == stored
     o.store_pairs = 7                                  # more than T: every pair
     assert _size(lib, _abi.OP_SOFTDTW, M, b, o) == (0, stored)
+    # in batch order (keep_batch_order) the first pairs of the batch keep R
+    o.store_pairs = 1
+    o.keep_batch_order = 1
+    rc, sz = _size(lib, _abi.OP_SOFTDTW, M, b, o)
+    assert rc == 0 and abs(sz - ck - 4 * extra(9000)) < 256
+    o.keep_batch_order = 0
     # the Adam and L-BFGS drivers take the same option
     assert _size(lib, _abi.OP_SOFTDTW_ADAM, M, b, o)[0] == 0
     o.store_pairs = -1

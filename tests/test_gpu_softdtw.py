@@ -189,7 +189,8 @@ def test_store_pairs_identical(wts, M, d, cost):
     """Column checkpoints with the longest pairs keeping R (store_pairs): the
     stored pairs run the backward that reads R, the others the fused one that
     recomputes it, in two launches.  Values and gradients equal, bit for bit,
-    those with every R stored and with every pair checkpointed; with one
+    those with every R stored and with every pair checkpointed, also in batch
+    order (keep_batch_order: the batch's first pairs keep R); with one
     channel and M a multiple of 8 (1024) the first launch is the one-channel
     backward without checked columns."""
     B, b = _case(70 + M, M, [900, 1300, 77, 1300, 31], d)
@@ -200,6 +201,7 @@ def test_store_pairs_identical(wts, M, d, cost):
     for opt in (wts.options(cost_kind=cost), wts.options(dir_mode=1, cost_kind=cost),
                 wts.options(dir_mode=1, cost_kind=cost, store_pairs=1),
                 wts.options(dir_mode=1, cost_kind=cost, store_pairs=3),
+                wts.options(dir_mode=1, cost_kind=cost, store_pairs=2, keep_batch_order=1),
                 wts.options(dir_mode=1, cost_kind=cost, store_pairs=5)):
         ws = wts.Workspace()
         v = wts.softdtw_forward(Bt, gb, 0.1, opt, ws=ws)
