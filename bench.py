@@ -442,15 +442,21 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     S, _ = store_pairs_that_fit(api, torch, dev, M, gsub)
     runs = []
     for s in range(S, max(0, S - 3), -1):
-        f_ms, b_ms, wgb, st, v_h, g_h = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma,
-                                                     api.options(dir_mode=1, store_pairs=s))
+        try:
+            f_ms, b_ms, wgb, st, v_h, g_h = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma,
+                                                         api.options(dir_mode=1, store_pairs=s))
+        except torch.cuda.OutOfMemoryError:
+            torch.cuda.empty_cache()
+            runs.append({"store_pairs": s, "skipped": "the workspace did not fit"})
+            continue
         runs.append({"store_pairs": s, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
                      "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": wgb,
                      "device_status": st,
                      "identical_to_checkpointed": bool(torch.equal(v_h, v_ck) and torch.equal(g_h, g_ck))})
         del v_h, g_h
-    if runs:
-        best = max(runs, key=lambda r: r["fwd_bwd_gcups"])
+    done = [r for r in runs if "fwd_bwd_gcups" in r]
+    if done:
+        best = max(done, key=lambda r: r["fwd_bwd_gcups"])
         res["softdtw_checkpoint"]["store_pairs"] = dict(
             best, note="the longest pairs keep R in HBM (store_pairs), the others column checkpoints; "
                        "best of the runs listed", runs=runs)
