@@ -37,25 +37,25 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per cell of the code-writing wavefront, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel build on 36 cycles of this workload: (0.1479 + 5.6418)e9 bytes /
+# kernel build on 36 cycles of this workload: (0.16208 + 5.64213)e9 bytes /
 # 2.2029e10 cells.  Traffic grows in proportion to the cells (codes +
 # hand-off rows).
-WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.1479 + 5.6418) * 1e9 / 2.2029e10
+WAVEFRONT_DIRS_DRAM_BYTES_PER_CELL = (0.16208 + 5.64213) * 1e9 / 2.2029e10
 # DRAM bytes (read + write) per cell of soft-DTW forward + backward, from one
 # ncu capture of both kernels (the same build) on the soft-DTW workload with
 # its cycles cut to an eighth (64 pairs, the benchmark's occupancy):
-# (0.0163 + 3.2686 + 3.3679 + 0.0536)e9 bytes / 7.9029e8 cells (stored R plus
+# (0.01512 + 3.26850 + 3.36838 + 0.05043)e9 bytes / 7.9029e8 cells (stored R plus
 # hand-off rows, in proportion to cells; the skew margin, 2.5 % of a band at
 # that length, is 0.3 % at full length).
-SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.0163 + 3.2686 + 3.3679 + 0.0536) * 1e9 / 7.9029e8
+SOFT_FWD_BWD_DRAM_BYTES_PER_CELL = (0.01512 + 3.26850 + 3.36838 + 0.05043) * 1e9 / 7.9029e8
 # Warp instructions per cell of the checkpointed soft-DTW passes (column
 # checkpoints, recompute fused into the backward), from one ncu capture
 # (smsp__inst_executed.sum) of the same build on the very-long workload's
-# 8 pairs cut to a quarter (5.842e9 cells): forward 4.9542e9, backward
-# 1.21216e10.  Both passes are bound by the issue rate (one warp instruction
+# 8 pairs cut to a quarter (5.842e9 cells): forward 4.9229e9, backward
+# 1.20786e10.  Both passes are bound by the issue rate (one warp instruction
 # per scheduler per cycle), not by a pipe or by DRAM.
-SOFT_CKPT_FWD_INSTR_PER_CELL = 4.9542e9 / 5.842045e9
-SOFT_CKPT_BWD_INSTR_PER_CELL = 1.21216e10 / 5.842045e9
+SOFT_CKPT_FWD_INSTR_PER_CELL = 4.9229e9 / 5.842045e9
+SOFT_CKPT_BWD_INSTR_PER_CELL = 1.20786e10 / 5.842045e9
 
 
 def softckpt_roofline(cells: int, fwd_ms: float, bwd_ms: float, sms: int, ex2: float | None, lg2: float | None):
@@ -386,7 +386,12 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     110,000 (medoid of a seeded 8-cycle subset, resampled; untimed).  DBA with
     every code stored (~95 GB) against checkpoint mode (band rows kept, codes
     recomputed 16 bands at a time), and soft-DTW forward + backward on 8 of the
-    pairs with checkpointing (stored R would take ~390 GB)."""
+    pairs with checkpointing (stored R would take ~390 GB), first, while the
+    device memory is least fragmented."""
+    import gc
+    api._default_ws.clear()              # earlier legs' default workspaces: the soft-DTW runs size by free memory
+    gc.collect()
+    torch.cuda.empty_cache()
     b = synth.config_batch(4)
     M = synth.PROTO_LEN[4]
     gb = api.Batch.from_numpy(b.data, b.offsets, device=dev)
@@ -397,6 +402,46 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     k = int(idx)
     B0 = api.resample(gsub.data[int(sub.offsets[k]):int(sub.offsets[k + 1])], M)
     res = {"workload": "32 cycles x 3 ch FP32, pre-gap N ~ U(100k,120k), 2% gaps, M=110000", "cells_per_iter": cells}
+    # soft-DTW forward + backward, 8 pairs, column checkpoints (stored R would
+    # take ~390 GB); then with as many pairs keeping R as the free memory holds
+    gamma = 0.1
+    scells = M * int(sub.lengths.sum())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_ms, b_ms, wgb, st, v_ck, g_ck = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma, api.options(dir_mode=1))
+    res["softdtw_checkpoint"] = {"pairs": 8, "gamma": gamma, "checkpoints": "every 16 steps per band", "cells": scells,
+                                 "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
+                                 "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
+                                 "workspace_gb": wgb, "device_status": st,
+                                 "roofline": softckpt_roofline(scells, f_ms, b_ms, sms, ex2, lg2)}
+    # the most pairs whose R fits, and two fewer: the backward runs the stored
+    # pairs' items and the checkpointed pairs' items in two launches, fastest
+    # when each launch's items are resident at once
+    S, _ = store_pairs_that_fit(api, torch, dev, M, gsub)
+    free_gb = torch.cuda.mem_get_info(dev)[0] / 1e9
+    held_gb = (torch.cuda.memory_allocated(dev) / 1e9, torch.cuda.memory_reserved(dev) / 1e9)
+    runs = []
+    for s in range(S, max(0, S - 3), -1):
+        try:
+            f_ms, b_ms, wgb, st, v_h, g_h = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma,
+                                                         api.options(dir_mode=1, store_pairs=s))
+        except torch.cuda.OutOfMemoryError:
+            torch.cuda.empty_cache()
+            runs.append({"store_pairs": s, "skipped": "the workspace did not fit"})
+            continue
+        runs.append({"store_pairs": s, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
+                     "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": wgb,
+                     "device_status": st,
+                     "identical_to_checkpointed": bool(torch.equal(v_h, v_ck) and torch.equal(g_h, g_ck))})
+        del v_h, g_h
+    done = [r for r in runs if "fwd_bwd_gcups" in r]
+    if done:
+        best = max(done, key=lambda r: r["fwd_bwd_gcups"])
+        res["softdtw_checkpoint"]["store_pairs"] = dict(
+            best, note="the longest pairs keep R in HBM (store_pairs), the others column checkpoints; "
+                       "best of the runs listed", runs=runs, free_gb_before=free_gb,
+            torch_allocated_reserved_gb=held_gb)
+    del v_ck, g_ck
+    torch.cuda.empty_cache()
     outs = {}
     from paper_2404_12134_gb300 import _abi
     ws = api.Workspace(dev)
@@ -425,43 +470,6 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
         ws = None
         torch.cuda.empty_cache()
     res["checkpoint_prototype_identical"] = bool(torch.equal(outs["stored"], outs["checkpoint"]))
-    # soft-DTW forward + backward, 8 pairs, column checkpoints (stored R would
-    # take ~390 GB); then with as many pairs keeping R as the free memory holds
-    gamma = 0.1
-    scells = M * int(sub.lengths.sum())
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    f_ms, b_ms, wgb, st, v_ck, g_ck = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma, api.options(dir_mode=1))
-    res["softdtw_checkpoint"] = {"pairs": 8, "gamma": gamma, "checkpoints": "every 16 steps per band", "cells": scells,
-                                 "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
-                                 "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
-                                 "workspace_gb": wgb, "device_status": st,
-                                 "roofline": softckpt_roofline(scells, f_ms, b_ms, sms, ex2, lg2)}
-    # the most pairs whose R fits, and two fewer: the backward runs the stored
-    # pairs' items and the checkpointed pairs' items in two launches, fastest
-    # when each launch's items are resident at once
-    S, _ = store_pairs_that_fit(api, torch, dev, M, gsub)
-    runs = []
-    for s in range(S, max(0, S - 3), -1):
-        try:
-            f_ms, b_ms, wgb, st, v_h, g_h = soft_fwd_bwd(api, torch, dev, barrier, B0, gsub, gamma,
-                                                         api.options(dir_mode=1, store_pairs=s))
-        except torch.cuda.OutOfMemoryError:
-            torch.cuda.empty_cache()
-            runs.append({"store_pairs": s, "skipped": "the workspace did not fit"})
-            continue
-        runs.append({"store_pairs": s, "fwd_ms": f_ms, "bwd_incl_recompute_ms": b_ms,
-                     "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9, "workspace_gb": wgb,
-                     "device_status": st,
-                     "identical_to_checkpointed": bool(torch.equal(v_h, v_ck) and torch.equal(g_h, g_ck))})
-        del v_h, g_h
-    done = [r for r in runs if "fwd_bwd_gcups" in r]
-    if done:
-        best = max(done, key=lambda r: r["fwd_bwd_gcups"])
-        res["softdtw_checkpoint"]["store_pairs"] = dict(
-            best, note="the longest pairs keep R in HBM (store_pairs), the others column checkpoints; "
-                       "best of the runs listed", runs=runs)
-    del v_ck, g_ck
-    torch.cuda.empty_cache()
     if cpu_sample:
         # the oracle (FP64) on a bounded sample: a full pair keeps a 1-byte
         # choice per cell (12 GB of host memory) and takes about a minute on
