@@ -389,7 +389,7 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     pairs with checkpointing (stored R would take ~390 GB), first, while the
     device memory is least fragmented."""
     import gc
-    api._default_ws.clear()              # earlier legs' default workspaces: the soft-DTW runs size by free memory
+    api.release_default_workspaces()     # earlier legs' default workspaces: the soft-DTW runs size by free memory
     gc.collect()
     torch.cuda.empty_cache()
     b = synth.config_batch(4)

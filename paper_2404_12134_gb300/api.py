@@ -113,6 +113,12 @@ class Workspace:
 _default_ws: dict = {}
 
 
+def release_default_workspaces():
+    """Drop the per-device workspaces that calls without an explicit
+    Workspace share (their memory returns to torch's allocator)."""
+    _default_ws.clear()
+
+
 def _ws(ws: Workspace | None, nbytes: int) -> torch.Tensor:
     if ws is None:
         dev = torch.cuda.current_device()
