@@ -539,11 +539,10 @@ SoftParams soft_params(const Layout& L, char* ws, float gamma, const wts_options
     return p;
 }
 
-int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block, int64_t n_items = -1,
-              int fused = -1)
+int soft_grid(const Layout& L, int backward, const wts_options* opt, int* grid, int* block, int64_t n_items = -1)
 {
     if (n_items < 0) n_items = L.n_items;
-    if (fused < 0) fused = L.soft_fused;
+    const int fused = L.soft_fused;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -1069,39 +1068,10 @@ int softdtw_backward(const float* B, int64_t M, const wts_batch* Y, float gamma,
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(backward hand-off rows)");
     SoftParams p = soft_params(L, ws, gamma, opt);
     int grid = 0, block = 0;
-    if (L.soft_fused && L.store_pairs > 0) {
-        // column checkpoints with the first store_pairs pairs of the order
-        // keeping R: their items (the first of the work list; every pair has
-        // the same bands) run the backward that reads R, then the others the
-        // fused backward that recomputes it
-        const int64_t nb = cdiv(M, L.BR);
-        const int64_t k = (int64_t)L.store_pairs * nb;
-        SoftParams a = p;
-        a.fused = 0;
-        a.n_items = (int)k;
-        a.item_base = 0;
-        if ((rc = soft_grid(L, 1, opt, &grid, &block, k, 0))) return rc;
-        {
-            Prof pr("softdtw_bwd", st);
-            e = launch_softdtw_bwd(L.D, a, grid, block, st);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
-        if (k < L.n_items) {
-            SoftParams b = p;
-            b.n_items = (int)(L.n_items - k);
-            b.item_base = (int)k;
-            e = cudaMemsetAsync(ws + L.off_hdr + offsetof(WsHeader, item_counter), 0, sizeof(int), st);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work cursor)");
-            if ((rc = soft_grid(L, 1, opt, &grid, &block, b.n_items))) return rc;
-            {
-                Prof pr("softdtw_bwd", st);
-                e = launch_softdtw_bwd(L.D, b, grid, block, st);
-            }
-            if (e != cudaSuccess) return cuda_fail(e, "soft-DTW backward launch");
-        }
-    } else if (L.group_bands == 0 || L.soft_fused) {
+    if (L.group_bands == 0 || L.soft_fused) {
         // R stored, or (checkpoint mode without a band) recomputed inside
-        // each band's warp from the column checkpoints: one launch
+        // each band's warp from the column checkpoints, the pairs that kept R
+        // (store_pairs) reading it: one launch
         if ((rc = soft_grid(L, 1, opt, &grid, &block))) return rc;
         {
             Prof pr("softdtw_bwd", st);

@@ -726,10 +726,9 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
         item = __shfl_sync(FULL, item, 0);
         if (item >= n_all) break;
         if (ld_volatile(&p.hdr->abort)) break;
-        item += p.item_base;
-        if (BWD && item >= p.item_base + p.n_items) {
+        if (BWD && item >= p.n_items) {
             // recompute of the next group up, beside this group's backward
-            const int r = item - p.item_base - p.n_items;
+            const int r = item - p.n_items;
             const int qr = r / p.rec_band_cnt, kr = r % p.rec_band_cnt;
             const PairDesc pr = p.pairs[p.order[qr]];
             fwd_band<D, R, BANDED, COST>(p, pr, p.rec_band_lo + kr, lane, p.rec_rbuf_band0 + kr, true, true);
@@ -753,9 +752,19 @@ __device__ __forceinline__ void soft_items(const SoftParams& p)
         if (BWD) {
             // bands bottom-up: the whole pair, or the range's last band first
             const int band = p.band_cnt > 0 ? p.band_lo + p.band_cnt - 1 - k : pd.nbands - 1 - k;
-            bwd_band<D, R, BANDED, COST, FUSED, ALIGNED>(p, pd, band, lane,
-                                                         rring_all + (threadIdx.x >> 5) * soft_warp_f4<D, R>(FUSED, BANDED),
-                                                         band - p.band_lo + p.rbuf_band0);
+            float4* wring = rring_all + (threadIdx.x >> 5) * soft_warp_f4<D, R>(FUSED, BANDED);
+            if constexpr (FUSED && !BANDED) {
+                static_assert(soft_warp_f4<D, R>(true, false) >= soft_warp_f4<D, R>(false, false),
+                              "the fused warp's shared memory holds the R ring");
+                // a pair that kept R (store_pairs) beside checkpointed ones: the
+                // backward that reads R, in this warp's part of shared memory
+                // (the fused layout is the larger)
+                if (pd.keep_r) {
+                    bwd_band<D, R, BANDED, COST, false>(p, pd, band, lane, wring, band - p.band_lo + p.rbuf_band0);
+                    continue;
+                }
+            }
+            bwd_band<D, R, BANDED, COST, FUSED, ALIGNED>(p, pd, band, lane, wring, band - p.band_lo + p.rbuf_band0);
         } else {
             const int band = p.band_cnt > 0 ? p.band_lo + k : k;
             fwd_band<D, R, BANDED, COST>(p, pd, band, lane, band - p.band_lo + p.rbuf_band0, p.recompute != 0,

@@ -38,13 +38,10 @@ struct SoftParams {
     // checkpoint mode without a band: column checkpoints instead of R groups.
     // The full forward writes them (ckcol != null), and the backward (fused = 1)
     // recomputes R a few steps at a time inside each band's warp
+    // Pairs whose PairDesc::keep_r is set (store_pairs) keep R instead: the
+    // fused backward runs their items through the backward that reads it.
     float* ckcol;
     int fused;
-    // first item of the launch: with stored pairs beside checkpointed ones
-    // (PairDesc::keep_r, the first pairs of the order), the backward runs the
-    // stored pairs' items [0, k) in one launch and the others [k, ...) in
-    // the fused one; n_items counts the launch's items
-    int item_base;
     long long spin_limit;    // polls before a wait gives up
     int skip_handoff;        // fault injection (tests): producers do not write hand-off rows
     int banded;              // pairs carry a Sakoe-Chiba band (PairDesc::band_bound); items run band-major
