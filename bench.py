@@ -413,9 +413,9 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
                                  "fwd_bwd_gcups": scells / ((f_ms + b_ms) * 1e-3) / 1e9,
                                  "workspace_gb": wgb, "device_status": st,
                                  "roofline": softckpt_roofline(scells, f_ms, b_ms, sms, ex2, lg2)}
-    # the most pairs whose R fits, and two fewer: the backward runs the stored
-    # pairs' items and the checkpointed pairs' items in two launches, fastest
-    # when each launch's items are resident at once
+    # the most pairs whose R fits, and two fewer (the fewer pairs recompute,
+    # the faster the backward, as long as the checkpointed pairs' items and
+    # the stored pairs' items fill the resident warps)
     S, _ = store_pairs_that_fit(api, torch, dev, M, gsub)
     free_gb = torch.cuda.mem_get_info(dev)[0] / 1e9
     held_gb = (torch.cuda.memory_allocated(dev) / 1e9, torch.cuda.memory_reserved(dev) / 1e9)

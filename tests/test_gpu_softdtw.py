@@ -187,8 +187,8 @@ def test_checkpoint_mode_identical(wts, G):
 @pytest.mark.parametrize("M,d,cost", [(1100, 1, 0), (1024, 1, 0), (700, 3, 0), (520, 2, 1)])
 def test_store_pairs_identical(wts, M, d, cost):
     """Column checkpoints with the longest pairs keeping R (store_pairs): the
-    stored pairs run the backward that reads R, the others the fused one that
-    recomputes it, in two launches.  Values and gradients equal, bit for bit,
+    stored pairs' items run the backward that reads R, the others the fused
+    one that recomputes it, in one launch.  Values and gradients equal, bit for bit,
     those with every R stored and with every pair checkpointed, also in batch
     order (keep_batch_order: the batch's first pairs keep R); with one
     channel and M a multiple of 8 (1024) the first launch is the one-channel
