@@ -416,7 +416,7 @@ def long_leg(api, torch, dev, barrier, iters: int = 2, cpu_sample: bool = True, 
     # the most pairs whose R fits, and two fewer (the fewer pairs recompute,
     # the faster the backward, as long as the checkpointed pairs' items and
     # the stored pairs' items fill the resident warps)
-    S, _ = store_pairs_that_fit(api, torch, dev, M, gsub)
+    S, _ = api.store_pairs_for_memory(M, gsub)
     free_gb = torch.cuda.mem_get_info(dev)[0] / 1e9
     held_gb = (torch.cuda.memory_allocated(dev) / 1e9, torch.cuda.memory_reserved(dev) / 1e9)
     runs = []
@@ -512,21 +512,6 @@ def soft_fwd_bwd(api, torch, dev, barrier, B0, gb, gamma, opt):
     del ws
     torch.cuda.empty_cache()
     return out
-
-
-def store_pairs_that_fit(api, torch, dev, M, gb, margin_gb: float = 16.0):
-    """The most pairs that can keep R (soft-DTW checkpoint mode's store_pairs)
-    with the workspace inside the device's free memory less a margin."""
-    from paper_2404_12134_gb300 import _abi
-    torch.cuda.empty_cache()
-    free = torch.cuda.mem_get_info(dev)[0] - margin_gb * 1e9
-    best, need = 0, 0
-    for s in range(1, gb.T + 1):
-        n = api.workspace_size(_abi.OP_SOFTDTW, M, gb, api.options(dir_mode=1, store_pairs=s))
-        if n > free:
-            break
-        best, need = s, n
-    return best, need
 
 
 def softckpt_leg(api, torch, dev, barrier, T: int = 8, scale: float = 1.0, gamma: float = 0.1, wpb: int = 0,

@@ -132,6 +132,31 @@ def workspace_size(op: int, M: int, batch: Batch, opts=None) -> int:
     return n.value
 
 
+def store_pairs_for_memory(M: int, batch: Batch, free_bytes: int | None = None, margin_bytes: int = 16 * 10**9,
+                           opts=None) -> tuple[int, int]:
+    """For soft-DTW's checkpoint mode (dir_mode = 1, no band): the most
+    pairs that can keep R (wts_options.store_pairs) with the workspace
+    within free_bytes (default: the current device's free memory) less
+    margin_bytes.  Returns (store_pairs, workspace bytes); (0, 0) if even one
+    stored pair does not fit.  opts supplies the other options (its dir_mode
+    and store_pairs are overridden)."""
+    if free_bytes is None:
+        torch.cuda.empty_cache()
+        free_bytes = torch.cuda.mem_get_info()[0]
+    o = wts_options()
+    if opts is not None:
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(o))
+    o.dir_mode = 1
+    best, need = 0, 0
+    for s in range(1, batch.T + 1):
+        o.store_pairs = s
+        n = workspace_size(_abi.OP_SOFTDTW, M, batch, o)
+        if n > free_bytes - margin_bytes:
+            break
+        best, need = s, n
+    return best, need
+
+
 def read_status(buf: torch.Tensor) -> int:
     s = ctypes.c_int32(0)
     check(_abi.load().wts_read_status(buf.data_ptr(), _stream(), ctypes.byref(s)))

@@ -292,3 +292,39 @@ def test_softdtw_store_pairs_workspace(lib):
     o.band = 0.0
     assert _size(lib, _abi.OP_DTW_ALIGN, M, b, o)[0] == _abi.WTS_EINVAL
     assert b"store_pairs" in lib.wts_last_error()
+
+
+def test_store_pairs_for_memory(lib):
+    """api.store_pairs_for_memory sizes soft-DTW's store_pairs by the free
+    device memory: the most pairs whose workspace (the library's own size)
+    fits in free memory less the margin."""
+    from paper_2404_12134_gb300 import api
+    lengths = [9000, 11000, 5000, 10000]
+    M = 10000
+    _, offs = _batch(lengths, d=3)
+
+    class FakeBatch:                                   # host-only sizing: no device data is touched
+        T = len(lengths)
+
+        def c(self):
+            b = _abi.wts_batch()
+            b.data = 16
+            b.offsets = 16
+            b.offsets_host = offs.ctypes.data
+            b.T = self.T
+            b.d = 3
+            return b
+
+    sizes = [api.workspace_size(_abi.OP_SOFTDTW, M, FakeBatch(), api.options(dir_mode=1, store_pairs=s))
+             for s in range(5)]
+    assert sizes == sorted(sizes) and sizes[0] < sizes[1]
+    margin = 16 * 10**9
+    for free, want in ((sizes[0] + 1, 0), (sizes[2] + margin, 2), (sizes[2] + margin - 1, 1),
+                       (sizes[4] + margin + 10**9, 4)):
+        got, need = api.store_pairs_for_memory(M, FakeBatch(), free_bytes=free, margin_bytes=margin,
+                                               opts=api.options(cost_kind=1, dir_mode=0))
+        assert got == want, (free, got, want)
+        want_need = api.workspace_size(_abi.OP_SOFTDTW, M, FakeBatch(),
+                                       api.options(cost_kind=1, dir_mode=1, store_pairs=want)) if want else 0
+        assert need == want_need
+

@@ -35,45 +35,3 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["metric"] == "dtw_gcups_dba_iteration" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
-
-
-def test_store_pairs_that_fit_picks_the_most_that_fit():
-    """The bench sizes soft-DTW's store_pairs by free device memory: the most
-    pairs whose workspace (the library's own size) fits, less the margin."""
-    import ctypes
-    import types
-    sys.path.insert(0, ROOT)
-    import bench
-    from paper_2404_12134_gb300 import _abi, api, build
-    build.build()
-    lib = _abi.load()
-    lengths = [9000, 11000, 5000, 10000]
-    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
-
-    class FakeBatch:
-        T = len(lengths)
-
-        def c(self):
-            b = _abi.wts_batch()
-            b.data = 16                       # never dereferenced by the sizing call
-            b.offsets = 16
-            b.offsets_host = offs.ctypes.data
-            b.T = self.T
-            b.d = 3
-            return b
-
-    def size(op, M, batch, opts):
-        n = ctypes.c_size_t(0)
-        assert lib.wts_workspace_size(op, M, ctypes.byref(batch.c()), ctypes.byref(opts), ctypes.byref(n)) == 0
-        return n.value
-
-    fake_api = types.SimpleNamespace(workspace_size=size, options=api.options)
-    M = 10000
-    sizes = [size(_abi.OP_SOFTDTW, M, FakeBatch(), api.options(dir_mode=1, store_pairs=s)) for s in range(5)]
-    assert sizes == sorted(sizes) and sizes[0] < sizes[1]
-    for free_bytes, want in ((sizes[0] + 1, 0), (sizes[2] + 16e9, 2), (sizes[2] + 16e9 - 1, 1), (sizes[4] + 20e9, 4)):
-        fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(
-            empty_cache=lambda: None, mem_get_info=lambda dev, f=free_bytes: (int(f), int(f) * 2)))
-        got, need = bench.store_pairs_that_fit(fake_api, fake_torch, None, M, FakeBatch())
-        assert got == want, (free_bytes, got, want)
-        assert need == (sizes[want] if want else 0)
